@@ -1,0 +1,242 @@
+"""CPU oracle of the learned sphere-tracing method — TEST INFRASTRUCTURE ONLY.
+
+A plain, slow FP64 restatement of what the CUDA library computes, written from the paper and sharing no
+code with the library:
+
+* ``rng.c``      Philox4x32-10 counter generator (published definition)
+* ``detmath.c``  log / sincos / atan2 from IEEE basic operations (bit-reproducible walk decisions)
+* ``walk.c``     brute-force HG random walk in the unit sphere (Sec. 3.1, Sec. 4.3 reservoir)
+* ``render.c``   sphere-traced and brute-force rendering with next-event estimation (Sec. 3, 4.1, 4.3)
+* ``cvae.py``    CVAE decoder, negative ELBO, analytic backward, Adam, training targets (Sec. 3.2, 4.1)
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+LIB_PATH = HERE / "libms_oracle.so"
+SOURCES = ["rng.c", "detmath.c", "walk.c", "render.c"]
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the C part of the oracle (no FMA contraction, so the FP64 walk is bit-reproducible)."""
+    srcs = [HERE / s for s in SOURCES]
+    newest = max(s.stat().st_mtime for s in srcs + [HERE / "oracle.h"])
+    if not force and LIB_PATH.exists() and LIB_PATH.stat().st_mtime >= newest:
+        return LIB_PATH
+    tmp = LIB_PATH.with_suffix(f".so.tmp{os.getpid()}")
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
+           "-o", str(tmp)] + [str(s) for s in srcs] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Medium(C.Structure):
+    _fields_ = [("optical_radius", C.c_double), ("g", C.c_double), ("albedo", C.c_double),
+                ("dir_in", C.c_double * 3), ("isotropic_start", C.c_int32),
+                ("first_event_at_origin", C.c_int32)]
+
+
+MEDIUM_DTYPE = np.dtype([("optical_radius", "<f8"), ("g", "<f8"), ("albedo", "<f8"), ("dir_in", "<f8", (3,)),
+                         ("isotropic_start", "<i4"), ("first_event_at_origin", "<i4")])
+assert MEDIUM_DTYPE.itemsize == C.sizeof(Medium)
+
+
+class Decoder(C.Structure):
+    _fields_ = [("p_in", C.c_int32), ("latent", C.c_int32), ("width", C.c_int32), ("p_out", C.c_int32),
+                ("w", C.POINTER(C.c_double))]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_uint32), ("max_segments", C.c_uint32),
+                ("cam_pos", C.c_double * 3), ("cam_at", C.c_double * 3), ("fov_y_deg", C.c_double),
+                ("light_pos", C.c_double * 3), ("light_I", C.c_double),
+                ("sigma_t", C.c_double), ("g", C.c_double), ("albedo", C.c_double),
+                ("disp_amp", C.c_double), ("disp_freq", C.c_double),
+                ("mode", C.c_int32), ("pad_", C.c_int32),
+                ("min_optical_radius", C.c_double), ("max_optical_radius", C.c_double),
+                ("seed", C.c_uint64), ("sample_offset", C.c_uint64)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(str(LIB_PATH))
+        P = C.c_void_p
+        L.om_philox.argtypes = [P, P, P]
+        L.om_philox_words.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, P]
+        L.om_log.argtypes = [C.c_double]
+        L.om_log.restype = C.c_double
+        L.om_sincos_turns.argtypes = [C.c_double, P, P]
+        L.om_atan2.argtypes = [C.c_double, C.c_double]
+        L.om_atan2.restype = C.c_double
+        L.om_walk.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, P, C.c_int, C.c_uint32, C.c_int, C.c_int,
+                              P, P, P, P, P, P, P, P, P, P, P, C.c_int]
+        L.om_walk.restype = C.c_int
+        L.om_render.argtypes = [P, P, P, P, C.c_int]
+        L.om_render.restype = C.c_int
+        L.om_decoder_sample.argtypes = [P, P, P, P, P]
+        L.om_hg_cosine.argtypes = [C.c_double, C.c_double]
+        L.om_hg_cosine.restype = C.c_double
+        L.om_scatter_dir.argtypes = [P, C.c_double, C.c_double, P]
+        L.om_inside_length.argtypes = [C.c_double, C.c_double, P, P]
+        L.om_inside_length.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- RNG and deterministic math
+
+def philox(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().om_philox(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def philox_words(seed, id0, n, step, tag):
+    out = np.zeros((n, 4), np.uint32)
+    lib().om_philox_words(seed, id0, n, step, tag, _ptr(out))
+    return out
+
+
+def u24(words):
+    return (np.asarray(words, np.uint32) >> np.uint32(8)).astype(np.float64) * 2.0 ** -24
+
+
+def det_log(x):
+    return np.array([lib().om_log(float(v)) for v in np.ravel(x)])
+
+
+def det_sincos_turns(u):
+    s, c = C.c_double(), C.c_double()
+    out = []
+    for v in np.ravel(u):
+        lib().om_sincos_turns(float(v), C.byref(s), C.byref(c))
+        out.append((s.value, c.value))
+    return np.array(out)
+
+
+def det_atan2(y, x):
+    return np.array([lib().om_atan2(float(a), float(b)) for a, b in zip(np.ravel(y), np.ravel(x))])
+
+
+def hg_cosine(u, g):
+    return np.array([lib().om_hg_cosine(float(v), float(g)) for v in np.ravel(u)])
+
+
+def scatter_dir(w, mu, u):
+    w = np.ascontiguousarray(w, np.float64)
+    out = np.zeros(3)
+    lib().om_scatter_dir(_ptr(w), float(mu), float(u), _ptr(out))
+    return out
+
+
+def normals_from_words(words):
+    """Box-Muller on 24-bit uniforms: word pairs (w0,w1), (w2,w3) -> four normals per row."""
+    u = u24(words)
+    out = np.empty_like(u)
+    for pair in range(2):
+        ua, ub = u[:, 2 * pair], u[:, 2 * pair + 1]
+        r = np.sqrt(-2.0 * np.log(1.0 - ua))
+        out[:, 2 * pair] = r * np.cos(2.0 * np.pi * ub)
+        out[:, 2 * pair + 1] = r * np.sin(2.0 * np.pi * ub)
+    return out
+
+
+def decoder_normals(seed, offset, n, count):
+    """Latent and posterior normals of the decoder queries offset..offset+n-1: counter (j, id_lo, id_hi, 0xD0),
+    j = 0, 1, ...; words of block j give normals 4j..4j+3.  Returns [n][count]."""
+    blocks = []
+    for j in range((count + 3) // 4):
+        blocks.append(normals_from_words(philox_words(seed, offset, n, j, 0xD0)))
+    return np.concatenate(blocks, axis=1)[:, :count]
+
+
+# ---------------------------------------------------------------- walk
+
+def walk(seed, n_photons, media, *, photon_offset=0, max_events=1 << 20, reservoir_mode=0, uniform_bits=53,
+         per_photon=True, n_threads=0):
+    """Run the oracle walk.  ``media`` is a dict of scalars or of length-n arrays with keys optical_radius,
+    g, albedo, dir_in ([3] or [n][3]), isotropic_start, first_event_at_origin."""
+    per_media = any(np.ndim(media[k]) > (1 if k == "dir_in" else 0) for k in media)
+    n_media = n_photons if per_media else 1
+    arr = np.zeros(max(n_media, 1), dtype=MEDIUM_DTYPE)
+    for k in ("optical_radius", "g", "albedo", "isotropic_start", "first_event_at_origin"):
+        arr[k] = np.broadcast_to(np.asarray(media[k]), (n_media,))
+    arr["dir_in"] = np.broadcast_to(np.asarray(media["dir_in"], np.float64), (n_media, 3))
+    out = dict(hist_n=np.zeros(64, np.uint64), hist_pos=np.zeros((32, 64), np.uint64),
+               hist_cos=np.zeros(64, np.uint64), counters=np.zeros(8, np.uint64))
+    if per_photon:
+        out.update(n_events=np.zeros(n_photons, np.int32), status=np.zeros(n_photons, np.uint8),
+                   exit_pos=np.zeros((n_photons, 3)), exit_dir=np.zeros((n_photons, 3)),
+                   rep_pos=np.zeros((n_photons, 3)), rep_dir=np.zeros((n_photons, 3)),
+                   rep_index=np.zeros(n_photons, np.int32))
+    g = out.get
+    out["threads"] = lib().om_walk(
+        seed, photon_offset, n_photons, _ptr(arr), int(per_media), max_events,
+        reservoir_mode, uniform_bits, _ptr(g("n_events")), _ptr(g("status")), _ptr(g("exit_pos")),
+        _ptr(g("exit_dir")), _ptr(g("rep_pos")), _ptr(g("rep_dir")), _ptr(g("rep_index")), _ptr(out["hist_n"]),
+        _ptr(out["hist_pos"]), _ptr(out["hist_cos"]), _ptr(out["counters"]), n_threads)
+    return out
+
+
+# ---------------------------------------------------------------- renderer
+
+def _decoder_struct(wvec, p_in, p_out, latent=4, width=16):
+    w = np.ascontiguousarray(np.asarray(wvec, np.float64))
+    return Decoder(p_in, latent, width, p_out, w.ctypes.data_as(C.POINTER(C.c_double))), w
+
+
+def render(params: dict, decoders=None, n_threads=0):
+    """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out)
+    for LengthGen, PathGen, EventGen.  Returns (image_sum[h][w], stats[8], threads)."""
+    P = RenderParams()
+    for k, v in params.items():
+        if isinstance(getattr(P, k), C.Array):
+            setattr(P, k, type(getattr(P, k))(*[float(t) for t in v]))
+        else:
+            setattr(P, k, v)
+    keep = []
+    decs = (Decoder * 3)()
+    if decoders is not None:
+        for i, (w, p_in, p_out) in enumerate(decoders):
+            d, arr = _decoder_struct(w, p_in, p_out)
+            decs[i] = d
+            keep.append(arr)
+    image = np.zeros((P.height, P.width), np.float64)
+    stats = np.zeros(8, np.uint64)
+    nt = lib().om_render(C.byref(P), C.cast(decs, C.c_void_p), _ptr(image), _ptr(stats), n_threads)
+    return image, stats, nt
+
+
+def decoder_sample_one(wvec, p_in, p_out, c, z, eps):
+    d, arr = _decoder_struct(wvec, p_in, p_out)
+    c = np.ascontiguousarray(c, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    e = np.ascontiguousarray(eps, np.float64)
+    x = np.zeros(p_out)
+    lib().om_decoder_sample(C.byref(d), _ptr(c), _ptr(z), _ptr(e), _ptr(x))
+    return x
+
+
+def inside_length(A, k, X, xl):
+    X = np.ascontiguousarray(X, np.float64)
+    xl = np.ascontiguousarray(xl, np.float64)
+    return lib().om_inside_length(A, k, _ptr(X), _ptr(xl))

@@ -1,0 +1,499 @@
+/*
+ * Oracle: renderer of a homogeneous translucent SDF object — TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Plain FP64 restatement, one path at a time, of:
+ *   Sec. 3 (first paragraph) / Fig. 2b: after a free flight to a collision, take the largest sphere inside
+ *       the boundary (from a signed distance function) and bypass the scattering inside it with the learned
+ *       models; otherwise (thin region) do one brute-force scattering event.  Delta tracking in a
+ *       homogeneous medium is exponential free flight.
+ *   Eq. 3: LengthGen samples N (phi = 1 physics), absorption A ~ Bernoulli(1 - phi^N), PathGen samples
+ *       (cos theta, alpha, beta), EventGen samples the representative event (X, W).
+ *   Eq. 4 and Sec. 4.1: x = r R^CVAE R_psi (sin theta, 0, cos theta); exit direction from (alpha, beta) in
+ *       the frame e_n = x^, e_b = w_in x x^, e_t = e_b x e_n; X and W rotated and scaled the same way;
+ *       sigma_t -> sigma_t * r before the models are evaluated.
+ *   Eq. 5 and Sec. 4.3: next-event estimation toward a point light with transmittance
+ *       exp(-sigma_t d_t) along the unrefracted segment; brute force adds phi * rho_g * gamma at every
+ *       event, sphere tracing adds Lambda^(N) * rho_g * gamma at the representative event.
+ * The readings taken where the paper is silent are listed beside each step below.
+ *
+ * Per path (pixel index -> counter id_hi, sample index -> id_lo) and segment step s (counter word 0):
+ *   tag 0: u0 free path, u1 HG cosine, u2 HG azimuth, u3 roulette
+ *   tag 1: u0 absorption test, u1 rotation angle psi
+ *   tags 2..7: Box-Muller normals n[0..23], tag t words (w0,w1) -> n[4(t-2)], n[4(t-2)+1], (w2,w3) -> next two
+ *   tag 8 at step 0: pixel jitter.
+ * Uniforms are (w >> 8) * 2^-24 (24-bit), identical to the single-precision kernels' stream.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+#define R_EPS        1e-4      /* distance from the boundary treated as on it */
+#define R_MAX_MARCH  1024      /* sphere-tracing steps per march; a march that runs out ends the path */
+#define R_N_MAX      16777216.0
+
+typedef struct {
+    int32_t p_in, latent, width, p_out;
+    const double* w;           /* W1[width][p_in+latent], b1, W2[width][width], b2, W3[2p_out][width], b3 */
+} om_decoder;
+
+typedef struct {
+    int32_t width, height;
+    uint32_t spp, max_segments;
+    double cam_pos[3], cam_at[3], fov_y_deg;
+    double light_pos[3], light_I;
+    double sigma_t, g, albedo;
+    double disp_amp, disp_freq;
+    int32_t mode;              /* 0 brute force, 1 sphere tracing */
+    int32_t pad_;
+    double min_optical_radius, max_optical_radius;
+    uint64_t seed, sample_offset;
+} om_render_params;
+
+typedef struct {
+    const om_render_params* P;
+    const om_decoder* dec;     /* [3]: LengthGen, PathGen, EventGen (NULL in brute force) */
+    double* image;
+    uint64_t* stats;
+    int next_row;
+    pthread_mutex_t lock;
+} render_job;
+
+static ov3 v3(double x, double y, double z) { ov3 r = { x, y, z }; return r; }
+static ov3 add(ov3 a, ov3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static ov3 sub(ov3 a, ov3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static ov3 mul(ov3 a, double s) { return v3(a.x * s, a.y * s, a.z * s); }
+static double dot(ov3 a, ov3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static ov3 cross(ov3 a, ov3 b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static ov3 normalize(ov3 a) { return mul(a, 1.0 / sqrt(dot(a, a))); }
+
+/* ---- scene: displaced unit sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz), negative inside ---- */
+typedef struct { double A, k, lip, rb2; } scene;
+
+static double sdf(const scene* S, ov3 p)
+{
+    return sqrt(dot(p, p)) - 1.0 - S->A * sin(S->k * p.x) * sin(S->k * p.y) * sin(S->k * p.z);
+}
+
+static ov3 sdf_grad(const scene* S, ov3 p)
+{
+    double sx = sin(S->k * p.x), sy = sin(S->k * p.y), sz = sin(S->k * p.z);
+    double cx = cos(S->k * p.x), cy = cos(S->k * p.y), cz = cos(S->k * p.z);
+    double n = sqrt(dot(p, p));
+    double ak = S->A * S->k;
+    return v3(p.x / n - ak * cx * sy * sz, p.y / n - ak * sx * cy * sz, p.z / n - ak * sx * sy * cz);
+}
+
+/* March inside the medium from p along w for at most l.  Returns 1 on a collision (*q = p + l w), 0 when
+ * the boundary is crossed outward at *q, 2 when the step cap runs out. */
+static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
+{
+    double t = 0.0;
+    for (int it = 0; it < R_MAX_MARCH; ++it) {
+        ov3 r = add(p, mul(w, t));
+        double d = -sdf(S, r) / S->lip;
+        if (d < R_EPS) {
+            if (dot(sdf_grad(S, r), w) > 0.0) {
+                *q = r;
+                return 0;
+            }
+            d = R_EPS;
+        }
+        if (t + d >= l) {
+            *q = add(p, mul(w, l));
+            return 1;
+        }
+        t = t + d;
+    }
+    return 2;
+}
+
+/* March outside from p along w.  Returns 1 when the path re-enters at *q, 0 when it leaves the bounding
+ * sphere, 2 when the step cap runs out. */
+static int march_outside(const scene* S, ov3 p, ov3 w, ov3* q)
+{
+    double t = 0.0;
+    for (int it = 0; it < R_MAX_MARCH; ++it) {
+        ov3 r = add(p, mul(w, t));
+        if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
+            return 0;
+        double d = sdf(S, r) / S->lip;
+        if (d < R_EPS) {
+            if (dot(sdf_grad(S, r), w) < 0.0) {
+                *q = r;
+                return 1;
+            }
+            d = R_EPS;
+        }
+        t = t + d;
+    }
+    return 2;
+}
+
+/* Length of the straight segment X -> x_L that lies inside the medium (Sec. 4.3, d_t); -1 when the step
+ * cap runs out (the estimate is then dropped). */
+static double inside_length(const scene* S, ov3 X, ov3 xl)
+{
+    ov3 dl = sub(xl, X);
+    double D = sqrt(dot(dl, dl));
+    ov3 w = mul(dl, 1.0 / D);
+    double t = 0.0, din = 0.0;
+    int inside = 1;
+    for (int it = 0; it < R_MAX_MARCH; ++it) {
+        if (t >= D)
+            return din;
+        ov3 r = add(X, mul(w, t));
+        double f = sdf(S, r);
+        if (inside) {
+            double d = -f / S->lip;
+            if (d < R_EPS) {
+                if (dot(sdf_grad(S, r), w) > 0.0) {
+                    inside = 0;
+                    continue;
+                }
+                d = R_EPS;
+            }
+            double step = fmin(d, D - t);
+            din = din + step;
+            t = t + step;
+        } else {
+            if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
+                return din;
+            double d = f / S->lip;
+            if (d < R_EPS) {
+                if (dot(sdf_grad(S, r), w) < 0.0) {
+                    inside = 1;
+                    continue;
+                }
+                d = R_EPS;
+            }
+            t = t + fmin(d, D - t);
+        }
+    }
+    return -1.0;
+}
+
+/* ---- random numbers ---- */
+typedef struct { uint32_t key[2]; uint64_t id; } stream;
+
+static void words(const stream* s, uint32_t step, uint32_t tag, uint32_t w[4])
+{
+    uint32_t ctr[4] = { step, (uint32_t)s->id, (uint32_t)(s->id >> 32), tag };
+    om_philox(ctr, s->key, w);
+}
+static double u24(uint32_t w) { return (double)(w >> 8) * 0x1.0p-24; }
+
+static void normals(const stream* s, uint32_t step, double n[24])
+{
+    for (uint32_t t = 2; t < 8; ++t) {
+        uint32_t w[4];
+        words(s, step, t, w);
+        for (int pair = 0; pair < 2; ++pair) {
+            double ua = u24(w[2 * pair]), ub = u24(w[2 * pair + 1]);
+            double r = sqrt(-2.0 * log(1.0 - ua));
+            n[4 * (t - 2) + 2 * pair] = r * cos(2.0 * M_PI * ub);
+            n[4 * (t - 2) + 2 * pair + 1] = r * sin(2.0 * M_PI * ub);
+        }
+    }
+}
+
+/* ---- learned models (Sec. 3.2): decoder MLP with Softplus between hidden layers ---- */
+static double softplus(double x) { return fmax(x, 0.0) + log1p(exp(-fabs(x))); }
+
+static void decoder_eval(const om_decoder* D, const double* in, double* out)
+{
+    int nin = D->p_in + D->latent, W = D->width, no = 2 * D->p_out;
+    const double* W1 = D->w;
+    const double* b1 = W1 + W * nin;
+    const double* W2 = b1 + W;
+    const double* b2 = W2 + W * W;
+    const double* W3 = b2 + W;
+    const double* b3 = W3 + no * W;
+    double h1[64], h2[64];
+    for (int i = 0; i < W; ++i) {
+        double a = b1[i];
+        for (int j = 0; j < nin; ++j) a += W1[i * nin + j] * in[j];
+        h1[i] = softplus(a);
+    }
+    for (int i = 0; i < W; ++i) {
+        double a = b2[i];
+        for (int j = 0; j < W; ++j) a += W2[i * W + j] * h1[j];
+        h2[i] = softplus(a);
+    }
+    for (int i = 0; i < no; ++i) {
+        double a = b3[i];
+        for (int j = 0; j < W; ++j) a += W3[i * W + j] * h2[j];
+        out[i] = a;
+    }
+}
+
+/* Draw one decoder sample x = mu + sqrt(Sigma) * eps (Sec. 3.2) from condition c and normals z, eps. */
+static void decoder_sample(const om_decoder* D, const double* c, const double* z, const double* eps, double* x)
+{
+    double in[32], out[32];
+    for (int j = 0; j < D->p_in; ++j) in[j] = c[j];
+    for (int j = 0; j < D->latent; ++j) in[D->p_in + j] = z[j];
+    decoder_eval(D, in, out);
+    for (int j = 0; j < D->p_out; ++j)
+        x[j] = out[j] + exp(0.5 * out[D->p_out + j]) * eps[j];
+}
+
+/* ---- phase function (Eq. 1) and its sampling ---- */
+static double hg_pdf(double cosang, double g)
+{
+    double den = 1.0 + g * g - 2.0 * g * cosang;
+    return (1.0 - g * g) / (4.0 * M_PI * den * sqrt(den));
+}
+
+static double hg_cosine(double u, double g)
+{
+    if (fabs(g) < 1e-4)
+        return 2.0 * u - 1.0;
+    double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+    return fmin(1.0, fmax(-1.0, (1.0 + g * g - t * t) / (2.0 * g)));
+}
+
+/* Orthonormal basis (t1, t2, w) of Duff et al. 2017; R^CVAE maps (0,0,1) to w. */
+static void onb(ov3 w, ov3* t1, ov3* t2)
+{
+    double sign = w.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sign + w.z);
+    double b = w.x * w.y * a;
+    *t1 = v3(1.0 + sign * w.x * w.x * a, sign * b, -sign * w.x);
+    *t2 = v3(b, sign + w.y * w.y * a, -w.y);
+}
+
+static ov3 scatter_dir(ov3 w, double mu, double u)
+{
+    ov3 t1, t2;
+    onb(w, &t1, &t2);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double ph = 2.0 * M_PI * u;
+    return normalize(add(add(mul(t1, st * cos(ph)), mul(t2, st * sin(ph))), mul(w, mu)));
+}
+
+/* Next-event estimate toward the point light from X, arriving with direction W (Eq. 5 term). */
+static double nee(const scene* S, const om_render_params* P, ov3 X, ov3 W, double weight, uint64_t* st)
+{
+    ov3 xl = v3(P->light_pos[0], P->light_pos[1], P->light_pos[2]);
+    ov3 dl = sub(xl, X);
+    double d2 = dot(dl, dl);
+    ov3 wl = mul(dl, 1.0 / sqrt(d2));
+    double rho = hg_pdf(dot(W, wl), P->g);
+    double din = inside_length(S, X, xl);
+    if (din < 0.0) {
+        st[6] += 1;
+        return 0.0;
+    }
+    return weight * rho * exp(-P->sigma_t * din) * P->light_I / d2;
+}
+
+/* One camera path; returns its contribution and updates the counters. */
+static double trace_path(const render_job* J, const scene* S, int px, int py, uint64_t sample, uint64_t* st)
+{
+    const om_render_params* P = J->P;
+    stream rs;
+    rs.key[0] = (uint32_t)P->seed;
+    rs.key[1] = (uint32_t)(P->seed >> 32);
+    rs.id = ((uint64_t)(uint32_t)(py * P->width + px) << 32) | (uint32_t)sample;
+    uint32_t w4[4];
+    words(&rs, 0u, 8u, w4);
+    double jx = u24(w4[0]), jy = u24(w4[1]);
+
+    /* pinhole camera */
+    ov3 cp = v3(P->cam_pos[0], P->cam_pos[1], P->cam_pos[2]);
+    ov3 fw = normalize(sub(v3(P->cam_at[0], P->cam_at[1], P->cam_at[2]), cp));
+    ov3 rt = normalize(cross(fw, v3(0.0, 1.0, 0.0)));
+    ov3 up = cross(rt, fw);
+    double th = tan(0.5 * P->fov_y_deg * M_PI / 180.0);
+    double aspect = (double)P->width / (double)P->height;
+    double sx = (2.0 * ((double)px + jx) / (double)P->width - 1.0) * th * aspect;
+    double sy = (1.0 - 2.0 * ((double)py + jy) / (double)P->height) * th;
+    ov3 w = normalize(add(add(fw, mul(rt, sx)), mul(up, sy)));
+
+    st[0] += 1;
+    ov3 p;
+    int hit = march_outside(S, cp, w, &p);
+    if (hit != 1) {
+        st[6] += (uint64_t)(hit == 2);
+        return 0.0;
+    }
+    st[1] += 1;
+
+    const double sig = P->sigma_t, g = P->g, phi = P->albedo;
+    double acc = 0.0;
+    for (uint32_t seg = 0;; ++seg) {
+        if (seg >= P->max_segments) {
+            st[6] += 1;
+            break;
+        }
+        st[2] += 1;
+        uint32_t u[4];
+        words(&rs, seg, 0u, u);
+        double l = -log(1.0 - u24(u[0])) / sig;
+        ov3 c;
+        int ev = march_inside(S, p, w, l, &c);
+        if (ev == 2) {
+            st[6] += 1;
+            break;
+        }
+        if (ev == 0) {
+            ov3 re;
+            int back = march_outside(S, c, w, &re);
+            if (back != 1) {
+                st[6] += (uint64_t)(back == 2);
+                break;                      /* left the object: black background */
+            }
+            p = re;                         /* re-entered: fresh flight (memoryless) */
+            continue;
+        }
+        if (P->mode == 1) {
+            double d = -sdf(S, c) / S->lip;
+            double r = fmin(d, P->max_optical_radius / sig);
+            double tau = sig * r;
+            if (tau >= P->min_optical_radius) {
+                /* ---- sphere-tracing step: the three models of Eq. 3 at optical radius tau ---- */
+                st[3] += 1;
+                uint32_t a4[4];
+                words(&rs, seg, 1u, a4);
+                double n[24];
+                normals(&rs, seg, n);
+                double ltau = log(tau);
+                double cL[2] = { ltau, g }, yN;
+                decoder_sample(&J->dec[0], cL, n + 0, n + 4, &yN);
+                double N = floor(exp(yN) + 0.5);
+                if (!(N >= 1.0)) N = 1.0;
+                if (N > R_N_MAX) N = R_N_MAX;
+                double lnN = log(N);
+                double cP[3] = { ltau, g, lnN }, xp[3];
+                decoder_sample(&J->dec[1], cP, n + 5, n + 9, xp);
+                double ct = fmin(1.0, fmax(-1.0, xp[0])), al = xp[1], be = xp[2];
+                double ab2 = al * al + be * be;
+                if (ab2 > 1.0) {
+                    double s = 1.0 / sqrt(ab2);
+                    al = al * s; be = be * s; ab2 = 1.0;
+                }
+                double cE[7] = { ltau, g, phi, ct, al, be, lnN }, xe[6];
+                decoder_sample(&J->dec[2], cE, n + 12, n + 16, xe);
+                double phiN = pow(phi, N);
+                double lam = (phi < 1.0) ? phi * (1.0 - phiN) / (1.0 - phi) : N;
+
+                /* Eq. 4 and Sec. 4.1: CVAE frame -> world */
+                ov3 t1, t2;
+                onb(w, &t1, &t2);
+                double psi = 2.0 * M_PI * u24(a4[1]);
+                double cs = cos(psi), sn = sin(psi);
+                double stt = sqrt(fmax(0.0, 1.0 - ct * ct));
+                double nn = sqrt(fmax(0.0, 1.0 - ab2));
+                ov3 xt = v3(stt, 0.0, ct);
+                ov3 wt = v3(be * ct + nn * stt, al, -be * stt + nn * ct);
+                ov3 Xt = v3(xe[0], xe[1], xe[2]);
+                double xn = sqrt(dot(Xt, Xt));
+                if (xn > 1.0) Xt = mul(Xt, 1.0 / xn);
+                ov3 Wt = v3(xe[3], xe[4], xe[5]);
+                double wn = sqrt(dot(Wt, Wt));
+                Wt = wn > 1e-12 ? mul(Wt, 1.0 / wn) : v3(0.0, 0.0, 1.0);
+                ov3 vs[4] = { xt, wt, Xt, Wt }, vw[4];
+                for (int k = 0; k < 4; ++k) {
+                    ov3 v1 = v3(cs * vs[k].x - sn * vs[k].y, sn * vs[k].x + cs * vs[k].y, vs[k].z);
+                    vw[k] = add(add(mul(t1, v1.x), mul(t2, v1.y)), mul(w, v1.z));
+                }
+                ov3 xexit = add(c, mul(vw[0], r));
+                ov3 wout = normalize(vw[1]);
+                ov3 X = add(c, mul(vw[2], r));
+                ov3 Wd = normalize(vw[3]);
+                st[7] += 1;
+                acc += nee(S, P, X, Wd, lam, st);
+                if (u24(a4[0]) >= phiN) {
+                    st[5] += 1;
+                    break;
+                }
+                p = xexit;
+                w = wout;
+                continue;
+            }
+        }
+        /* ---- brute-force scattering event (Sec. 3.1) with next-event estimation (Eq. 5) ---- */
+        st[4] += 1;
+        st[7] += 1;
+        acc += nee(S, P, c, w, phi, st);
+        if (u24(u[3]) >= phi) {
+            st[5] += 1;
+            break;
+        }
+        w = scatter_dir(w, hg_cosine(u24(u[1]), g), u24(u[2]));
+        p = c;
+    }
+    return acc;
+}
+
+static void* render_worker(void* arg)
+{
+    render_job* J = (render_job*)arg;
+    const om_render_params* P = J->P;
+    scene S;
+    S.A = P->disp_amp;
+    S.k = P->disp_freq;
+    S.lip = 1.0 + P->disp_amp * P->disp_freq;
+    double rb = 1.0 + P->disp_amp + 1e-3;
+    S.rb2 = rb * rb;
+    uint64_t st[8] = { 0 };
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int py = J->next_row++;
+        pthread_mutex_unlock(&J->lock);
+        if (py >= P->height)
+            break;
+        for (int px = 0; px < P->width; ++px) {
+            double acc = 0.0;
+            for (uint32_t s = 0; s < P->spp; ++s)
+                acc += trace_path(J, &S, px, py, P->sample_offset + s, st);
+            J->image[(size_t)py * P->width + px] += acc;
+        }
+    }
+    pthread_mutex_lock(&J->lock);
+    for (int k = 0; k < 8; ++k) J->stats[k] += st[k];
+    pthread_mutex_unlock(&J->lock);
+    return NULL;
+}
+
+/*
+ * Render: image[h][w] accumulates the sum over the spp samples of each pixel (divide by spp for the mean).
+ * stats[8]: camera paths, paths entering the object, flight segments, sphere steps, brute events,
+ * absorbed paths, truncated paths or dropped estimates (segment cap or march step cap), next-event
+ * estimates.  Returns the number of threads used.
+ */
+int om_render(const om_render_params* P, const om_decoder* dec3, double* image, uint64_t* stats, int n_threads)
+{
+    render_job J;
+    J.P = P;
+    J.dec = dec3;
+    J.image = image;
+    J.stats = stats;
+    J.next_row = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    int nt = om_num_threads(n_threads);
+    if (nt > P->height) nt = P->height > 0 ? P->height : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+    for (int t = 0; t < nt; ++t)
+        pthread_create(&th[t], NULL, render_worker, &J);
+    for (int t = 0; t < nt; ++t)
+        pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    return nt;
+}
+
+/* Single-query decoder sample, exposed for the tests. */
+void om_decoder_sample(const om_decoder* D, const double* c, const double* z, const double* eps, double* x)
+{
+    decoder_sample(D, c, z, eps, x);
+}
+
+/* Inside length of one segment, exposed for the tests. */
+double om_inside_length(double A, double k, const double* X, const double* xl)
+{
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    return inside_length(&S, v3(X[0], X[1], X[2]), v3(xl[0], xl[1], xl[2]));
+}

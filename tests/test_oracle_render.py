@@ -1,0 +1,109 @@
+"""Pins of the oracle renderer (Sec. 3, 4.1, 4.3; Eq. 1 and 5), CPU only."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2011_03082_b300 import synth
+
+
+def test_inside_length_undisplaced_sphere_is_the_chord(orc):
+    rng = np.random.default_rng(0)
+    xl = np.array([2.0, 2.0, 3.0])
+    for _ in range(200):
+        X = rng.uniform(-0.55, 0.55, 3)
+        w = (xl - X) / np.linalg.norm(xl - X)
+        b, c = X @ w, X @ X - 1
+        chord = -b + math.sqrt(b * b - c)
+        assert abs(orc.inside_length(0.0, 6.0, X, xl) - chord) < 2e-4
+
+
+def test_inside_length_displaced_sphere_against_dense_sampling(orc):
+    A, k = 0.1, 6.0
+    rng = np.random.default_rng(1)
+    f = lambda p: np.linalg.norm(p, axis=-1) - 1 - A * np.sin(k * p[..., 0]) * np.sin(k * p[..., 1]) * np.sin(k * p[..., 2])
+    checked = 0
+    for _ in range(60):
+        X = rng.uniform(-0.8, 0.8, 3)
+        if f(X) > -0.02:
+            continue
+        xl = rng.uniform(-3, 3, 3) * np.array([1, 1, 0]) + np.array([0, 0, 3.0])
+        t = np.linspace(0, 1, 400001)
+        pts = X + t[:, None] * (xl - X)
+        inside = f(pts) < 0
+        ref = inside[:-1].mean() * np.linalg.norm(xl - X)
+        assert abs(orc.inside_length(A, k, X, xl) - ref) < 1e-3
+        checked += 1
+    assert checked > 20
+
+
+def _render(orc, **kw):
+    decoders = kw.pop("decoders", None)
+    p = synth.render_scene(kw.pop("sigma_t", 8.0), width=kw.pop("width", 16), height=kw.pop("height", 16),
+                           spp=kw.pop("spp", 4), mode=kw.pop("mode", 0))
+    p.update(kw)
+    return orc.render(p, decoders)
+
+
+def test_zero_albedo_gives_black_image(orc):
+    img, st, _ = _render(orc, albedo=0.0)
+    assert st[4] > 0 and np.all(img == 0.0)
+
+
+def test_vanishing_density_gives_black_image(orc):
+    img, st, _ = _render(orc, sigma_t=1e-9)
+    assert st[1] > 0 and st[4] == 0 and np.all(img == 0.0)
+
+
+def test_light_intensity_is_linear(orc):
+    a, _, _ = _render(orc, light_I=10.0)
+    b, _, _ = _render(orc, light_I=20.0)
+    assert np.allclose(b, 2 * a, rtol=1e-14, atol=0) and a.sum() > 0
+
+
+def test_sphere_mode_without_spheres_equals_brute_force(orc):
+    """With a minimum optical radius no sphere reaches, the sphere tracer takes the thin-region fallback at
+    every collision and consumes the same random numbers as brute force."""
+    a, sa, _ = _render(orc, mode=0)
+    b, sb, _ = _render(orc, mode=1, min_optical_radius=1e30)
+    assert np.array_equal(a, b) and np.array_equal(sa, sb)
+
+
+def test_single_scattering_limit_matches_quadrature(orc):
+    """Undisplaced sphere, tiny albedo: only the first event's NEE survives (O(phi^2) corrections).  The pixel
+    value is phi * int_0^2 sigma e^{-sigma s} rho_g(cos) e^{-sigma d_in(s)} I / d(s)^2 ds along the central
+    camera ray entering at (0,0,1) going -z (Eq. 2 transmittance, Eq. 1 phase function, Eq. 5 term)."""
+    sigma, g, phi, I = 2.0, 0.6, 1e-3, 10.0
+    xl = np.array([2.0, 2.0, 3.0])
+    W = np.array([0.0, 0.0, -1.0])
+
+    def integrand(s):
+        X = np.array([0.0, 0.0, 1.0 - s])
+        dl = xl - X
+        d = np.linalg.norm(dl)
+        wl = dl / d
+        cosang = W @ wl
+        rho = (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * cosang) ** 1.5)
+        b, c = X @ wl, X @ X - 1
+        din = -b + math.sqrt(b * b - c)
+        return sigma * math.exp(-sigma * s) * rho * math.exp(-sigma * din) * I / (d * d)
+
+    ref = phi * integrate.quad(integrand, 0.0, 2.0, epsabs=1e-14, limit=200)[0]
+    spp = 40000
+    p = synth.render_scene(sigma, width=1, height=1, spp=spp, mode=0, g=g, albedo=phi, disp_amp=0.0)
+    p["fov_y_deg"] = 1e-4
+    img, st, _ = orc.render(p)
+    est = img[0, 0] / spp
+    # per-path standard error from the same integrand: second moment by quadrature
+    m2 = phi * phi * integrate.quad(lambda s: integrand(s) ** 2 / (sigma * math.exp(-sigma * s)), 0, 2)[0]
+    se = math.sqrt(max(m2 - ref * ref, 0) / spp)
+    assert abs(est - ref) < 5 * se + 2e-3 * ref, (est, ref, se)
+
+
+def test_sphere_mode_runs_with_models(orc):
+    decs = []
+    for i, (name, (p_in, p_out)) in enumerate(synth.MODEL_SHAPES.items()):
+        decs.append((synth.xavier_decoder(100 + i, p_in, p_out).astype(np.float64), p_in, p_out))
+    img, st, _ = _render(orc, mode=1, sigma_t=64.0, decoders=decs)
+    assert st[3] > 0 and np.all(np.isfinite(img)) and np.all(img >= 0)
