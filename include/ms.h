@@ -1,0 +1,232 @@
+/*
+ * ms.h — C ABI of the learned sphere-tracing library for subsurface scattering (one B300, sm_103a).
+ *
+ * The method (Leonard, Hoehlein, Westermann, "Learning Multiple-Scattering Solutions for Sphere-Tracing of
+ * Volumetric Subsurface Effects"): light paths through a homogeneous translucent medium (extinction
+ * sigma_t, albedo phi, Henyey-Greenstein anisotropy g) are advanced in large steps; at each collision the
+ * largest sphere inside the boundary is taken from a signed distance function and three conditional-VAE
+ * decoders sample what happens inside it: the number of scattering events N (LengthGen, which sets the
+ * absorption probability 1 - phi^N), the exit point and direction (PathGen) and one representative
+ * in-scatter event for next-event estimation (EventGen).  The brute-force Henyey-Greenstein walk is both the
+ * plain method and the generator of the models' training data.
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented as "device" are CUDA device pointers owned by the caller; "host" pointers are read
+ *    during the call only.  The library allocates no device memory: scratch space is passed in by the
+ *    caller, sized by the matching *_workspace_size() function, and must be 256-byte aligned.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL means the legacy default stream);
+ *    the call returns before the GPU finishes.  Outputs documented as "accumulated" are added to, so calls
+ *    on disjoint photon or sample ranges (photon_offset, sample_offset) compose; the caller zeroes them.
+ *  - Arguments are validated on the host before anything is enqueued.  Errors return a negative ms_status
+ *    and leave a message for ms_last_error() (per host thread); no exception crosses the ABI.  A call that
+ *    returns an error has enqueued nothing.
+ *  - Random numbers come from the counter-based generator Philox4x32-10 keyed by `seed`; results depend only
+ *    on (seed, ids, offsets) and not on launch configuration.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MS_OK = 0,
+    MS_WARN_TRUNCATED = 1,      /* reserved: caps are reported in the asynchronous counters instead         */
+    MS_ERR_INVALID_ARG = -1,
+    MS_ERR_CUDA = -2,           /* a CUDA runtime call failed; ms_last_error() has the CUDA error string   */
+    MS_ERR_TIMEOUT = -3,        /* a device loop exhausted its iteration budget                           */
+    MS_ERR_UNSUPPORTED = -4     /* unsupported shape or precision                                         */
+} ms_status;
+
+enum { MS_FP32 = 0, MS_FP64 = 1, MS_FP16 = 2, MS_BF16 = 3 };
+enum { MS_BRUTE = 0, MS_SPHERE = 1 };
+enum { MS_ESCAPED = 0, MS_ABSORBED = 1, MS_TRUNCATED = 2 };
+
+/* Message of the last error on the calling host thread ("" if none). */
+const char* ms_last_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int ms_version(void);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Brute-force Henyey-Greenstein random walk in the unit sphere (Sec. 3.1, Eq. 1; reservoir Sec. 4.3).
+ *
+ * A photon starts at the centre with direction dir_in (or isotropic).  With first_event_at_origin = 1 (the
+ * paper's training convention) the first scattering event is at the centre; with 0 the photon first flies.
+ * Free paths are l = -log(1 - xi) / sigma_t with sigma_t the optical radius (sphere radius 1); at each event
+ * Russian roulette continues with probability albedo and the new direction is drawn from the HG phase
+ * function (cosine between old and new propagation direction, mean g); the walk ends at the first crossing
+ * of the sphere.  N counts events including the one at the centre; an absorbed photon's N is the event at
+ * which it was absorbed.
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct {
+    float optical_radius;       /* sigma_t * R > 0                                  */
+    float g;                    /* HG anisotropy, |g| < 1                            */
+    float albedo;               /* phi in [0, 1]                                     */
+    float dir_in[3];            /* incoming direction (normalised by the library)    */
+    int32_t isotropic_start;    /* 1: initial direction uniform on the sphere        */
+    int32_t first_event_at_origin;
+} ms_medium;                    /* 32 bytes */
+
+typedef struct {
+    uint64_t seed;
+    uint64_t photon_offset;     /* first photon id (for sharding)                                     */
+    uint64_t n_photons;
+    const ms_medium* media;     /* device: 1 entry, or n_photons entries if per_photon_media          */
+    int32_t per_photon_media;
+    uint32_t max_events;        /* a photon with this many events and no exit is truncated (>= 1)     */
+    int32_t reservoir;          /* representative event: 0 none; 1 uniform over the events; 2 weights
+                                   albedo^k with roulette off (training data: the path follows the
+                                   albedo-1 physics, Sec. 3.2, and the event is chosen as in Sec. 4.3) */
+    int32_t precision;          /* MS_FP32: 24-bit uniforms, single precision, the fast path.
+                                   MS_FP64: 53-bit uniforms and double precision built from correctly
+                                   rounded basic operations: every integer output is reproducible bit
+                                   for bit by an implementation of the same steps.                     */
+} ms_walk_params;
+
+typedef struct {
+    /* per photon, device, optional (NULL): indexed by photon id - photon_offset */
+    int32_t* n_events;
+    uint8_t* status;            /* MS_ESCAPED / MS_ABSORBED / MS_TRUNCATED                             */
+    float* exit_pos;            /* [n][3] exit point on the unit sphere (0 if not escaped)             */
+    float* exit_dir;            /* [n][3] exit direction (0 if not escaped)                            */
+    float* rep_pos;             /* [n][3] representative event position (reservoir != 0)               */
+    float* rep_dir;             /* [n][3] direction arriving at the representative event               */
+    int32_t* rep_index;         /* [n] its event index k in 1..N (0: none)                             */
+    /* accumulated, device, optional (NULL) */
+    unsigned long long* hist_n;     /* [64]: bin 0 for N = 0, else min(63, 1 + 4*floor(log2 N) + the two
+                                       bits below the leading one of N) — quarter octaves              */
+    unsigned long long* hist_pos;   /* [32][64] escaped photons: cos(theta) = x_z in 32 equal bins over
+                                       [-1,1], azimuth atan2(x_y, x_x) + pi in 64 equal bins          */
+    unsigned long long* hist_cos;   /* [64] escaped photons: exit_dir . exit_pos in 64 bins over [0,1]  */
+    unsigned long long* counters;   /* [8]: escaped, absorbed, truncated, total events, 0, 0, 0, 0     */
+} ms_walk_out;
+
+size_t ms_walk_workspace_size(const ms_walk_params* p);
+/* Truncated photons are counted in counters[2]; the call does not wait for the GPU, so it returns MS_OK
+ * and the caller reads the counters. */
+ms_status ms_simulate_walks(const ms_walk_params* p, const ms_walk_out* out, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Conditional-VAE decoder inference (Sec. 3.2): y = W3 sp(W2 sp(W1 [c; z] + b1) + b2) + b3 with
+ * sp = Softplus, y = (mu, log Sigma) of a diagonal Gaussian, sample x = mu + exp(log Sigma / 2) * eps.
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t p_in;               /* condition size, 1..12                                               */
+    int32_t latent;             /* latent size L, 1..8 (p_in + latent <= 16)                          */
+    int32_t width;              /* hidden width W, must be 16                                          */
+    int32_t p_out;              /* output size P, 1..8                                                 */
+    int32_t precision;          /* MS_FP32, MS_FP16 or MS_BF16 (FP32 accumulation)                     */
+    const float* weights;       /* device, packed float32: W1[W][p_in+L] b1[W] W2[W][W] b2[W]
+                                   W3[2P][W] b3[2P] (row-major [out][in])                              */
+} ms_decoder;
+
+/* cond: device [n][p_in].  z_eps: device [n][latent + p_out] standard normals (z then eps), or NULL to draw
+ * them in the kernel: normals 4j..4j+3 of query q come from counter (j, id_lo, id_hi, 0xD0), id = offset+q,
+ * by Box-Muller on 24-bit uniforms (words (w0,w1) and (w2,w3)).  out_mean_logvar: device [n][2P] or NULL;
+ * out_sample: device [n][P] or NULL. */
+ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const float* z_eps, uint64_t seed,
+                        uint64_t offset, uint64_t n, float* out_mean_logvar, float* out_sample, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * CVAE training (Sec. 3.2): encoder Enc([x; c]) -> (mu_e, log Sigma_e) in R^L, z = mu_e + exp(lv_e/2) eps,
+ * decoder as above; loss = mean over the batch of the negative ELBO
+ *   0.5 sum_d (lv_d + (x_d - mu_d)^2 exp(-lv_d) + ln 2pi) + 0.5 sum_l (mu_l^2 + exp(lv_l) - lv_l - 1).
+ * Parameters: encoder block E1[W][P+p_in] e1 E2[W][W] e2 E3[2L][W] e3, then the decoder block (as
+ * ms_decoder.weights).  The optimiser is Adam (AdamW with weight_decay > 0), as in Sec. 3.2.
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t p_in, p_out, latent, width;   /* width must be 16; p_in + latent <= 16; p_out + p_in <= 16 */
+    int32_t precision;                    /* MS_FP32 (BF16 compute with FP32 master weights: MS_BF16)   */
+} ms_cvae_shape;
+
+size_t ms_cvae_num_params(const ms_cvae_shape* s);
+size_t ms_cvae_workspace_size(const ms_cvae_shape* s, uint64_t batch);
+
+/* Loss and gradient of one batch.  x: device [B][p_out]; c: device [B][p_in]; eps_z: device [B][latent]
+ * standard normals, or NULL to draw them: normals 4j..4j+3 of sample b come from counter
+ * (j, b, step, 0xE0) by Box-Muller on 24-bit uniforms (B < 2^32).
+ * grad: device [n_params] (overwritten) or NULL; loss3: device [3] (overwritten): loss, rec, kl.
+ * The gradient reduction is deterministic (fixed order). */
+ms_status ms_cvae_forward_backward(const ms_cvae_shape* s, const float* params, const float* x, const float* c,
+                                   const float* eps_z, uint64_t B, uint64_t seed, uint64_t step, float* grad,
+                                   float* loss3, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One bias-corrected Adam step t >= 1 on n parameters (device arrays, in place). */
+ms_status ms_adam_step(float* params, float* m, float* v, const float* grad, uint64_t n, uint64_t t, float lr,
+                       float beta1, float beta2, float eps, float weight_decay, void* stream);
+
+/* ms_cvae_forward_backward followed by ms_adam_step (beta 0.9/0.999, eps 1e-8) on the same stream;
+ * the gradient lives in the workspace. */
+ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, float* m, float* v, const float* x,
+                             const float* c, const float* eps_z, uint64_t B, uint64_t seed, uint64_t step,
+                             float lr, float weight_decay, float* loss3, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
+/* Walk records -> conditions and targets of the three CVAEs (Sec. 4.1, Eq. 3, Eq. 4 inverted).  Each record
+ * is rotated about (0,0,1) by -psi, psi = atan2(x_y, x_x), so the exit point is (sin theta, 0, cos theta);
+ * alpha = w~_y, beta = w~_x cos theta - w~_z sin theta.  N is dequantised as y = ln(N - 1/2 + u) with u the
+ * 24-bit uniform of word 0 at counter (0, id_lo, id_hi, 0x44), id = photon index.  Outputs (device):
+ * cL [n][2] = (ln tau, g), xL [n][1] = y, cP [n][3] = (ln tau, g, ln N), xP [n][3] = (cos theta, alpha,
+ * beta), cE [n][7] = (ln tau, g, phi, cos theta, alpha, beta, ln N), xE [n][6] = (X~, W~). */
+ms_status ms_training_records(uint64_t n, const int32_t* n_events, const float* exit_pos, const float* exit_dir,
+                              const float* rep_pos, const float* rep_dir, const ms_medium* media,
+                              int32_t per_photon_media, uint64_t seed, float* cL, float* xL, float* cP,
+                              float* xP, float* cE, float* xE, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Rendering a homogeneous translucent SDF object with a point light (Sec. 3, Fig. 2b; Sec. 4.1; Sec. 4.3,
+ * Eq. 5).  The object is the displaced unit sphere f(p) = |p| - 1 - A sin(k x) sin(k y) sin(k z) (negative
+ * inside); |f| / (1 + A k) is a conservative distance.  The boundary is index matched (no refraction, as in
+ * the paper's unrefracted NEE).  Camera paths enter the object; after each free flight to a collision:
+ *   MS_SPHERE: if sigma_t * r >= min_optical_radius with r = min(distance bound, max_optical_radius /
+ *     sigma_t), one sphere step: LengthGen -> N, PathGen -> exit (Eq. 4), EventGen -> (X, W), NEE at X with
+ *     weight Lambda = sum_{i=1..N} phi^i, then absorption with probability 1 - phi^N; otherwise, and always
+ *   MS_BRUTE: one scattering event: NEE with weight phi, roulette, HG scattering.
+ * The background is black and the light is not visible, so every contribution is a next-event estimate
+ * phi-or-Lambda * rho_g(W . w_L) * exp(-sigma_t d_in) * I / |x_L - X|^2.
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t width, height;
+    uint32_t spp;               /* samples per pixel; sample indices sample_offset .. +spp-1             */
+    uint32_t max_segments;      /* flights per path before truncation                                  */
+    float cam_pos[3], cam_at[3], fov_y_deg;
+    float light_pos[3], light_I;
+    float sigma_t, g, albedo;
+    float disp_amp, disp_freq;  /* A, k of the SDF                                                     */
+    int32_t mode;               /* MS_BRUTE or MS_SPHERE                                               */
+    float min_optical_radius;   /* smallest sigma_t * r for a sphere step (thin-region fallback)      */
+    float max_optical_radius;   /* largest sigma_t * r (the training range of the models)             */
+    uint64_t seed, sample_offset;
+} ms_render_params;
+
+typedef struct {
+    ms_decoder length;          /* LengthGen: p_in 2 (ln tau, g), p_out 1 (ln N dequantised)             */
+    ms_decoder path;            /* PathGen:   p_in 3 (ln tau, g, ln N), p_out 3 (cos theta, alpha, beta) */
+    ms_decoder event;           /* EventGen:  p_in 7 (ln tau, g, phi, cos theta, alpha, beta, ln N),
+                                   p_out 6 (X~, W~)                                                      */
+} ms_cvae_set;
+
+size_t ms_render_workspace_size(const ms_render_params* reqs, int n_requests);
+
+/* image: device [height][width] doubles, accumulated: the sum over the pixel's samples (divide by spp).
+ * stats: device [8] accumulated: camera paths, paths entering the object, flights, sphere steps, brute
+ * events, absorbed, truncated paths or dropped estimates, next-event estimates.  models: host struct with
+ * device weight pointers (ignored in MS_BRUTE). */
+ms_status ms_render(const ms_render_params* p, const ms_cvae_set* models, double* image,
+                    unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Many requests in one persistent launch.  reqs: host [n]; images: device, request i's [h][w] image starts
+ * at the sum of the previous requests' h*w; stats: device [n][8]. */
+ms_status ms_render_batch(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
+                          unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MS_H */
