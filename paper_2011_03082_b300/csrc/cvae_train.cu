@@ -1,0 +1,409 @@
+// CVAE training (Sec. 3.2): negative ELBO, its analytic gradient and Adam, hand-written.
+//
+//   encoder  [x ; c] -> 16 -> 16 -> (mu_e, log Sigma_e) in R^L       (Softplus between hidden layers)
+//   z = mu_e + exp(lv_e / 2) eps
+//   decoder  [c ; z] -> 16 -> 16 -> (mu_d, log Sigma_d) in R^P
+//   loss = mean_b [ 0.5 sum_d (lv_d + (x_d - mu_d)^2 e^{-lv_d} + ln 2 pi) + 0.5 sum_l (mu_l^2 + e^{lv_l} - lv_l - 1) ]
+//
+// Kernel design:
+//  * fwd_bwd: one sample per thread, 128 samples per block.  Forward and backward run in registers; the
+//    layer inputs and the back-propagated deltas of every layer are staged in shared memory (rows padded to
+//    an odd stride), after which the block forms its partial weight gradient sum_s delta[s][o] * in[s][k]
+//    with one thread per parameter, summing samples in a fixed order.  Per-block partials go to the
+//    workspace: no floating-point atomics anywhere, so the gradient is bit-reproducible.
+//  * reduce: one thread per parameter sums the block partials in block order and writes the gradient and
+//    the loss terms.
+//  * adam: element-wise bias-corrected Adam (AdamW decay when weight_decay > 0).
+#include <cmath>
+
+#include "ms_device.cuh"
+
+namespace ms {
+namespace train {
+
+constexpr int kW = 16;
+constexpr int kL = 4;
+constexpr int kSamples = 128;
+
+template <int PI, int PO>
+struct Shape {
+    static constexpr int IE = PO + PI;                // encoder input
+    static constexpr int ID = PI + kL;                // decoder input
+    // packed parameter offsets: encoder E1 e1 E2 e2 E3 e3, then decoder D1 d1 D2 d2 D3 d3
+    static constexpr int E1 = 0, e1 = E1 + kW * IE, E2 = e1 + kW, e2 = E2 + kW * kW, E3 = e2 + kW,
+                         e3 = E3 + 2 * kL * kW, D1 = e3 + 2 * kL, d1 = D1 + kW * ID, D2 = d1 + kW,
+                         d2 = D2 + kW * kW, D3 = d2 + kW, d3 = D3 + 2 * PO * kW, NP = d3 + 2 * PO;
+    // shared staging: per sample, the inputs and deltas of the six layers; rows of stride 17 (odd)
+    static constexpr int R = 17;
+    enum Slot { IN1E, H1E, H2E, IN1D, H1D, H2D, DA1E, DA2E, DOE, DA1D, DA2D, DY, NSLOT };
+};
+
+__device__ __forceinline__ float sigmoidf_fast(float a) { return __fdividef(1.0f, 1.0f + __expf(-a)); }
+
+template <int K, int O>
+__device__ __forceinline__ void fwd_layer(const float* __restrict__ Wm, const float* __restrict__ b,
+                                          const float (&x)[K], float (&a)[O])
+{
+#pragma unroll
+    for (int o = 0; o < O; ++o) {
+        float acc = __ldg(b + o);
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc = fmaf(__ldg(Wm + o * K + k), x[k], acc);
+        a[o] = acc;
+    }
+}
+
+// dx = W^T da
+template <int K, int O>
+__device__ __forceinline__ void bwd_layer(const float* __restrict__ Wm, const float (&da)[O], float (&dx)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) dx[k] = 0.0f;
+#pragma unroll
+    for (int o = 0; o < O; ++o)
+#pragma unroll
+        for (int k = 0; k < K; ++k) dx[k] = fmaf(__ldg(Wm + o * K + k), da[o], dx[k]);
+}
+
+template <int PI, int PO>
+__global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ prm, const float* __restrict__ X,
+                                                    const float* __restrict__ Cc, const float* __restrict__ EPS,
+                                                    uint64_t B, uint64_t seed, uint64_t step,
+                                                    float* __restrict__ partial)
+{
+    using S = Shape<PI, PO>;
+    extern __shared__ float sm[];
+    const int t = threadIdx.x;
+    const uint64_t b = (uint64_t)blockIdx.x * kSamples + t;
+    const bool live = b < B;
+    float* row_base = sm;   // [NSLOT][kSamples][R]
+    auto row = [&](int slot, int s) -> float* { return row_base + ((size_t)slot * kSamples + s) * S::R; };
+    __shared__ float s_rec[kSamples / 32], s_kl[kSamples / 32];
+
+    // ---------------- forward ----------------
+    float xin[S::IE], c[PI], x[PO];
+#pragma unroll
+    for (int j = 0; j < PO; ++j) x[j] = live ? X[b * PO + j] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < PI; ++j) c[j] = live ? Cc[b * PI + j] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < PO; ++j) xin[j] = x[j];
+#pragma unroll
+    for (int j = 0; j < PI; ++j) xin[PO + j] = c[j];
+    float eps[kL];
+    if (EPS) {
+#pragma unroll
+        for (int l = 0; l < kL; ++l) eps[l] = live ? EPS[b * kL + l] : 0.0f;
+    } else {
+        const Stream st(seed, (step << 32) | (b & 0xffffffffull));
+        const Words w = st.at(0u, 0xE0u);
+        const float2 p0 = box_muller(w.w0, w.w1), p1 = box_muller(w.w2, w.w3);
+        eps[0] = p0.x; eps[1] = p0.y; eps[2] = p1.x; eps[3] = p1.y;
+    }
+    float a1e[kW], h1e[kW], a2e[kW], h2e[kW], oe[2 * kL];
+    fwd_layer<S::IE, kW>(prm + S::E1, prm + S::e1, xin, a1e);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) h1e[o] = softplus(a1e[o]);
+    fwd_layer<kW, kW>(prm + S::E2, prm + S::e2, h1e, a2e);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) h2e[o] = softplus(a2e[o]);
+    fwd_layer<kW, 2 * kL>(prm + S::E3, prm + S::e3, h2e, oe);
+    float sd_e[kL], z[kL];
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+        sd_e[l] = __expf(0.5f * oe[kL + l]);
+        z[l] = oe[l] + sd_e[l] * eps[l];
+    }
+    float din[S::ID];
+#pragma unroll
+    for (int j = 0; j < PI; ++j) din[j] = c[j];
+#pragma unroll
+    for (int l = 0; l < kL; ++l) din[PI + l] = z[l];
+    float a1d[kW], h1d[kW], a2d[kW], h2d[kW], y[2 * PO];
+    fwd_layer<S::ID, kW>(prm + S::D1, prm + S::d1, din, a1d);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) h1d[o] = softplus(a1d[o]);
+    fwd_layer<kW, kW>(prm + S::D2, prm + S::d2, h1d, a2d);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) h2d[o] = softplus(a2d[o]);
+    fwd_layer<kW, 2 * PO>(prm + S::D3, prm + S::d3, h2d, y);
+
+    const float invB = 1.0f / (float)B;
+    float rec = 0.0f, kl = 0.0f;
+    float dy[2 * PO];
+#pragma unroll
+    for (int d = 0; d < PO; ++d) {
+        const float r = x[d] - y[d];
+        const float iv = __expf(-y[PO + d]);
+        rec += 0.5f * (y[PO + d] + r * r * iv + 1.8378770664093453f);
+        dy[d] = live ? -r * iv * invB : 0.0f;
+        dy[PO + d] = live ? 0.5f * (1.0f - r * r * iv) * invB : 0.0f;
+    }
+#pragma unroll
+    for (int l = 0; l < kL; ++l) kl += 0.5f * (oe[l] * oe[l] + sd_e[l] * sd_e[l] - oe[kL + l] - 1.0f);
+
+    // ---------------- backward ----------------
+    float dh[kW], da2d[kW], da1d[kW], ddin[S::ID];
+    bwd_layer<kW, 2 * PO>(prm + S::D3, dy, dh);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) da2d[o] = dh[o] * sigmoidf_fast(a2d[o]);
+    bwd_layer<kW, kW>(prm + S::D2, da2d, dh);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) da1d[o] = dh[o] * sigmoidf_fast(a1d[o]);
+    bwd_layer<S::ID, kW>(prm + S::D1, da1d, ddin);
+    float doe[2 * kL];
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+        const float dz = ddin[PI + l];
+        doe[l] = live ? dz + oe[l] * invB : 0.0f;
+        doe[kL + l] = live ? dz * eps[l] * 0.5f * sd_e[l] + 0.5f * (sd_e[l] * sd_e[l] - 1.0f) * invB : 0.0f;
+    }
+    float da2e[kW], da1e[kW];
+    bwd_layer<kW, 2 * kL>(prm + S::E3, doe, dh);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) da2e[o] = dh[o] * sigmoidf_fast(a2e[o]);
+    bwd_layer<kW, kW>(prm + S::E2, da2e, dh);
+#pragma unroll
+    for (int o = 0; o < kW; ++o) da1e[o] = dh[o] * sigmoidf_fast(a1e[o]);
+
+    // ---------------- stage layer inputs and deltas ----------------
+    const float m = live ? 1.0f : 0.0f;
+#pragma unroll
+    for (int k = 0; k < S::IE; ++k) row(S::IN1E, t)[k] = xin[k] * m;
+#pragma unroll
+    for (int k = 0; k < kW; ++k) {
+        row(S::H1E, t)[k] = h1e[k] * m;
+        row(S::H2E, t)[k] = h2e[k] * m;
+        row(S::H1D, t)[k] = h1d[k] * m;
+        row(S::H2D, t)[k] = h2d[k] * m;
+        row(S::DA1E, t)[k] = da1e[k];
+        row(S::DA2E, t)[k] = da2e[k];
+        row(S::DA1D, t)[k] = da1d[k];
+        row(S::DA2D, t)[k] = da2d[k];
+    }
+#pragma unroll
+    for (int k = 0; k < S::ID; ++k) row(S::IN1D, t)[k] = din[k] * m;
+#pragma unroll
+    for (int k = 0; k < 2 * kL; ++k) row(S::DOE, t)[k] = doe[k];
+#pragma unroll
+    for (int k = 0; k < 2 * PO; ++k) row(S::DY, t)[k] = dy[k];
+    // loss partials (fixed-order warp and block sums)
+    rec *= m;
+    kl *= m;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        rec += __shfl_xor_sync(0xffffffffu, rec, off);
+        kl += __shfl_xor_sync(0xffffffffu, kl, off);
+    }
+    if ((t & 31) == 0) { s_rec[t >> 5] = rec; s_kl[t >> 5] = kl; }
+    __syncthreads();
+
+    // ---------------- block gradient: one thread per parameter, samples in order ----------------
+    float* out = partial + (size_t)blockIdx.x * (S::NP + 2);
+    for (int p = t; p < S::NP; p += kSamples) {
+        int dslot, islot, K, base, O;
+        if (p < S::e1) { dslot = S::DA1E; islot = S::IN1E; K = S::IE; base = S::E1; O = kW; }
+        else if (p < S::E2) { dslot = S::DA1E; islot = -1; K = 1; base = S::e1; O = kW; }
+        else if (p < S::e2) { dslot = S::DA2E; islot = S::H1E; K = kW; base = S::E2; O = kW; }
+        else if (p < S::E3) { dslot = S::DA2E; islot = -1; K = 1; base = S::e2; O = kW; }
+        else if (p < S::e3) { dslot = S::DOE; islot = S::H2E; K = kW; base = S::E3; O = 2 * kL; }
+        else if (p < S::D1) { dslot = S::DOE; islot = -1; K = 1; base = S::e3; O = 2 * kL; }
+        else if (p < S::d1) { dslot = S::DA1D; islot = S::IN1D; K = S::ID; base = S::D1; O = kW; }
+        else if (p < S::D2) { dslot = S::DA1D; islot = -1; K = 1; base = S::d1; O = kW; }
+        else if (p < S::d2) { dslot = S::DA2D; islot = S::H1D; K = kW; base = S::D2; O = kW; }
+        else if (p < S::D3) { dslot = S::DA2D; islot = -1; K = 1; base = S::d2; O = kW; }
+        else if (p < S::d3) { dslot = S::DY; islot = S::H2D; K = kW; base = S::D3; O = 2 * PO; }
+        else { dslot = S::DY; islot = -1; K = 1; base = S::d3; O = 2 * PO; }
+        (void)O;
+        const int q = p - base;
+        const int o = islot >= 0 ? q / K : q;
+        const int k = islot >= 0 ? q - o * K : 0;
+        const float* dcol = row(dslot, 0) + o;
+        float acc = 0.0f;
+        if (islot >= 0) {
+            const float* icol = row(islot, 0) + k;
+#pragma unroll 8
+            for (int s = 0; s < kSamples; ++s) acc = fmaf(dcol[s * S::R], icol[s * S::R], acc);
+        } else {
+#pragma unroll 8
+            for (int s = 0; s < kSamples; ++s) acc += dcol[s * S::R];
+        }
+        out[p] = acc;
+    }
+    if (t == 0) {
+        float r = 0.0f, k = 0.0f;
+        for (int w = 0; w < kSamples / 32; ++w) { r += s_rec[w]; k += s_kl[w]; }
+        out[S::NP] = r;
+        out[S::NP + 1] = k;
+    }
+}
+
+// grad[p] = sum over blocks of partial[blk][p] in block order; loss3 = (rec + kl, rec, kl) / B.
+__global__ void reduce_partials(const float* __restrict__ partial, int nblk, int np, uint64_t B,
+                                float* __restrict__ grad, float* __restrict__ loss3)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np + 2) return;
+    float acc = 0.0f;
+    for (int blk = 0; blk < nblk; ++blk) acc += partial[(size_t)blk * (np + 2) + p];
+    if (p < np) {
+        if (grad) grad[p] = acc;
+    } else if (loss3) {
+        const float v = acc / (float)B;
+        if (p == np) { loss3[1] = v; } else { loss3[2] = v; }
+    }
+}
+
+__global__ void finish_loss(float* loss3)
+{
+    if (threadIdx.x == 0 && loss3) loss3[0] = loss3[1] + loss3[2];
+}
+
+__global__ void adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                     const float* __restrict__ g, uint64_t n, float lr, float b1, float b2, float eps, float wd,
+                     float c1, float c2)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float w = p[i];
+    if (wd != 0.0f) w = w - lr * wd * w;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] = w - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+struct Plan {
+    int np = 0;
+    cudaError_t (*launch)(const float*, const float*, const float*, const float*, uint64_t, uint64_t, uint64_t,
+                          float*, cudaStream_t) = nullptr;
+};
+
+template <int PI, int PO>
+cudaError_t launch_fb(const float* prm, const float* X, const float* C, const float* E, uint64_t B, uint64_t seed,
+                      uint64_t step, float* partial, cudaStream_t s)
+{
+    using S = Shape<PI, PO>;
+    const size_t smem = (size_t)S::NSLOT * kSamples * S::R * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned nblk = (unsigned)((B + kSamples - 1) / kSamples);
+    fwd_bwd<PI, PO><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
+    return cudaGetLastError();
+}
+
+#define MS_TRAIN_SHAPES(X) X(1, 1) X(2, 1) X(3, 3) X(4, 1) X(4, 3) X(4, 6) X(7, 6)
+
+Plan plan_for(const ms_cvae_shape& sh)
+{
+    Plan pl;
+    if (sh.latent != kL || sh.width != kW) return pl;
+#define MS_CASE(pi, po)                                                                                        \
+    if (sh.p_in == pi && sh.p_out == po) {                                                                    \
+        pl.np = Shape<pi, po>::NP;                                                                            \
+        pl.launch = launch_fb<pi, po>;                                                                        \
+    }
+    MS_TRAIN_SHAPES(MS_CASE)
+#undef MS_CASE
+    return pl;
+}
+
+}  // namespace train
+}  // namespace ms
+
+using namespace ms::train;
+
+extern "C" size_t ms_cvae_num_params(const ms_cvae_shape* s)
+{
+    if (!s) return 0;
+    const size_t W = (size_t)s->width, L = (size_t)s->latent, PI = (size_t)s->p_in, PO = (size_t)s->p_out;
+    const size_t enc = W * (PO + PI) + W + W * W + W + 2 * L * W + 2 * L;
+    const size_t dec = W * (PI + L) + W + W * W + W + 2 * PO * W + 2 * PO;
+    return enc + dec;
+}
+
+extern "C" size_t ms_cvae_workspace_size(const ms_cvae_shape* s, uint64_t batch)
+{
+    if (!s) return 0;
+    const size_t nblk = (size_t)((batch + kSamples - 1) / kSamples);
+    const size_t np = ms_cvae_num_params(s);
+    const size_t partial = nblk * (np + 2) * sizeof(float);
+    const size_t grad = np * sizeof(float);
+    return ((partial + 255) & ~(size_t)255) + ((grad + 255) & ~(size_t)255);
+}
+
+static ms_status check_shape(const ms_cvae_shape* s, const char* fn, Plan* out)
+{
+    if (!s) return ms::set_error(MS_ERR_INVALID_ARG, "%s: null shape", fn);
+    if (s->precision != MS_FP32)
+        return ms::set_error(MS_ERR_UNSUPPORTED, "%s: only MS_FP32 training is built", fn);
+    *out = plan_for(*s);
+    if (!out->launch)
+        return ms::set_error(MS_ERR_UNSUPPORTED,
+                             "%s: shape (p_in %d, p_out %d, latent %d, width %d) is not built; built: latent 4, "
+                             "width 16, (p_in, p_out) in (1,1) (2,1) (3,3) (4,1) (4,3) (4,6) (7,6)",
+                             fn, s->p_in, s->p_out, s->latent, s->width);
+    return MS_OK;
+}
+
+extern "C" ms_status ms_cvae_forward_backward(const ms_cvae_shape* s, const float* params, const float* x,
+                                              const float* c, const float* eps_z, uint64_t B, uint64_t seed,
+                                              uint64_t step, float* grad, float* loss3, void* workspace,
+                                              size_t workspace_bytes, void* stream)
+{
+    Plan pl;
+    ms_status st = check_shape(s, "ms_cvae_forward_backward", &pl);
+    if (st != MS_OK) return st;
+    MS_CHECK_ARG(B >= 1 && B < (1ull << 32), "ms_cvae_forward_backward: batch must be in [1, 2^32)");
+    MS_CHECK_ARG(params && x && c, "ms_cvae_forward_backward: null params, x or c");
+    MS_CHECK_ARG(workspace && workspace_bytes >= ms_cvae_workspace_size(s, B),
+                 "ms_cvae_forward_backward: workspace of at least %zu bytes required", ms_cvae_workspace_size(s, B));
+    MS_CHECK_ARG(((uintptr_t)workspace & 255u) == 0, "ms_cvae_forward_backward: workspace must be 256-byte aligned");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    float* partial = static_cast<float*>(workspace);
+    const int nblk = (int)((B + kSamples - 1) / kSamples);
+    MS_CUDA(pl.launch(params, x, c, eps_z, B, seed, step, partial, cs));
+    const int n = pl.np + 2;
+    reduce_partials<<<(n + 127) / 128, 128, 0, cs>>>(partial, nblk, pl.np, B, grad, loss3);
+    MS_CUDA(cudaGetLastError());
+    finish_loss<<<1, 32, 0, cs>>>(loss3);
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
+}
+
+extern "C" ms_status ms_adam_step(float* params, float* m, float* v, const float* grad, uint64_t n, uint64_t t,
+                                  float lr, float beta1, float beta2, float eps, float weight_decay, void* stream)
+{
+    MS_CHECK_ARG(params && m && v && grad, "ms_adam_step: null array");
+    MS_CHECK_ARG(t >= 1, "ms_adam_step: step t must be >= 1");
+    if (n == 0) return MS_OK;
+    const float c1 = (float)(1.0 - std::pow((double)beta1, (double)t));
+    const float c2 = (float)(1.0 - std::pow((double)beta2, (double)t));
+    adam<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(params, m, v, grad, n, lr, beta1,
+                                                                                    beta2, eps, weight_decay, c1, c2);
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
+}
+
+extern "C" ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, float* m, float* v, const float* x,
+                                        const float* c, const float* eps_z, uint64_t B, uint64_t seed, uint64_t step,
+                                        float lr, float weight_decay, float* loss3, void* workspace,
+                                        size_t workspace_bytes, void* stream)
+{
+    Plan pl;
+    ms_status st = check_shape(s, "ms_cvae_train_step", &pl);
+    if (st != MS_OK) return st;
+    MS_CHECK_ARG(step >= 1, "ms_cvae_train_step: step must be >= 1");
+    MS_CHECK_ARG(B >= 1 && B < (1ull << 32), "ms_cvae_train_step: batch must be in [1, 2^32)");
+    MS_CHECK_ARG(workspace && workspace_bytes >= ms_cvae_workspace_size(s, B),
+                 "ms_cvae_train_step: workspace of at least %zu bytes required", ms_cvae_workspace_size(s, B));
+    const size_t nblk = (size_t)((B + kSamples - 1) / kSamples);
+    const size_t partial_bytes = ((nblk * (pl.np + 2) * sizeof(float)) + 255) & ~(size_t)255;
+    float* grad = reinterpret_cast<float*>(static_cast<char*>(workspace) + partial_bytes);
+    st = ms_cvae_forward_backward(s, params, x, c, eps_z, B, seed, step, grad, loss3, workspace, workspace_bytes,
+                                  stream);
+    if (st != MS_OK) return st;
+    return ms_adam_step(params, m, v, grad, (uint64_t)pl.np, step, lr, 0.9f, 0.999f, 1e-8f, weight_decay, stream);
+}

@@ -1,0 +1,126 @@
+// ms_cvae_infer: batched CVAE decoder sampling (Sec. 3.2) — x = mu + exp(log Sigma / 2) eps with
+// (mu, log Sigma) = Dec([c; z]) and z, eps standard normal.
+//
+// Single precision: one query per thread over a grid-stride loop; the block stages the decoder weights in
+// shared memory once (decoder.cuh); z and eps are read from the caller or drawn in registers from the query's
+// Philox counter.  Half precision (FP16/BF16 with FP32 accumulation) is decoder_mma.cu.
+#include "decoder.cuh"
+
+namespace ms {
+namespace dec {
+
+constexpr int kInferThreads = 256;
+
+template <int IN4, int P>
+__global__ void __launch_bounds__(kInferThreads, 2) infer_f32(const float* __restrict__ wts, int p_in, int latent,
+                                                              const float* __restrict__ cond,
+                                                              const float* __restrict__ z_eps, uint64_t seed,
+                                                              uint64_t offset, uint64_t n, float* __restrict__ mlv,
+                                                              float* __restrict__ smp)
+{
+    __shared__ __align__(16) float s[smem_floats(IN4, P)];
+    // per-thread staging row: [c ; z] in the first IN4 entries, then eps (dynamic offsets stay in shared memory)
+    __shared__ __align__(16) float row[kInferThreads][IN4 + 8];
+    stage_weights(s, wts, p_in + latent, IN4, P);
+    __syncthreads();
+    float* my = row[threadIdx.x];
+    const int nz = latent + P;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+#pragma unroll
+        for (int k = 0; k < IN4 + 8; ++k) my[k] = 0.0f;
+        for (int k = 0; k < p_in; ++k) my[k] = cond[q * p_in + k];
+        if (z_eps) {
+            for (int m = 0; m < nz; ++m) my[m < latent ? p_in + m : IN4 + m - latent] = z_eps[q * nz + m];
+        } else {
+            const Stream st(seed, offset + q);
+            for (int j = 0; 4 * j < nz; ++j) {
+                const float4 v = normals4(st, (uint32_t)j, 0xD0u);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int m = 4 * j + t;
+                    if (m < nz) my[m < latent ? p_in + m : IN4 + m - latent] = vv[t];
+                }
+            }
+        }
+        float x[IN4];
+#pragma unroll
+        for (int k = 0; k < IN4; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(my + k);
+            x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
+        }
+        float y[pad4(2 * P)];
+        mlp<IN4, P>(s, x, y);
+        if (mlv) {
+#pragma unroll
+            for (int o = 0; o < 2 * P; ++o) mlv[q * (2 * P) + o] = y[o];
+        }
+        if (smp) {
+#pragma unroll
+            for (int o = 0; o < P; ++o) smp[q * P + o] = y[o] + __expf(0.5f * y[P + o]) * my[IN4 + o];
+        }
+    }
+}
+
+template <int IN4, int P>
+cudaError_t launch_f32(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
+                       uint64_t n, float* mlv, float* smp, cudaStream_t stream)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_f32<IN4, P>, kInferThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (n + kInferThreads - 1) / kInferThreads;
+    if (grid > need) grid = need;
+    infer_f32<IN4, P><<<(unsigned)grid, kInferThreads, 0, stream>>>(d.weights, d.p_in, d.latent, cond, z_eps, seed,
+                                                                    offset, n, mlv, smp);
+    return cudaGetLastError();
+}
+
+template <int IN4>
+cudaError_t dispatch_p(const ms_decoder& d, const float* c, const float* z, uint64_t seed, uint64_t off, uint64_t n,
+                       float* mlv, float* smp, cudaStream_t s)
+{
+    switch (d.p_out) {
+    case 1: return launch_f32<IN4, 1>(d, c, z, seed, off, n, mlv, smp, s);
+    case 2: return launch_f32<IN4, 2>(d, c, z, seed, off, n, mlv, smp, s);
+    case 3: return launch_f32<IN4, 3>(d, c, z, seed, off, n, mlv, smp, s);
+    case 4: return launch_f32<IN4, 4>(d, c, z, seed, off, n, mlv, smp, s);
+    case 5: return launch_f32<IN4, 5>(d, c, z, seed, off, n, mlv, smp, s);
+    case 6: return launch_f32<IN4, 6>(d, c, z, seed, off, n, mlv, smp, s);
+    case 7: return launch_f32<IN4, 7>(d, c, z, seed, off, n, mlv, smp, s);
+    default: return launch_f32<IN4, 8>(d, c, z, seed, off, n, mlv, smp, s);
+    }
+}
+
+}  // namespace dec
+}  // namespace ms
+
+extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const float* z_eps, uint64_t seed,
+                                   uint64_t offset, uint64_t n, float* out_mean_logvar, float* out_sample,
+                                   void* stream)
+{
+    MS_CHECK_ARG(d != nullptr && d->weights != nullptr, "ms_cvae_infer: null decoder or weights");
+    MS_CHECK_ARG(d->width == 16, "ms_cvae_infer: width must be 16 (got %d)", d->width);
+    MS_CHECK_ARG(d->p_in >= 1 && d->latent >= 1 && d->latent <= 8 && d->p_in + d->latent <= 16,
+                 "ms_cvae_infer: need 1 <= p_in, 1 <= latent <= 8, p_in + latent <= 16");
+    MS_CHECK_ARG(d->p_out >= 1 && d->p_out <= 8, "ms_cvae_infer: p_out must be in 1..8");
+    MS_CHECK_ARG(d->precision == MS_FP32 || d->precision == MS_FP16 || d->precision == MS_BF16,
+                 "ms_cvae_infer: precision must be MS_FP32, MS_FP16 or MS_BF16");
+    MS_CHECK_ARG(n == 0 || cond != nullptr, "ms_cvae_infer: cond is null");
+    if (n == 0 || (out_mean_logvar == nullptr && out_sample == nullptr)) return MS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d->precision != MS_FP32)
+        return ms::set_error(MS_ERR_UNSUPPORTED, "ms_cvae_infer: half-precision decoders are not built yet");
+    const int in4 = ms::dec::pad4(d->p_in + d->latent);
+    cudaError_t e;
+    switch (in4) {
+    case 4: e = ms::dec::dispatch_p<4>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
+    case 8: e = ms::dec::dispatch_p<8>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
+    case 12: e = ms::dec::dispatch_p<12>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
+    default: e = ms::dec::dispatch_p<16>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
+    }
+    MS_CUDA(e);
+    return MS_OK;
+}

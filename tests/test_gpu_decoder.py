@@ -1,0 +1,83 @@
+"""GPU parity of ms_cvae_infer (Sec. 3.2 decoder) against the FP64 oracle decoder.
+
+Tolerances: FP32 max |error| <= 1e-5 on the decoder outputs when z and eps are given (the arithmetic of the
+kernel alone); <= 1e-4 when the kernel draws z and eps from its Philox stream (single-precision Box-Muller
+against the oracle's double-precision Box-Muller on the same words)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cvae
+from paper_2011_03082_b300 import ms, synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4, 1), (4, 6), (2, 1), (3, 3), (7, 6), (1, 8), (12, 2)]
+
+
+def _run(w, p_in, p_out, cond, n, z_eps=None, seed=7, offset=0, latent=4):
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    wt, ct = dev(w), dev(cond)
+    ze = dev(z_eps) if z_eps is not None else None
+    mlv = torch.zeros(n, 2 * p_out, device="cuda")
+    smp = torch.zeros(n, p_out, device="cuda")
+    d = ms.decoder_struct(wt, p_in, p_out, latent=latent)
+    ms.ms_cvae_infer(d, ct, n, z_eps=ze, seed=seed, offset=offset, out_mean_logvar=mlv, out_sample=smp)
+    torch.cuda.synchronize()
+    return mlv.cpu().numpy(), smp.cpu().numpy()
+
+
+@pytest.mark.parametrize("p_in,p_out", SHAPES)
+@pytest.mark.parametrize("n", [1, 1000, 65539])
+def test_decoder_given_normals(p_in, p_out, n):
+    shape = cvae.Shape(p_in, p_out)
+    w = synth.xavier_decoder(7, p_in, p_out)
+    w = w + np.float32(0.05) * synth.standard_normals(8, w.shape)   # nonzero biases too
+    rng = np.random.default_rng(1)
+    cond = rng.uniform(-1, 2, (n, p_in)).astype(np.float32)
+    ze = synth.standard_normals(2, (n, 4 + p_out))
+    mlv, smp = _run(w, p_in, p_out, cond, n, ze)
+    mu, lv = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :4])
+    assert np.abs(mlv[:, :p_out] - mu).max() <= 1e-5
+    assert np.abs(mlv[:, p_out:] - lv).max() <= 1e-5
+    ref = mu + np.exp(0.5 * lv) * ze[:, 4:]
+    assert np.abs(smp - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("p_in,p_out", [(4, 1), (4, 6)])
+def test_decoder_philox_normals(orc, p_in, p_out):
+    n, offset = 5000, 123456
+    w = synth.xavier_decoder(7, p_in, p_out)
+    cond = synth.decoder_queries(7, n)[:, :p_in]
+    mlv, smp = _run(w, p_in, p_out, cond, n, None, seed=7, offset=offset)
+    nz = orc.decoder_normals(7, offset, n, 4 + p_out)
+    shape = cvae.Shape(p_in, p_out)
+    mu, lv = cvae.decoder_forward(w.astype(np.float64), shape, cond, nz[:, :4])
+    assert np.abs(mlv[:, :p_out] - mu).max() <= 1e-4
+    ref = mu + np.exp(0.5 * lv) * nz[:, 4:]
+    assert np.abs(smp - ref).max() <= 1e-4
+
+
+def test_decoder_full_size_sampled(orc):
+    """The 2^22-query configuration (condition [log tau, g, albedo, cos] + z of dim 4, P_out 6): sampled
+    queries recomputed by the oracle."""
+    n, p_in, p_out = 1 << 22, 4, 6
+    w = synth.xavier_decoder(7, p_in, p_out)
+    cond = synth.decoder_queries(7, n)
+    mlv, smp = _run(w, p_in, p_out, cond, n, None, seed=7)
+    idx = np.random.default_rng(3).choice(n, 2000, replace=False)
+    idx.sort()
+    nz = np.concatenate([orc.decoder_normals(7, int(i), 1, 10) for i in idx])
+    mu, lv = cvae.decoder_forward(w.astype(np.float64), cvae.Shape(p_in, p_out), cond[idx], nz[:, :4])
+    assert np.abs(mlv[idx, :p_out] - mu).max() <= 1e-4
+    assert np.all(np.isfinite(smp))
+
+
+def test_decoder_rejects_bad_shapes():
+    w = torch.zeros(1000, device="cuda")
+    c = torch.zeros(4, 4, device="cuda")
+    out = torch.zeros(4, 2, device="cuda")
+    for kw in (dict(p_in=4, p_out=9), dict(p_in=13, p_out=1), dict(p_in=4, p_out=1, width=8)):
+        d = ms.decoder_struct(w, kw["p_in"], kw["p_out"], width=kw.get("width", 16))
+        with pytest.raises(ms.MsError):
+            ms.ms_cvae_infer(d, c, 4, out_mean_logvar=out)

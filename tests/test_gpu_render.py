@@ -1,0 +1,120 @@
+"""GPU parity of ms_render / ms_render_batch against the oracle renderer (Sec. 3, 4.1, 4.3, Eq. 5).
+
+The GPU renders in single precision on the same Philox stream as the FP64 oracle, so paths coincide except
+where a single-precision decision flips.  Acceptance (image RMSE within 1% of the oracle's own sampling
+noise): with oracle images O1 (seed 1) and O2 (seed 2) and the GPU image G2 (seed 2),
+|RMSE(G2, O1) / RMSE(O2, O1) - 1| <= 0.01, and G2 is much closer to O2 than O2 is to O1."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2011_03082_b300 import ms, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _models():
+    out = {}
+    for i, (name, (p_in, p_out)) in enumerate(synth.MODEL_SHAPES.items()):
+        out[name] = (synth.xavier_decoder(100 + i, p_in, p_out), p_in, p_out)
+    return out
+
+
+def gpu_render(params, models=None):
+    img = torch.zeros(params["height"], params["width"], dtype=torch.float64, device="cuda")
+    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    cs = None
+    keep = []
+    if models is not None:
+        dm = {}
+        for k, (w, pi, po) in models.items():
+            t = torch.from_numpy(w).cuda()
+            keep.append(t)
+            dm[k] = (t, pi, po)
+        cs = ms.cvae_set(dm)
+    ms.ms_render(ms.render_params(params), cs, img, st)
+    torch.cuda.synchronize()
+    return img.cpu().numpy(), st.cpu().numpy()
+
+
+def oracle_render(orc, params, models=None):
+    decs = None
+    if models is not None:
+        decs = [(models[k][0].astype(np.float64), models[k][1], models[k][2]) for k in ("length", "path", "event")]
+    img, st, _ = orc.render(params, decs)
+    return img, st
+
+
+def rmse(a, b):
+    return float(np.sqrt(np.mean((a - b) ** 2)))
+
+
+CASES = [("brute_16", 16.0, 0), ("brute_64", 64.0, 0), ("sphere_64", 64.0, 1), ("sphere_16", 16.0, 1)]
+
+
+@pytest.mark.parametrize("name,sigma,mode", CASES, ids=[c[0] for c in CASES])
+def test_render_matches_oracle(orc, name, sigma, mode):
+    models = _models() if mode == 1 else None
+    p1 = synth.render_scene(sigma, width=32, height=32, spp=16, mode=mode, seed=1)
+    p2 = dict(p1, seed=2)
+    o1, _ = oracle_render(orc, p1, models)
+    o2, s2 = oracle_render(orc, p2, models)
+    g2, gs = gpu_render(p2, models)
+    noise = rmse(o2, o1)
+    assert noise > 0
+    assert abs(rmse(g2, o1) / noise - 1.0) <= 0.01, (rmse(g2, o1), noise)
+    assert rmse(g2, o2) <= 0.2 * noise, (rmse(g2, o2), noise)
+    assert gs[0] == s2[0] == 32 * 32 * 16
+    assert abs(int(gs[1]) - int(s2[1])) <= 0.002 * s2[1]
+    for k in (2, 3, 4, 7):
+        assert abs(int(gs[k]) - int(s2[k])) <= 0.01 * max(s2[k], 100), (k, gs[k], s2[k])
+
+
+def test_zero_albedo_is_black():
+    img, st = gpu_render(synth.render_scene(16.0, width=16, height=16, spp=4, mode=0, albedo=0.0))
+    assert st[4] > 0 and np.all(img == 0.0)
+
+
+def test_sample_offsets_and_batches_compose():
+    models = _models()
+    full = synth.render_scene(32.0, width=24, height=16, spp=8, mode=1, seed=3)
+    a, sa = gpu_render(full, models)
+    h1, s1 = gpu_render(dict(full, spp=4), models)
+    h2, s2 = gpu_render(dict(full, spp=4, sample_offset=4), models)
+    assert np.allclose(a, h1 + h2, rtol=1e-9, atol=1e-12) and np.array_equal(sa, s1 + s2)
+    # three requests in one persistent launch equal the three single renders
+    reqs = [full, synth.render_scene(8.0, width=8, height=8, spp=3, mode=0, seed=4),
+            synth.render_scene(128.0, width=5, height=7, spp=2, mode=1, seed=5, disp_freq=3.0)]
+    singles = [gpu_render(r, models) for r in reqs]
+    npx = sum(r["width"] * r["height"] for r in reqs)
+    imgs = torch.zeros(npx, dtype=torch.float64, device="cuda")
+    st = torch.zeros(len(reqs), 8, dtype=torch.int64, device="cuda")
+    dm = {k: (torch.from_numpy(w).cuda(), pi, po) for k, (w, pi, po) in models.items()}
+    ms.ms_render_batch([ms.render_params(r) for r in reqs], ms.cvae_set(dm), imgs, st)
+    torch.cuda.synchronize()
+    off = 0
+    for i, (r, (img, s)) in enumerate(zip(reqs, singles)):
+        n = r["width"] * r["height"]
+        assert np.allclose(imgs[off:off + n].cpu().numpy(), img.ravel(), rtol=1e-9, atol=1e-12)
+        assert np.array_equal(st[i].cpu().numpy(), s)
+        off += n
+
+
+def test_full_size_render_properties():
+    """512 x 512 pixels, 256 samples per pixel, sigma_t 64, sphere tracing with decoders."""
+    p = synth.render_scene(64.0, mode=1)
+    img, st = gpu_render(p, _models())
+    assert st[0] == 512 * 512 * 256
+    assert np.all(np.isfinite(img)) and np.all(img >= 0) and img.sum() > 0
+    assert st[3] > 0 and st[7] <= st[3] + st[4]
+
+
+def test_bad_requests_are_rejected():
+    img = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    for bad in (dict(sigma_t=0.0), dict(g=1.0), dict(albedo=1.5), dict(width=0), dict(mode=5)):
+        p = dict(synth.render_scene(8.0, width=2, height=2, spp=1, mode=0), **bad)
+        with pytest.raises(ms.MsError):
+            ms.ms_render(ms.render_params(p), None, img, st)
+    with pytest.raises(ms.MsError, match="decoders"):
+        ms.ms_render(ms.render_params(synth.render_scene(8.0, width=2, height=2, spp=1, mode=1)), None, img, st)

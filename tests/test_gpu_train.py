@@ -1,0 +1,115 @@
+"""GPU parity of the hand-written CVAE training (Sec. 3.2) against the FP64 oracle: loss terms, gradients,
+Adam, determinism, and the loss curve of 20 steps."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cvae
+from paper_2011_03082_b300 import ms, synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(2, 1), (3, 3), (7, 6), (4, 6)]
+
+
+def _data(p_in, p_out, B, seed):
+    rng = np.random.default_rng(seed)
+    p = synth.xavier_cvae(seed, p_in, p_out)
+    p = (p + 0.05 * rng.standard_normal(p.size)).astype(np.float32)
+    x = rng.standard_normal((B, p_out)).astype(np.float32)
+    c = rng.standard_normal((B, p_in)).astype(np.float32)
+    e = rng.standard_normal((B, 4)).astype(np.float32)
+    return p, x, c, e
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("p_in,p_out", SHAPES)
+@pytest.mark.parametrize("B", [1, 300, 4096])
+def test_loss_and_gradient_match_oracle(p_in, p_out, B):
+    p, x, c, e = _data(p_in, p_out, B, 1)
+    shape = ms.cvae_shape(p_in, p_out)
+    grad = torch.zeros(p.size, device="cuda")
+    loss3 = torch.zeros(3, device="cuda")
+    ms.ms_cvae_forward_backward(shape, _dev(p), _dev(x), _dev(c), B, eps_z=_dev(e), grad=grad, loss3=loss3)
+    torch.cuda.synchronize()
+    loss, rec, kl, g = cvae.neg_elbo_grad(p.astype(np.float64), cvae.Shape(p_in, p_out), x, c, e)
+    l3 = loss3.cpu().numpy()
+    assert np.allclose(l3, [loss, rec, kl], rtol=1e-4, atol=1e-5)
+    gg = grad.cpu().numpy()
+    scale = np.abs(g).max()
+    assert np.abs(gg - g).max() <= 1e-4 * scale, np.abs(gg - g).max() / scale
+
+
+def test_gradient_is_deterministic():
+    p_in, p_out, B = 7, 6, 65536
+    p, x, c, _ = _data(p_in, p_out, B, 2)
+    shape = ms.cvae_shape(p_in, p_out)
+    outs = []
+    for _ in range(2):
+        grad = torch.zeros(p.size, device="cuda")
+        loss3 = torch.zeros(3, device="cuda")
+        ms.ms_cvae_forward_backward(shape, _dev(p), _dev(x), _dev(c), B, seed=3, step=5, grad=grad, loss3=loss3)
+        torch.cuda.synchronize()
+        outs.append((grad.cpu().numpy(), loss3.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_philox_eps_matches_oracle_normals(orc):
+    p_in, p_out, B, step = 3, 3, 2000, 9
+    p, x, c, _ = _data(p_in, p_out, B, 4)
+    shape = ms.cvae_shape(p_in, p_out)
+    grad = torch.zeros(p.size, device="cuda")
+    loss3 = torch.zeros(3, device="cuda")
+    ms.ms_cvae_forward_backward(shape, _dev(p), _dev(x), _dev(c), B, seed=11, step=step, grad=grad, loss3=loss3)
+    torch.cuda.synchronize()
+    # normals of sample b: counter (0, b, step, 0xE0): id = (step << 32) | b
+    e = orc.normals_from_words(orc.philox_words(11, step << 32, B, 0, 0xE0))
+    loss, rec, kl, g = cvae.neg_elbo_grad(p.astype(np.float64), cvae.Shape(p_in, p_out), x, c, e)
+    assert np.allclose(loss3.cpu().numpy(), [loss, rec, kl], rtol=1e-4, atol=1e-5)
+    assert np.abs(grad.cpu().numpy() - g).max() <= 1e-3 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("wd", [0.0, 0.01])
+def test_adam_matches_oracle(wd):
+    rng = np.random.default_rng(5)
+    n = 1300
+    p0 = rng.standard_normal(n).astype(np.float32)
+    pt, mt, vt = _dev(p0.copy()), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    p, m, v = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for t in range(1, 6):
+        g = rng.standard_normal(n).astype(np.float32)
+        ms.ms_adam_step(pt, mt, vt, _dev(g), t, 1e-3, weight_decay=wd)
+        p, m, v = cvae.adam_step(p, m, v, g.astype(np.float64), t, 1e-3, weight_decay=wd)
+    torch.cuda.synchronize()
+    assert np.abs(pt.cpu().numpy() - p).max() <= 1e-6
+
+
+def test_training_loss_curve_matches_oracle():
+    """20 Adam steps on a 1,024-sample batch with given eps: the GPU and oracle loss curves agree."""
+    p_in, p_out, B = 3, 3, 1024
+    p, x, c, _ = _data(p_in, p_out, B, 6)
+    rng = np.random.default_rng(7)
+    shape = ms.cvae_shape(p_in, p_out)
+    pt, mt, vt = _dev(p.copy()), torch.zeros(p.size, device="cuda"), torch.zeros(p.size, device="cuda")
+    po, mo, vo = p.astype(np.float64), np.zeros(p.size), np.zeros(p.size)
+    loss3 = torch.zeros(3, device="cuda")
+    gl, ol = [], []
+    for t in range(1, 21):
+        e = rng.standard_normal((B, 4)).astype(np.float32)
+        ms.ms_cvae_train_step(shape, pt, mt, vt, _dev(x), _dev(c), B, eps_z=_dev(e), step=t, lr=1e-2, loss3=loss3)
+        gl.append(float(loss3[0]))
+        loss, _, _, g = cvae.neg_elbo_grad(po, cvae.Shape(p_in, p_out), x, c, e)
+        po, mo, vo = cvae.adam_step(po, mo, vo, g, t, 1e-2)
+        ol.append(loss)
+    assert np.allclose(gl, ol, rtol=2e-3), (gl, ol)
+    assert gl[-1] < gl[0]
+
+
+def test_unsupported_shape_is_rejected():
+    shape = ms.cvae_shape(5, 5)
+    with pytest.raises(ms.MsError, match="not built"):
+        ms.ms_cvae_forward_backward(shape, torch.zeros(10, device="cuda"), torch.zeros(10, device="cuda"),
+                                    torch.zeros(10, device="cuda"), 2, ws=ms.workspace(1 << 20))
