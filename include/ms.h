@@ -214,14 +214,16 @@ typedef struct {
 size_t ms_render_workspace_size(const ms_render_params* reqs, int n_requests);
 
 /* image: device [height][width] doubles, accumulated: the sum over the pixel's samples (divide by spp).
- * stats: device [8] accumulated: camera paths, paths entering the object, flights, sphere steps, brute
- * events, absorbed, truncated paths or dropped estimates, next-event estimates.  models: host struct with
- * device weight pointers (ignored in MS_BRUTE). */
+ * stats: device [MS_RENDER_STATS] accumulated: camera paths, paths entering the object, flights, sphere
+ * steps, brute events, absorbed, truncated paths or dropped estimates, next-event estimates, SDF distance
+ * evaluations, SDF gradient evaluations, then zeros.  models: host struct with device weight pointers
+ * (ignored in MS_BRUTE). */
+#define MS_RENDER_STATS 16
 ms_status ms_render(const ms_render_params* p, const ms_cvae_set* models, double* image,
                     unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Many requests in one persistent launch.  reqs: host [n]; images: device, request i's [h][w] image starts
- * at the sum of the previous requests' h*w; stats: device [n][8]. */
+/* Many requests (1..64) in one persistent launch.  reqs: host [n]; images: device, request i's [h][w] image
+ * starts at the sum of the previous requests' h*w; stats: device [n][MS_RENDER_STATS]. */
 ms_status ms_render_batch(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
                           unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);
 

@@ -206,7 +206,7 @@ def _decoder_struct(wvec, p_in, p_out, latent=4, width=16):
 
 def render(params: dict, decoders=None, n_threads=0):
     """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out)
-    for LengthGen, PathGen, EventGen.  Returns (image_sum[h][w], stats[8], threads)."""
+    for LengthGen, PathGen, EventGen.  Returns (image_sum[h][w], stats[16], threads)."""
     P = RenderParams()
     for k, v in params.items():
         if isinstance(getattr(P, k), C.Array):
@@ -221,7 +221,7 @@ def render(params: dict, decoders=None, n_threads=0):
             decs[i] = d
             keep.append(arr)
     image = np.zeros((P.height, P.width), np.float64)
-    stats = np.zeros(8, np.uint64)
+    stats = np.zeros(16, np.uint64)
     nt = lib().om_render(C.byref(P), C.cast(decs, C.c_void_p), _ptr(image), _ptr(stats), n_threads)
     return image, stats, nt
 

@@ -71,13 +71,17 @@ static ov3 normalize(ov3 a) { return mul(a, 1.0 / sqrt(dot(a, a))); }
 /* ---- scene: displaced unit sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz), negative inside ---- */
 typedef struct { double A, k, lip, rb2; } scene;
 
+static _Thread_local uint64_t t_sdf_evals, t_grad_evals;
+
 static double sdf(const scene* S, ov3 p)
 {
+    t_sdf_evals += 1;
     return sqrt(dot(p, p)) - 1.0 - S->A * sin(S->k * p.x) * sin(S->k * p.y) * sin(S->k * p.z);
 }
 
 static ov3 sdf_grad(const scene* S, ov3 p)
 {
+    t_grad_evals += 1;
     double sx = sin(S->k * p.x), sy = sin(S->k * p.y), sz = sin(S->k * p.z);
     double cx = cos(S->k * p.x), cy = cos(S->k * p.y), cz = cos(S->k * p.z);
     double n = sqrt(dot(p, p));
@@ -438,7 +442,9 @@ static void* render_worker(void* arg)
     S.lip = 1.0 + P->disp_amp * P->disp_freq;
     double rb = 1.0 + P->disp_amp + 1e-3;
     S.rb2 = rb * rb;
-    uint64_t st[8] = { 0 };
+    uint64_t st[16] = { 0 };
+    t_sdf_evals = 0;
+    t_grad_evals = 0;
     for (;;) {
         pthread_mutex_lock(&J->lock);
         int py = J->next_row++;
@@ -452,17 +458,19 @@ static void* render_worker(void* arg)
             J->image[(size_t)py * P->width + px] += acc;
         }
     }
+    st[8] = t_sdf_evals;
+    st[9] = t_grad_evals;
     pthread_mutex_lock(&J->lock);
-    for (int k = 0; k < 8; ++k) J->stats[k] += st[k];
+    for (int k = 0; k < 16; ++k) J->stats[k] += st[k];
     pthread_mutex_unlock(&J->lock);
     return NULL;
 }
 
 /*
  * Render: image[h][w] accumulates the sum over the spp samples of each pixel (divide by spp for the mean).
- * stats[8]: camera paths, paths entering the object, flight segments, sphere steps, brute events,
+ * stats[16]: camera paths, paths entering the object, flight segments, sphere steps, brute events,
  * absorbed paths, truncated paths or dropped estimates (segment cap or march step cap), next-event
- * estimates.  Returns the number of threads used.
+ * estimates, SDF distance evaluations, SDF gradient evaluations, zeros.  Returns the number of threads used.
  */
 int om_render(const om_render_params* P, const om_decoder* dec3, double* image, uint64_t* stats, int n_threads)
 {

@@ -31,6 +31,7 @@ namespace render {
 
 constexpr int kThreads = 256;
 constexpr int kMaxReq = 64;
+constexpr int kStats = MS_RENDER_STATS;
 constexpr float kEps = 1e-4f;       // distance from the boundary treated as on it
 constexpr int kMaxMarch = 1024;     // sphere-tracing steps per march; running out ends the path
 constexpr float kNMax = 16777216.0f;
@@ -53,7 +54,7 @@ struct Batch {
     const float* wP;
     const float* wE;
     double* image;
-    unsigned long long* stats;   // [n][8]
+    unsigned long long* stats;   // [n][kStats]
     unsigned long long* ticket;
 };
 
@@ -71,14 +72,19 @@ __device__ __forceinline__ float dot(V a, V b) { return fmaf(a.x, b.x, fmaf(a.y,
 __device__ __forceinline__ V cross(V a, V b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
 __device__ __forceinline__ V unit(V a) { return a * rsqrtf(dot(a, a)); }
 
+// per-thread SDF evaluation counters (distance, gradient), flushed into the request's stats
+struct Evals { unsigned f, g; };
+
 // ---- the displaced sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz) (negative inside) ----
-__device__ __forceinline__ float sdf(const Req& q, V p)
+__device__ __forceinline__ float sdf(const Req& q, V p, Evals& ev)
 {
+    ++ev.f;
     return sqrtf(dot(p, p)) - 1.0f - q.A * __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z);
 }
 
-__device__ __forceinline__ V sdf_grad(const Req& q, V p)
+__device__ __forceinline__ V sdf_grad(const Req& q, V p, Evals& ev)
 {
+    ++ev.g;
     float sx, cx, sy, cy, sz, cz;
     __sincosf(q.k * p.x, &sx, &cx);
     __sincosf(q.k * p.y, &sy, &cy);
@@ -89,14 +95,14 @@ __device__ __forceinline__ V sdf_grad(const Req& q, V p)
 }
 
 // 1: collision at *c = p + l w; 0: crossed the boundary outward at *c; 2: step cap
-__device__ int march_inside(const Req& q, V p, V w, float l, V* c)
+__device__ int march_inside(const Req& q, V p, V w, float l, V* c, Evals& ev)
 {
     float t = 0.0f;
     for (int it = 0; it < kMaxMarch; ++it) {
         const V r = p + w * t;
-        float d = -sdf(q, r) / q.lip;
+        float d = -sdf(q, r, ev) / q.lip;
         if (d < kEps) {
-            if (dot(sdf_grad(q, r), w) > 0.0f) { *c = r; return 0; }
+            if (dot(sdf_grad(q, r, ev), w) > 0.0f) { *c = r; return 0; }
             d = kEps;
         }
         if (t + d >= l) { *c = p + w * l; return 1; }
@@ -106,15 +112,15 @@ __device__ int march_inside(const Req& q, V p, V w, float l, V* c)
 }
 
 // 1: re-entered at *c; 0: left the bounding sphere; 2: step cap
-__device__ int march_outside(const Req& q, V p, V w, V* c)
+__device__ int march_outside(const Req& q, V p, V w, V* c, Evals& ev)
 {
     float t = 0.0f;
     for (int it = 0; it < kMaxMarch; ++it) {
         const V r = p + w * t;
         if (dot(r, r) > q.rb2 && dot(r, w) >= 0.0f) return 0;
-        float d = sdf(q, r) / q.lip;
+        float d = sdf(q, r, ev) / q.lip;
         if (d < kEps) {
-            if (dot(sdf_grad(q, r), w) < 0.0f) { *c = r; return 1; }
+            if (dot(sdf_grad(q, r, ev), w) < 0.0f) { *c = r; return 1; }
             d = kEps;
         }
         t += d;
@@ -123,7 +129,7 @@ __device__ int march_outside(const Req& q, V p, V w, V* c)
 }
 
 // length of X -> light inside the medium (Sec. 4.3 d_t); negative when the step cap runs out
-__device__ float inside_length(const Req& q, V X, V xl)
+__device__ float inside_length(const Req& q, V X, V xl, Evals& ev)
 {
     const V dl = xl - X;
     const float D = sqrtf(dot(dl, dl));
@@ -133,11 +139,11 @@ __device__ float inside_length(const Req& q, V X, V xl)
     for (int it = 0; it < kMaxMarch; ++it) {
         if (t >= D) return din;
         const V r = X + w * t;
-        const float f = sdf(q, r);
+        const float f = sdf(q, r, ev);
         if (inside) {
             float d = -f / q.lip;
             if (d < kEps) {
-                if (dot(sdf_grad(q, r), w) > 0.0f) { inside = false; continue; }
+                if (dot(sdf_grad(q, r, ev), w) > 0.0f) { inside = false; continue; }
                 d = kEps;
             }
             const float step = fminf(d, D - t);
@@ -147,7 +153,7 @@ __device__ float inside_length(const Req& q, V X, V xl)
             if (dot(r, r) > q.rb2 && dot(r, w) >= 0.0f) return din;
             float d = f / q.lip;
             if (d < kEps) {
-                if (dot(sdf_grad(q, r), w) < 0.0f) { inside = true; continue; }
+                if (dot(sdf_grad(q, r, ev), w) < 0.0f) { inside = true; continue; }
                 d = kEps;
             }
             t += fminf(d, D - t);
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
     __shared__ int s_queue[kThreads];
     __shared__ int s_warp_count[kThreads / 32];
     __shared__ int s_nq;
-    __shared__ unsigned long long s_stats[kMaxReq * 8];
+    __shared__ unsigned long long s_stats[kMaxReq * kStats];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool learned = B.wL != nullptr;
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
         dec::stage_weights(wpth, B.wP, 3 + 4, kInP, kPP);
         dec::stage_weights(wev, B.wE, 7 + 4, kInE, kPE);
     }
-    for (int k = tid; k < kMaxReq * 8; k += kThreads) s_stats[k] = 0ull;
+    for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     __syncthreads();
 
     // slot state (owned by this thread)
@@ -251,9 +257,16 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
     V p = v3(0, 0, 0), w = v3(0, 0, 1);
     double acc = 0.0;
     bool drained = false;   // warp-uniform
+    Evals ev{0u, 0u};
 
-    auto stat = [&](int r, int k, unsigned long long v) { atomicAdd(&s_stats[r * 8 + k], v); };
+    auto stat = [&](int r, int k, unsigned long long v) { atomicAdd(&s_stats[r * kStats + k], v); };
+    auto flush_evals = [&](int r) {
+        if (ev.f) stat(r, 8, ev.f);
+        if (ev.g) stat(r, 9, ev.g);
+        ev.f = ev.g = 0u;
+    };
     auto finish = [&]() {
+        flush_evals(req);
         if (acc != 0.0) {
             const Req& q = B.r[req];
             atomicAdd(&B.image[q.image_offset + id_hi], acc);
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
                                &o, &d);
                     stat(r, 0, 1ull);
                     V hit;
-                    const int h = march_outside(q, o, d, &hit);
+                    const int h = march_outside(q, o, d, &hit, ev);
                     if (h == 1) {
                         stat(r, 1, 1ull);
                         live = true;
@@ -300,8 +313,9 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
                         p = hit;
                         w = d;
                         acc = 0.0;
-                    } else if (h == 2) {
-                        stat(r, 6, 1ull);
+                    } else {
+                        if (h == 2) stat(r, 6, 1ull);
+                        flush_evals(r);
                     }
                 } else {
                     need = false;
@@ -325,13 +339,13 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
                 const Words u = st.at(seg, 0u);
                 const float l = -__logf(1.0f - u24(u.w0)) / q.sigma;
                 V c;
-                const int ev = march_inside(q, p, w, l, &c);
-                if (ev == 2) {
+                const int ev_kind = march_inside(q, p, w, l, &c, ev);
+                if (ev_kind == 2) {
                     stat(req, 6, 1ull);
                     finish();
-                } else if (ev == 0) {
+                } else if (ev_kind == 0) {
                     V re;
-                    const int back = march_outside(q, c, w, &re);
+                    const int back = march_outside(q, c, w, &re, ev);
                     if (back == 1) {
                         p = re;
                         ++seg;
@@ -342,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
                 } else {
                     bool done_event = false;
                     if (q.mode == MS_SPHERE && learned) {
-                        const float d = -sdf(q, c) / q.lip;
+                        const float d = -sdf(q, c, ev) / q.lip;
                         const float r = fminf(d, q.tau_max / q.sigma);
                         const float tau = q.sigma * r;
                         if (tau >= q.tau_min) {
@@ -487,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
             const V dl = xl - nX;
             const float d2 = dot(dl, dl);
             const V wl2 = dl * rsqrtf(d2);
-            const float din = inside_length(q, nX, xl);
+            const float din = inside_length(q, nX, xl, ev);
             if (din < 0.0f) {
                 stat(req, 6, 1ull);
             } else {
@@ -500,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
     }
 
     // ---------------- per-request counters -> global ----------------
-    for (int k = tid; k < B.n * 8; k += kThreads)
+    for (int k = tid; k < B.n * kStats; k += kThreads)
         if (s_stats[k]) atomicAdd(&B.stats[k], s_stats[k]);
 }
 

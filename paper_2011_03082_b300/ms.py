@@ -19,6 +19,7 @@ LIB_PATH = PKG / "libms.so"
 MS_FP32, MS_FP64, MS_FP16, MS_BF16 = 0, 1, 2, 3
 MS_BRUTE, MS_SPHERE = 0, 1
 MS_ESCAPED, MS_ABSORBED, MS_TRUNCATED = 0, 1, 2
+MS_RENDER_STATS = 16
 
 # the C ABI's exported symbols (checked by the tests against include/ms.h)
 EXPORTS = ("ms_last_error", "ms_version", "ms_walk_workspace_size", "ms_simulate_walks", "ms_cvae_infer",

@@ -1,0 +1,141 @@
+"""Training pipeline of the three learned samplers (Sec. 3.1-3.2, Sec. 4.1, Eq. 3), on the GPU.
+
+1. ``generate_records``: brute-force HG walks from the centre of the unit sphere in the paper's convention
+   (first event at the centre, incoming direction (0,0,1)) with per-walk media drawn like the training set
+   (optical radius log-uniform in [1,256], g U[0,0.95], albedo U[0.9,1]); the path follows the albedo-1
+   physics and the representative event is chosen with weights albedo^k (``reservoir=2``); the records are
+   turned into the conditions and targets of LengthGen, PathGen and EventGen by ``ms_training_records``.
+2. ``train``: each CVAE is trained with the library's forward/backward/Adam kernels (``ms_cvae_train_step``)
+   on random mini-batches.
+3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder) and
+   the training log.
+
+Run as ``python -m paper_2011_03082_b300.pipeline [--walks N] [--steps S] [--out PATH]``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+from pathlib import Path
+
+import numpy as np
+import torch
+
+from . import ms, synth
+
+FORMAT = 1
+DEFAULT_WEIGHTS = Path(__file__).resolve().parent / "weights" / "cvae_set.npz"
+MODELS = ("length", "path", "event")
+RECORD_KEYS = {"length": ("cL", "xL"), "path": ("cP", "xP"), "event": ("cE", "xE")}
+
+
+def generate_records(n_walks: int, seed: int = 1, device="cuda") -> dict:
+    tau, g, phi = synth.training_media(seed, n_walks)
+    media = ms.media_tensor(tau.astype(np.float32), g.astype(np.float32), phi.astype(np.float32), (0.0, 0.0, 1.0),
+                            0, 1, device=device)
+    out = ms.walk_outputs(n_walks, device=device)
+    ms.ms_simulate_walks(media, n_walks, out, seed=seed, reservoir=2, precision=ms.MS_FP32, max_events=1 << 24)
+    recs = {k: torch.empty(n_walks, d, device=device) for k, d in
+            (("cL", 2), ("xL", 1), ("cP", 3), ("xP", 3), ("cE", 7), ("xE", 6))}
+    ms.ms_training_records(n_walks, out["n_events"], out["exit_pos"], out["exit_dir"], out["rep_pos"],
+                           out["rep_dir"], media, seed + 1000, recs)
+    recs["counters"] = out["counters"]
+    return recs
+
+
+def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch: int, lr: float, seed: int,
+              log_every: int = 100):
+    p_in, p_out = synth.MODEL_SHAPES[name]
+    shape = ms.cvae_shape(p_in, p_out)
+    params = torch.from_numpy(synth.xavier_cvae(seed, p_in, p_out)).to(c.device)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    ws = ms.workspace(ms.ms_cvae_workspace_size(shape, batch), c.device)
+    loss3 = torch.zeros(3, device=c.device)
+    gen = torch.Generator(device=c.device)
+    gen.manual_seed(seed)
+    n = c.shape[0]
+    log = []
+    xb = torch.empty(batch, p_out, device=c.device)
+    cb = torch.empty(batch, p_in, device=c.device)
+    for t in range(1, steps + 1):
+        idx = torch.randint(0, n, (batch,), device=c.device, generator=gen)
+        torch.index_select(x, 0, idx, out=xb)
+        torch.index_select(c, 0, idx, out=cb)
+        ms.ms_cvae_train_step(shape, params, m, v, xb, cb, batch, seed=seed, step=t, lr=lr, loss3=loss3, ws=ws)
+        if t % log_every == 0 or t == 1 or t == steps:
+            log.append((t, *[float(v_) for v_ in loss3.tolist()]))
+    return params, log
+
+
+def train(records: dict, *, steps=2000, batch=65536, lr=1e-3, seed=1, log_every=100) -> dict:
+    models = {}
+    for i, name in enumerate(MODELS):
+        ck, xk = RECORD_KEYS[name]
+        params, log = train_one(name, records[ck], records[xk], steps=steps, batch=batch, lr=lr,
+                                seed=seed + 17 * i, log_every=log_every)
+        models[name] = dict(params=params.cpu().numpy(), log=log)
+    return models
+
+
+def decoder_part(name: str, params: np.ndarray) -> np.ndarray:
+    """The decoder block of a packed CVAE parameter vector (what the renderer evaluates)."""
+    p_in, p_out = synth.MODEL_SHAPES[name]
+    W, L = synth.WIDTH, synth.LATENT
+    n_enc = W * (p_out + p_in) + W + W * W + W + 2 * L * W + 2 * L
+    return np.ascontiguousarray(params[n_enc:], dtype=np.float32)
+
+
+def save(path, models: dict, meta: dict):
+    path = Path(path)
+    path.parent.mkdir(parents=True, exist_ok=True)
+    arrays = {f"{k}_params": v["params"].astype(np.float32) for k, v in models.items()}
+    arrays.update({f"{k}_log": np.asarray(v["log"], np.float64) for k, v in models.items()})
+    np.savez(path, format=np.int64(FORMAT), meta=json.dumps(meta), **arrays)
+
+
+def load(path=DEFAULT_WEIGHTS) -> dict:
+    z = np.load(path, allow_pickle=False)
+    if int(z["format"]) != FORMAT:
+        raise ValueError(f"{path}: unsupported weights format {int(z['format'])}")
+    return {k: dict(params=z[f"{k}_params"], log=z[f"{k}_log"]) for k in MODELS} | {
+        "meta": json.loads(str(z["meta"]))}
+
+
+def device_decoders(models: dict, device="cuda") -> dict:
+    """{name: (decoder weights on the device, p_in, p_out)} as ms.cvae_set expects."""
+    out = {}
+    for name in MODELS:
+        p_in, p_out = synth.MODEL_SHAPES[name]
+        out[name] = (torch.from_numpy(decoder_part(name, models[name]["params"])).to(device), p_in, p_out)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--walks", type=int, default=1 << 24)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--out", default=str(DEFAULT_WEIGHTS))
+    a = ap.parse_args(argv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    recs = generate_records(a.walks, a.seed)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    c = recs["counters"].cpu().tolist()
+    meta = dict(walks=a.walks, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, walk_seconds=t1 - t0,
+                train_seconds=t2 - t1, walk_counters=c,
+                final_loss={k: v["log"][-1][1] for k, v in models.items()})
+    save(a.out, models, meta)
+    print(json.dumps(meta))
+
+
+if __name__ == "__main__":
+    main()

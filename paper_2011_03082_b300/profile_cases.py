@@ -1,0 +1,94 @@
+"""Small, fixed invocations of each kernel for profiling (ncu) and quick timing.
+
+``python -m paper_2011_03082_b300.profile_cases CASE [--repeat R]`` with CASE one of:
+  walk      65,536 photons, optical radius 8, g 0.8, albedo 0.999, isotropic start (FP32)
+  walk24    2^24 walks with the training media (FP32, reservoir)
+  decoder   2^22 decoder queries, P_out 6 (FP32, Philox normals)
+  train     one training step of EventGen, batch 65,536
+  render    one 128x128 px x 16 spp render at sigma_t 64, sphere tracing with the trained decoders
+  brute     the same render in brute-force mode
+Each case runs ``--repeat`` times (default 2) and prints the CUDA-event time of the last run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import build, ms, pipeline, synth
+
+
+def case_walk(n=65536, reservoir=0, media=None):
+    w = synth.walk_cfg()
+    if media is None:
+        media = ms.media_tensor(w["optical_radius"], w["g"], w["albedo"], w["dir_in"], 1, 0)
+    out = ms.walk_outputs(n, per_photon=reservoir > 0)
+    ws = ms.workspace(256)
+    return lambda: ms.ms_simulate_walks(media, n, out, seed=1, reservoir=reservoir, ws=ws)
+
+
+def case_walk24():
+    n = 1 << 24
+    tau, g, phi = synth.training_media(1, n)
+    media = ms.media_tensor(tau.astype(np.float32), g.astype(np.float32), phi.astype(np.float32), (0, 0, 1), 0, 1)
+    return case_walk(n, 2, media)
+
+
+def case_decoder(n=1 << 22, p_out=6):
+    w = torch.from_numpy(synth.xavier_decoder(7, 4, p_out)).cuda()
+    c = torch.from_numpy(synth.decoder_queries(7, n)).cuda()
+    mlv = torch.empty(n, 2 * p_out, device="cuda")
+    smp = torch.empty(n, p_out, device="cuda")
+    d = ms.decoder_struct(w, 4, p_out)
+    return lambda: ms.ms_cvae_infer(d, c, n, seed=7, out_mean_logvar=mlv, out_sample=smp)
+
+
+def case_train(B=65536):
+    p_in, p_out = synth.MODEL_SHAPES["event"]
+    shape = ms.cvae_shape(p_in, p_out)
+    p = torch.from_numpy(synth.xavier_cvae(1, p_in, p_out)).cuda()
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    g = torch.Generator().manual_seed(0)
+    x = torch.randn(B, p_out, generator=g).cuda()
+    c = torch.randn(B, p_in, generator=g).cuda()
+    ws = ms.workspace(ms.ms_cvae_workspace_size(shape, B))
+    loss3 = torch.zeros(3, device="cuda")
+    return lambda: ms.ms_cvae_train_step(shape, p, m, v, x, c, B, step=1, loss3=loss3, ws=ws)
+
+
+def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0):
+    models = pipeline.load()
+    cset = ms.cvae_set(pipeline.device_decoders(models))
+    p = ms.render_params(synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode))
+    img = torch.zeros(res * res, dtype=torch.float64, device="cuda")
+    st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    ws = ms.workspace(ms.ms_render_workspace_size([p]))
+    return lambda: ms.ms_render(p, cset if mode == ms.MS_SPHERE else None, img, st, ws=ws)
+
+
+CASES = {"walk": case_walk, "walk24": case_walk24, "decoder": case_decoder, "train": case_train,
+         "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE)}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=sorted(CASES))
+    ap.add_argument("--repeat", type=int, default=2)
+    a = ap.parse_args(argv)
+    build.build()
+    fn = CASES[a.case]()
+    ms_ = None
+    for _ in range(a.repeat):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        ms_ = s.elapsed_time(e)
+    print(json.dumps({"case": a.case, "ms": ms_}))
+
+
+if __name__ == "__main__":
+    main()

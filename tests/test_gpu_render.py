@@ -22,7 +22,7 @@ def _models():
 
 def gpu_render(params, models=None):
     img = torch.zeros(params["height"], params["width"], dtype=torch.float64, device="cuda")
-    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    st = torch.zeros(16, dtype=torch.int64, device="cuda")
     cs = None
     keep = []
     if models is not None:
@@ -66,7 +66,7 @@ def test_render_matches_oracle(orc, name, sigma, mode):
     assert rmse(g2, o2) <= 0.2 * noise, (rmse(g2, o2), noise)
     assert gs[0] == s2[0] == 32 * 32 * 16
     assert abs(int(gs[1]) - int(s2[1])) <= 0.002 * s2[1]
-    for k in (2, 3, 4, 7):
+    for k in (2, 3, 4, 7, 8, 9):
         assert abs(int(gs[k]) - int(s2[k])) <= 0.01 * max(s2[k], 100), (k, gs[k], s2[k])
 
 
@@ -88,7 +88,7 @@ def test_sample_offsets_and_batches_compose():
     singles = [gpu_render(r, models) for r in reqs]
     npx = sum(r["width"] * r["height"] for r in reqs)
     imgs = torch.zeros(npx, dtype=torch.float64, device="cuda")
-    st = torch.zeros(len(reqs), 8, dtype=torch.int64, device="cuda")
+    st = torch.zeros(len(reqs), 16, dtype=torch.int64, device="cuda")
     dm = {k: (torch.from_numpy(w).cuda(), pi, po) for k, (w, pi, po) in models.items()}
     ms.ms_render_batch([ms.render_params(r) for r in reqs], ms.cvae_set(dm), imgs, st)
     torch.cuda.synchronize()
@@ -111,7 +111,7 @@ def test_full_size_render_properties():
 
 def test_bad_requests_are_rejected():
     img = torch.zeros(4, dtype=torch.float64, device="cuda")
-    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    st = torch.zeros(16, dtype=torch.int64, device="cuda")
     for bad in (dict(sigma_t=0.0), dict(g=1.0), dict(albedo=1.5), dict(width=0), dict(mode=5)):
         p = dict(synth.render_scene(8.0, width=2, height=2, spp=1, mode=0), **bad)
         with pytest.raises(ms.MsError):

@@ -67,7 +67,8 @@ def test_sphere_mode_without_spheres_equals_brute_force(orc):
     every collision and consumes the same random numbers as brute force."""
     a, sa, _ = _render(orc, mode=0)
     b, sb, _ = _render(orc, mode=1, min_optical_radius=1e30)
-    assert np.array_equal(a, b) and np.array_equal(sa, sb)
+    assert np.array_equal(a, b) and np.array_equal(sa[:8], sb[:8])
+    assert sb[8] == sa[8] + sb[4]      # plus one distance evaluation per collision for the sphere radius
 
 
 def test_single_scattering_limit_matches_quadrature(orc):
