@@ -148,9 +148,8 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
         if (t >= D)
             return din;
         ov3 r = add(X, mul(w, t));
-        double f = sdf(S, r);
         if (inside) {
-            double d = -f / S->lip;
+            double d = -sdf(S, r) / S->lip;
             if (d < R_EPS) {
                 if (dot(sdf_grad(S, r), w) > 0.0) {
                     inside = 0;
@@ -164,7 +163,7 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
         } else {
             if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
                 return din;
-            double d = f / S->lip;
+            double d = sdf(S, r) / S->lip;
             if (d < R_EPS) {
                 if (dot(sdf_grad(S, r), w) < 0.0) {
                     inside = 1;

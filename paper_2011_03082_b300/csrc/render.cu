@@ -2,29 +2,35 @@
 // SDF object with next-event estimation toward a point light.
 //
 // Method (Sec. 3 and Fig. 2b; Sec. 4.1, Eq. 3-4; Sec. 4.3, Eq. 5): a camera path enters the object and
-// alternates free flights (exponential, the homogeneous case of delta tracking) with, at each collision,
+// alternates free flights (exponential: the homogeneous case of delta tracking) with, at each collision,
 // either one sphere-tracing step — the largest sphere inside the boundary from the SDF, LengthGen /
 // absorption / PathGen / EventGen at the rescaled optical radius sigma_t r, NEE at the representative event
 // with weight Lambda^(N) — or, in thin regions and in brute-force mode, one scattering event with NEE weight
 // phi, Russian roulette and HG scattering.
 //
-// Kernel design (persistent, one launch for any number of requests):
-//  * each block owns 256 path slots, one per thread; slots are refilled from a global ticket of camera
-//    samples with one warp-aggregated atomic per refill round;
-//  * a block iteration is a wavefront of stages separated by barriers: (1) refill, (2) flight by the owning
-//    thread (SDF sphere-tracing march inside, and outside on exit to find a re-entry), brute-force events
-//    in place, (3) the sphere steps, compacted into a shared-memory queue with __ballot_sync / __popc and a
-//    block prefix so the three decoder MLPs run on full warps, (4) next-event estimation (shadow march) by
-//    the owning thread;
-//  * the decoder weights of all three models sit in shared memory (broadcast float4 loads, decoder.cuh);
-//  * a path's contributions accumulate in a register in double precision and are added to its pixel once,
-//    when the path ends; per-request counters are shared-memory atomics flushed at block exit;
-//  * every loop is bounded: segments per path, march steps per march, and the block loop ends when the
-//    ticket is drained and no slot is live.
+// Kernel design: one cooperative persistent launch (any number of requests) that runs waves of two stages
+// separated by grid-wide barriers, over path records kept in global queues (the workspace):
+//  * stage A (marching): every lane runs a small state machine — camera march, free-flight march, re-entry
+//    march, shadow march — advancing ONE signed-distance step per loop iteration; when a lane's march ends
+//    it finishes that piece of work (brute-force event, NEE contribution, path end, hand-off) and takes new
+//    work at once (a path returning from stage B, else a new camera sample), so warps stay converged on the
+//    same short loop body however long the individual marches are.  A path stays in its lane through its
+//    brute-force events; it leaves when it needs a sphere step (-> sphere queue), after kSegPerVisit
+//    flights (-> flight queue, bounds the stage's tail) or when it ends;
+//  * stage B (decoders): the sphere queue is dense, so the three decoder MLPs run on full warps with weights
+//    in shared memory (broadcast float4 loads, decoder.cuh); results go back to the flight queue carrying a
+//    pending NEE request that stage A resolves first;
+//  * queue indices come from warp-aggregated atomics (__ballot_sync / __popc); the number of live paths is
+//    capped by the queue capacity; a path's NEE sum stays in its record and is added to its pixel (double)
+//    once; counters are per-lane registers flushed to shared, then global, memory;
+//  * everything is bounded: segments per path, steps per march, waves per launch (error flag if exceeded).
 #include <cmath>
+#include <cooperative_groups.h>
 
 #include "decoder.cuh"
 #include "ms_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ms {
 namespace render {
@@ -33,8 +39,10 @@ constexpr int kThreads = 256;
 constexpr int kMaxReq = 64;
 constexpr int kStats = MS_RENDER_STATS;
 constexpr float kEps = 1e-4f;       // distance from the boundary treated as on it
-constexpr int kMaxMarch = 1024;     // sphere-tracing steps per march; running out ends the path
+constexpr int kMaxMarch = 1024;     // steps per march; running out ends the path
 constexpr float kNMax = 16777216.0f;
+constexpr uint32_t kSegPerVisit = 64;
+constexpr uint64_t kMaxWaves = 1ull << 24;
 
 struct Req {
     float cam[3], at[3], tan_half, aspect;
@@ -46,16 +54,40 @@ struct Req {
     uint64_t seed, sample_offset, image_offset, samples_begin;
 };
 
+// One path in a queue (80 bytes, five 16-byte words).
+struct __align__(16) Path {
+    float px, py, pz, wx;
+    float wy, wz;
+    uint32_t id_lo, id_hi;
+    uint32_t seg, flags;            // flags: request (bits 0-7), pending NEE (bit 8), ends after NEE (bit 9)
+    float acc, nee_wgt;
+    float Xx, Xy, Xz, Wx;           // pending NEE request (X, W); sphere jobs keep r, tau in Xx, Xy
+    float Wy, Wz, pad0, pad1;
+};
+constexpr uint32_t kFlagNee = 1u << 8, kFlagEnd = 1u << 9;
+
+struct Ctl {                         // in the workspace, zeroed before the launch
+    unsigned long long ticket;
+    unsigned long long work;         // items taken by either stage (progress check)
+    int alive;
+    int error;
+    int f_count[2], f_taken[2];
+    int s_count[2], s_taken[2];
+};
+
 struct Batch {
     int n;
+    int capacity;                    // paths per queue
     uint64_t total;
     Req r[kMaxReq];
-    const float* wL;     // decoder weights (packed float32) LengthGen, PathGen, EventGen; null in brute force
+    const float* wL;                 // decoder weights LengthGen, PathGen, EventGen (null: brute force only)
     const float* wP;
     const float* wE;
     double* image;
-    unsigned long long* stats;   // [n][kStats]
-    unsigned long long* ticket;
+    unsigned long long* stats;       // [n][kStats]
+    Ctl* ctl;
+    Path* fq[2];                     // flight queues (by wave parity)
+    Path* sq[2];                     // sphere queues (by wave parity)
 };
 
 // decoder shapes: LengthGen (2 + 4 -> 1), PathGen (3 + 4 -> 3), EventGen (7 + 4 -> 6)
@@ -72,19 +104,14 @@ __device__ __forceinline__ float dot(V a, V b) { return fmaf(a.x, b.x, fmaf(a.y,
 __device__ __forceinline__ V cross(V a, V b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
 __device__ __forceinline__ V unit(V a) { return a * rsqrtf(dot(a, a)); }
 
-// per-thread SDF evaluation counters (distance, gradient), flushed into the request's stats
-struct Evals { unsigned f, g; };
-
 // ---- the displaced sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz) (negative inside) ----
-__device__ __forceinline__ float sdf(const Req& q, V p, Evals& ev)
+__device__ __forceinline__ float sdf(const Req& q, V p)
 {
-    ++ev.f;
     return sqrtf(dot(p, p)) - 1.0f - q.A * __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z);
 }
 
-__device__ __forceinline__ V sdf_grad(const Req& q, V p, Evals& ev)
+__device__ __forceinline__ V sdf_grad(const Req& q, V p)
 {
-    ++ev.g;
     float sx, cx, sy, cy, sz, cz;
     __sincosf(q.k * p.x, &sx, &cx);
     __sincosf(q.k * p.y, &sy, &cy);
@@ -92,74 +119,6 @@ __device__ __forceinline__ V sdf_grad(const Req& q, V p, Evals& ev)
     const float inv = rsqrtf(dot(p, p));
     const float ak = q.A * q.k;
     return v3(p.x * inv - ak * cx * sy * sz, p.y * inv - ak * sx * cy * sz, p.z * inv - ak * sx * sy * cz);
-}
-
-// 1: collision at *c = p + l w; 0: crossed the boundary outward at *c; 2: step cap
-__device__ int march_inside(const Req& q, V p, V w, float l, V* c, Evals& ev)
-{
-    float t = 0.0f;
-    for (int it = 0; it < kMaxMarch; ++it) {
-        const V r = p + w * t;
-        float d = -sdf(q, r, ev) / q.lip;
-        if (d < kEps) {
-            if (dot(sdf_grad(q, r, ev), w) > 0.0f) { *c = r; return 0; }
-            d = kEps;
-        }
-        if (t + d >= l) { *c = p + w * l; return 1; }
-        t += d;
-    }
-    return 2;
-}
-
-// 1: re-entered at *c; 0: left the bounding sphere; 2: step cap
-__device__ int march_outside(const Req& q, V p, V w, V* c, Evals& ev)
-{
-    float t = 0.0f;
-    for (int it = 0; it < kMaxMarch; ++it) {
-        const V r = p + w * t;
-        if (dot(r, r) > q.rb2 && dot(r, w) >= 0.0f) return 0;
-        float d = sdf(q, r, ev) / q.lip;
-        if (d < kEps) {
-            if (dot(sdf_grad(q, r, ev), w) < 0.0f) { *c = r; return 1; }
-            d = kEps;
-        }
-        t += d;
-    }
-    return 2;
-}
-
-// length of X -> light inside the medium (Sec. 4.3 d_t); negative when the step cap runs out
-__device__ float inside_length(const Req& q, V X, V xl, Evals& ev)
-{
-    const V dl = xl - X;
-    const float D = sqrtf(dot(dl, dl));
-    const V w = dl * (1.0f / D);
-    float t = 0.0f, din = 0.0f;
-    bool inside = true;
-    for (int it = 0; it < kMaxMarch; ++it) {
-        if (t >= D) return din;
-        const V r = X + w * t;
-        const float f = sdf(q, r, ev);
-        if (inside) {
-            float d = -f / q.lip;
-            if (d < kEps) {
-                if (dot(sdf_grad(q, r, ev), w) > 0.0f) { inside = false; continue; }
-                d = kEps;
-            }
-            const float step = fminf(d, D - t);
-            din += step;
-            t += step;
-        } else {
-            if (dot(r, r) > q.rb2 && dot(r, w) >= 0.0f) return din;
-            float d = f / q.lip;
-            if (d < kEps) {
-                if (dot(sdf_grad(q, r, ev), w) < 0.0f) { inside = true; continue; }
-                d = kEps;
-            }
-            t += fminf(d, D - t);
-        }
-    }
-    return -1.0f;
 }
 
 __device__ __forceinline__ float hg_pdf(float cosang, float g)
@@ -194,7 +153,6 @@ __device__ __forceinline__ V scatter_dir(V w, float mu, float u)
     return unit(t1 * (st * cp) + t2 * (st * sp) + w * mu);
 }
 
-// Camera ray of sample (pixel, jitter) of request q.
 __device__ __forceinline__ void camera_ray(const Req& q, int px, int py, float jx, float jy, V* o, V* d)
 {
     const V cp = v3(q.cam[0], q.cam[1], q.cam[2]);
@@ -207,16 +165,6 @@ __device__ __forceinline__ void camera_ray(const Req& q, int px, int py, float j
     *d = unit(fw + rt * sx + up * sy);
 }
 
-// per-slot data exchanged with the sphere stage
-struct SphereJob {
-    float c[3], w[3], r, tau;
-    uint32_t id_lo, id_hi, seg, req;
-};
-struct SphereOut {
-    float X[3], W[3], lam, p[3], w[3];
-    int absorbed;
-};
-
 __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
 {
     int lo = 0, hi = B.n - 1;
@@ -227,17 +175,52 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
     return lo;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_constant__ Batch B)
+// Warp-aggregated slot reservation: each lane with `want` gets a distinct index from *counter.
+__device__ __forceinline__ int warp_push_index(int* counter, bool want)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (m == 0u) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return want ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+__device__ __forceinline__ void store_path(Path* dst, const Path& p)
+{
+    const float4* s = reinterpret_cast<const float4*>(&p);
+    float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) d[k] = s[k];
+}
+
+__device__ __forceinline__ Path load_path(const Path* src)
+{
+    Path p;
+    const float4* s = reinterpret_cast<const float4*>(src);
+    float4* d = reinterpret_cast<float4*>(&p);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) d[k] = __ldcg(s + k);
+    return p;
+}
+
+// Per-lane counters of the request the lane is currently serving, flushed to shared memory on change.
+constexpr int kUsedStats = 10;
+struct Counters {
+    int req = -1;
+    unsigned c[kUsedStats] = {};
+};
+
+enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow };
+
+__global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_constant__ Batch B)
 {
     __shared__ __align__(16) float sw[kSmemL + kSmemP + kSmemE];
-    __shared__ SphereJob s_job[kThreads];
-    __shared__ SphereOut s_out[kThreads];
-    __shared__ int s_queue[kThreads];
-    __shared__ int s_warp_count[kThreads / 32];
-    __shared__ int s_nq;
     __shared__ unsigned long long s_stats[kMaxReq * kStats];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    cg::grid_group grid = cg::this_grid();
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool learned = B.wL != nullptr;
     float* wl = sw;
     float* wpth = sw + kSmemL;
@@ -250,278 +233,446 @@ __global__ void __launch_bounds__(kThreads, 1) render_kernel(const __grid_consta
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     __syncthreads();
 
-    // slot state (owned by this thread)
-    bool live = false;
-    int req = 0;
-    uint32_t id_lo = 0, id_hi = 0, seg = 0;
-    V p = v3(0, 0, 0), w = v3(0, 0, 1);
-    double acc = 0.0;
-    bool drained = false;   // warp-uniform
-    Evals ev{0u, 0u};
-
-    auto stat = [&](int r, int k, unsigned long long v) { atomicAdd(&s_stats[r * kStats + k], v); };
-    auto flush_evals = [&](int r) {
-        if (ev.f) stat(r, 8, ev.f);
-        if (ev.g) stat(r, 9, ev.g);
-        ev.f = ev.g = 0u;
-    };
-    auto finish = [&]() {
-        flush_evals(req);
-        if (acc != 0.0) {
-            const Req& q = B.r[req];
-            atomicAdd(&B.image[q.image_offset + id_hi], acc);
+    Ctl* ctl = B.ctl;
+    Counters cnt;
+    auto count = [&](int req, int k, unsigned v) {
+        if (req != cnt.req) {
+            if (cnt.req >= 0)
+#pragma unroll
+                for (int j = 0; j < kUsedStats; ++j)
+                    if (cnt.c[j]) { atomicAdd(&s_stats[cnt.req * kStats + j], (unsigned long long)cnt.c[j]); cnt.c[j] = 0u; }
+            cnt.req = req;
         }
-        acc = 0.0;
-        live = false;
+        cnt.c[k] += v;
     };
+    bool drained = false;   // warp-uniform: camera tickets exhausted
+    unsigned long long last_work = ~0ull;
 
-    for (;;) {
-        // ---------------- (1) refill free slots with new camera samples ----------------
-        bool need = !live;
-        for (;;) {
-            const unsigned m = __ballot_sync(0xffffffffu, need && !drained);
-            if (m == 0u) break;
-            unsigned long long base = 0;
-            const int leader = __ffs(m) - 1;
-            if (lane == leader) base = atomicAdd(B.ticket, (unsigned long long)__popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (base + __popc(m) >= B.total) drained = true;
-            if (need && ((m >> lane) & 1u)) {
-                const uint64_t t = base + __popc(m & ((1u << lane) - 1u));
-                if (t < B.total) {
-                    const int r = find_req(B, t);
-                    const Req& q = B.r[r];
-                    const uint64_t local = t - q.samples_begin;
-                    const uint32_t pixel = (uint32_t)(local / q.spp);
-                    const uint32_t sample = (uint32_t)(q.sample_offset + local % q.spp);
-                    const Stream st(q.seed, ((uint64_t)pixel << 32) | sample);
-                    const Words j = st.at(0u, 8u);
-                    V o, d;
-                    camera_ray(q, (int)(pixel % (uint32_t)q.W), (int)(pixel / (uint32_t)q.W), u24(j.w0), u24(j.w1),
-                               &o, &d);
-                    stat(r, 0, 1ull);
-                    V hit;
-                    const int h = march_outside(q, o, d, &hit, ev);
-                    if (h == 1) {
-                        stat(r, 1, 1ull);
-                        live = true;
+    uint64_t wave = 0;
+    for (;; ++wave) {
+        const int P = (int)(wave & 1ull), Q = P ^ 1;
+        // ================= stage A: marching state machine =================
+        if (blockIdx.x == 0 && tid == 0) { ctl->s_count[Q] = 0; ctl->s_taken[Q] = 0; }
+        {
+            Path pa;                                   // the lane's path
+            int st = kIdle;
+            int req = 0;
+            V mo = v3(0, 0, 0), md = v3(0, 0, 1);      // march origin / direction
+            float mt = 0.0f, ml = 0.0f, din = 0.0f;    // march parameter, flight length or segment length
+            int mstep = 0;
+            bool inside = true;
+            uint32_t visit = 0;                        // flights in this visit
+            const int f_in = __ldcg(&ctl->f_count[P]);
+            bool f_left = true;                        // warp-uniform: flight queue not yet drained
+            bool room = true;                          // warp-uniform: the queues can take new paths
+            for (;;) {
+                // ---------- refill idle lanes: returning paths first, then new camera samples ----------
+                bool need = st == kIdle;
+                unsigned m = __ballot_sync(0xffffffffu, need);
+                if (m && f_left) {
+                    const int leader = __ffs(m) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&ctl->f_taken[P], __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    const int avail = max(0, min(__popc(m), f_in - base));
+                    if (avail < __popc(m)) f_left = false;
+                    if (lane == leader && avail > 0) atomicAdd(&ctl->work, (unsigned long long)avail);
+                    const int rank = __popc(m & ((1u << lane) - 1u));
+                    if (need && rank < avail) {
+                        pa = load_path(B.fq[P] + base + rank);
+                        req = (int)(pa.flags & 0xffu);
+                        visit = 0;
                         need = false;
-                        req = r;
-                        id_lo = sample;
-                        id_hi = pixel;
-                        seg = 0;
-                        p = hit;
-                        w = d;
-                        acc = 0.0;
-                    } else {
-                        if (h == 2) stat(r, 6, 1ull);
-                        flush_evals(r);
-                    }
-                } else {
-                    need = false;
-                }
-            }
-        }
-        if (!__syncthreads_or(live)) break;
-
-        // ---------------- (2) flight; brute-force events in place ----------------
-        const Req& q = B.r[req];
-        bool sphere = false, nee_req = false, end_after_nee = false;
-        V nX = v3(0, 0, 0), nW = v3(0, 0, 1);
-        float nwt = 0.0f;
-        if (live) {
-            if (seg >= q.max_segments) {
-                stat(req, 6, 1ull);
-                finish();
-            } else {
-                stat(req, 2, 1ull);
-                const Stream st(q.seed, ((uint64_t)id_hi << 32) | id_lo);
-                const Words u = st.at(seg, 0u);
-                const float l = -__logf(1.0f - u24(u.w0)) / q.sigma;
-                V c;
-                const int ev_kind = march_inside(q, p, w, l, &c, ev);
-                if (ev_kind == 2) {
-                    stat(req, 6, 1ull);
-                    finish();
-                } else if (ev_kind == 0) {
-                    V re;
-                    const int back = march_outside(q, c, w, &re, ev);
-                    if (back == 1) {
-                        p = re;
-                        ++seg;
-                    } else {
-                        if (back == 2) stat(req, 6, 1ull);
-                        finish();
-                    }
-                } else {
-                    bool done_event = false;
-                    if (q.mode == MS_SPHERE && learned) {
-                        const float d = -sdf(q, c, ev) / q.lip;
-                        const float r = fminf(d, q.tau_max / q.sigma);
-                        const float tau = q.sigma * r;
-                        if (tau >= q.tau_min) {
-                            sphere = true;
-                            done_event = true;
-                            SphereJob& jb = s_job[tid];
-                            jb.c[0] = c.x; jb.c[1] = c.y; jb.c[2] = c.z;
-                            jb.w[0] = w.x; jb.w[1] = w.y; jb.w[2] = w.z;
-                            jb.r = r; jb.tau = tau;
-                            jb.id_lo = id_lo; jb.id_hi = id_hi; jb.seg = seg; jb.req = (uint32_t)req;
-                        }
-                    }
-                    if (!done_event) {
-                        stat(req, 4, 1ull);
-                        nee_req = true;
-                        nX = c;
-                        nW = w;
-                        nwt = q.phi;
-                        if (u24(u.w3) >= q.phi) {
-                            stat(req, 5, 1ull);
-                            end_after_nee = true;
+                        if (pa.flags & kFlagNee) {
+                            st = kShadow;
+                            mo = v3(pa.Xx, pa.Xy, pa.Xz);
+                            const Req& q = B.r[req];
+                            const V dl = v3(q.light[0], q.light[1], q.light[2]) - mo;
+                            ml = sqrtf(dot(dl, dl));
+                            md = dl * (1.0f / ml);
+                            mt = 0.0f; din = 0.0f; inside = true; mstep = 0;
                         } else {
-                            w = scatter_dir(w, hg_cosine(u24(u.w1), q.g), u24(u.w2));
-                            p = c;
-                            ++seg;
+                            st = kFlight;
+                            mstep = -1;                // start a flight below
+                        }
+                    }
+                    m = __ballot_sync(0xffffffffu, need);
+                }
+                if (m && !drained && room) {
+                    const int leader = __ffs(m) - 1;
+                    const int k = __popc(m);
+                    int got = 0, flags = 0;   // flags: 1 tickets exhausted, 2 queues full
+                    unsigned long long t0 = 0;
+                    if (lane == leader) {
+                        const int old = atomicAdd(&ctl->alive, k);
+                        const int grant = min(k, max(0, B.capacity - old));
+                        if (grant < k) {
+                            atomicSub(&ctl->alive, k - grant);
+                            flags |= 2;
+                        }
+                        if (grant > 0) {
+                            t0 = atomicAdd(&ctl->ticket, (unsigned long long)grant);
+                            const unsigned long long left = t0 < B.total ? B.total - t0 : 0ull;
+                            got = (int)min((unsigned long long)grant, left);
+                            if (got < grant) atomicSub(&ctl->alive, grant - got);
+                            if (t0 + (unsigned long long)grant >= B.total) flags |= 1;
+                            if (got > 0) atomicAdd(&ctl->work, (unsigned long long)got);
+                        }
+                    }
+                    got = __shfl_sync(0xffffffffu, got, leader);
+                    flags = __shfl_sync(0xffffffffu, flags, leader);
+                    t0 = __shfl_sync(0xffffffffu, t0, leader);
+                    if (flags & 1) drained = true;
+                    if (flags & 2) room = false;
+                    const int rank = __popc(m & ((1u << lane) - 1u));
+                    if (need && rank < got) {
+                        const uint64_t t = t0 + rank;
+                        req = find_req(B, t);
+                        const Req& q = B.r[req];
+                        const uint64_t local = t - q.samples_begin;
+                        const uint32_t pixel = (uint32_t)(local / q.spp);
+                        const uint32_t sample = (uint32_t)(q.sample_offset + local % q.spp);
+                        const Stream rs(q.seed, ((uint64_t)pixel << 32) | sample);
+                        const Words j = rs.at(0u, 8u);
+                        camera_ray(q, (int)(pixel % (uint32_t)q.W), (int)(pixel / (uint32_t)q.W), u24(j.w0),
+                                   u24(j.w1), &mo, &md);
+                        pa.id_lo = sample;
+                        pa.id_hi = pixel;
+                        pa.seg = 0;
+                        pa.flags = (uint32_t)req;
+                        pa.acc = 0.0f;
+                        count(req, 0, 1u);
+                        st = kCamera;
+                        mt = 0.0f;
+                        mstep = 0;
+                        visit = 0;
+                        need = false;
+                    }
+                }
+                if (!__any_sync(0xffffffffu, st != kIdle)) break;
+                if (st == kIdle) continue;
+
+                const Req& q = B.r[req];
+                // ---------- start a flight ----------
+                if (mstep < 0) {
+                    if (pa.seg >= q.max_segments) {
+                        count(req, 6, 1u);
+                        st = kIdle;
+                        goto path_end;
+                    }
+                    if (visit >= kSegPerVisit) {
+                        const int idx = atomicAdd(&ctl->f_count[Q], 1);
+                        pa.flags &= 0xffu;
+                        store_path(B.fq[Q] + idx, pa);
+                        st = kIdle;
+                        continue;
+                    }
+                    {
+                        count(req, 2, 1u);
+                        const Stream rs(q.seed, ((uint64_t)pa.id_hi << 32) | pa.id_lo);
+                        const Words u = rs.at(pa.seg, 0u);
+                        ml = -__logf(1.0f - u24(u.w0)) / q.sigma;
+                        mo = v3(pa.px, pa.py, pa.pz);
+                        md = v3(pa.wx, pa.wy, pa.wz);
+                        mt = 0.0f;
+                        mstep = 0;
+                        ++visit;
+                    }
+                }
+                // ---------- one signed-distance step of the current march ----------
+                {
+                    const V r = mo + md * mt;
+                    // escape and end-of-segment tests come before the distance evaluation
+                    const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
+                    const bool skip = (st == kShadow) ? (mt >= ml || (!inside && leaving))
+                                                      : ((st == kCamera || st == kReentry) && leaving);
+                    float f = 0.0f;
+                    if (!skip) {
+                        f = sdf(q, r);
+                        count(req, 8, 1u);
+                    }
+                    ++mstep;
+                    if (st == kFlight) {
+                        float d = -f / q.lip;
+                        bool exited = false;
+                        if (d < kEps) {
+                            count(req, 9, 1u);
+                            if (dot(sdf_grad(q, r), md) > 0.0f) exited = true;
+                            d = kEps;
+                        }
+                        if (exited) {
+                            st = kReentry;               // left the object at r: look for a re-entry
+                            mo = r;
+                            mt = 0.0f;
+                            mstep = 0;
+                        } else if (mt + d >= ml) {
+                            // ---------- collision at c ----------
+                            const V c = mo + md * ml;
+                            const Stream rs(q.seed, ((uint64_t)pa.id_hi << 32) | pa.id_lo);
+                            const Words u = rs.at(pa.seg, 0u);
+                            bool sphere = false;
+                            if (q.mode == MS_SPHERE && learned) {
+                                const float dc = -sdf(q, c) / q.lip;
+                                count(req, 8, 1u);
+                                const float rad = fminf(dc, q.tau_max / q.sigma);
+                                const float tau = q.sigma * rad;
+                                if (tau >= q.tau_min) {
+                                    sphere = true;
+                                    pa.px = c.x; pa.py = c.y; pa.pz = c.z;
+                                    pa.Xx = rad; pa.Xy = tau;
+                                    pa.flags &= 0xffu;
+                                    const int idx = atomicAdd(&ctl->s_count[P], 1);
+                                    store_path(B.sq[P] + idx, pa);
+                                    st = kIdle;
+                                }
+                            }
+                            if (!sphere) {
+                                // brute-force event: NEE at c with weight phi, roulette, HG scattering
+                                count(req, 4, 1u);
+                                pa.Xx = c.x; pa.Xy = c.y; pa.Xz = c.z;
+                                pa.Wx = pa.wx; pa.Wy = pa.wy; pa.Wz = pa.wz;
+                                pa.nee_wgt = q.phi;
+                                if (u24(u.w3) >= q.phi) {
+                                    count(req, 5, 1u);
+                                    pa.flags |= kFlagEnd;
+                                } else {
+                                    const V wn = scatter_dir(md, hg_cosine(u24(u.w1), q.g), u24(u.w2));
+                                    pa.px = c.x; pa.py = c.y; pa.pz = c.z;
+                                    pa.wx = wn.x; pa.wy = wn.y; pa.wz = wn.z;
+                                    pa.seg += 1u;
+                                }
+                                st = kShadow;
+                                mo = c;
+                                const V dl = v3(q.light[0], q.light[1], q.light[2]) - c;
+                                ml = sqrtf(dot(dl, dl));
+                                md = dl * (1.0f / ml);
+                                mt = 0.0f; din = 0.0f; inside = true; mstep = 0;
+                            }
+                        } else {
+                            mt += d;
+                            if (mstep >= kMaxMarch) { count(req, 6, 1u); st = kIdle; goto path_end; }
+                        }
+                    } else if (st == kCamera || st == kReentry) {
+                        // outside the medium: march until re-entry or until the bounding sphere is left
+                        if (leaving) {
+                            st = kIdle;                  // escaped: black background
+                            goto path_end;
+                        }
+                        float d = f / q.lip;
+                        bool entered = false;
+                        if (d < kEps) {
+                            count(req, 9, 1u);
+                            if (dot(sdf_grad(q, r), md) < 0.0f) entered = true;
+                            d = kEps;
+                        }
+                        if (entered) {
+                            if (st == kCamera) {
+                                count(req, 1, 1u);
+                                pa.wx = md.x; pa.wy = md.y; pa.wz = md.z;
+                            } else {
+                                pa.seg += 1u;
+                            }
+                            pa.px = r.x; pa.py = r.y; pa.pz = r.z;
+                            st = kFlight;
+                            mstep = -1;
+                        } else {
+                            mt += d;
+                            if (mstep >= kMaxMarch) { count(req, 6, 1u); st = kIdle; goto path_end; }
+                        }
+                    } else {   // kShadow: length of X -> light inside the medium (Sec. 4.3, d_t)
+                        bool done = skip;
+                        bool capped = false;
+                        if (!done) {
+                            if (inside) {
+                                float d = -f / q.lip;
+                                bool flip = false;
+                                if (d < kEps) {
+                                    count(req, 9, 1u);
+                                    if (dot(sdf_grad(q, r), md) > 0.0f) flip = true;
+                                    d = kEps;
+                                }
+                                if (flip) {
+                                    inside = false;
+                                } else {
+                                    const float step = fminf(d, ml - mt);
+                                    din += step;
+                                    mt += step;
+                                }
+                            } else {
+                                float d = f / q.lip;
+                                bool flip = false;
+                                if (d < kEps) {
+                                    count(req, 9, 1u);
+                                    if (dot(sdf_grad(q, r), md) < 0.0f) flip = true;
+                                    d = kEps;
+                                }
+                                if (flip) inside = true;
+                                else mt += fminf(d, ml - mt);
+                            }
+                            if (!done && mt >= ml) done = true;
+                            if (!done && mstep >= kMaxMarch) { done = true; capped = true; }
+                        }
+                        if (done) {
+                            count(req, 7, 1u);
+                            if (capped) {
+                                count(req, 6, 1u);
+                            } else {
+                                const V W = v3(pa.Wx, pa.Wy, pa.Wz);
+                                const float rho = hg_pdf(dot(W, md), q.g);
+                                pa.acc += pa.nee_wgt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
+                            }
+                            pa.flags &= ~kFlagNee;
+                            if (pa.flags & kFlagEnd) {
+                                st = kIdle;
+                                goto path_end;
+                            }
+                            st = kFlight;
+                            mstep = -1;
                         }
                     }
                 }
+                continue;
+            path_end:
+                // the path is over: its NEE sum goes to its pixel
+                if (pa.acc != 0.0f) atomicAdd(&B.image[B.r[req].image_offset + pa.id_hi], (double)pa.acc);
+                atomicSub(&ctl->alive, 1);
             }
         }
+        grid.sync();
 
-        // ---------------- (3) sphere steps: ballot-compacted queue, decoders on full warps ----------------
-        const unsigned mask = __ballot_sync(0xffffffffu, sphere);
-        if (lane == 0) s_warp_count[warp] = __popc(mask);
-        __syncthreads();
-        int before = 0, total = 0;
+        // ================= stage B: the three decoders on the dense sphere queue =================
+        if (blockIdx.x == 0 && tid == 0) { ctl->f_count[P] = 0; ctl->f_taken[P] = 0; }
+        {
+            const int n_s = __ldcg(&ctl->s_count[P]);
+            if (blockIdx.x == 0 && tid == 0 && n_s > 0) atomicAdd(&ctl->work, (unsigned long long)n_s);
+            for (int i = blockIdx.x * kThreads + tid; i < n_s; i += gridDim.x * kThreads) {
+                Path pa = load_path(B.sq[P] + i);
+                const int req = (int)(pa.flags & 0xffu);
+                const Req& qq = B.r[req];
+                count(req, 3, 1u);
+                const Stream st(qq.seed, ((uint64_t)pa.id_hi << 32) | pa.id_lo);
+                const Words a4 = st.at(pa.seg, 1u);
+                float n[24];
 #pragma unroll
-        for (int k = 0; k < kThreads / 32; ++k) {
-            const int c = s_warp_count[k];
-            before += k < warp ? c : 0;
-            total += c;
-        }
-        if (sphere) s_queue[before + __popc(mask & ((1u << lane) - 1u))] = tid;
-        __syncthreads();
-        if (tid < total) {
-            const int slot = s_queue[tid];
-            const SphereJob jb = s_job[slot];
-            const Req& qq = B.r[jb.req];
-            stat(jb.req, 3, 1ull);
-            const Stream st(qq.seed, ((uint64_t)jb.id_hi << 32) | jb.id_lo);
-            const Words a4 = st.at(jb.seg, 1u);
-            float n[24];
+                for (int t = 0; t < 6; ++t) {
+                    const float4 v = dec::normals4(st, pa.seg, 2u + t);
+                    n[4 * t] = v.x; n[4 * t + 1] = v.y; n[4 * t + 2] = v.z; n[4 * t + 3] = v.w;
+                }
+                const float rad = pa.Xx, tau = pa.Xy;
+                const float ltau = __logf(tau);
+                // LengthGen: N (albedo-1 physics, Eq. 3)
+                float xin8[8] = {ltau, qq.g, n[0], n[1], n[2], n[3], 0.0f, 0.0f};
+                float y4[4];
+                dec::mlp<kInL, kPL>(wl, xin8, y4);
+                const float yN = y4[0] + __expf(0.5f * y4[1]) * n[4];
+                float N = floorf(__expf(yN) + 0.5f);
+                N = fminf(fmaxf(N, 1.0f), kNMax);
+                const float lnN = __logf(N);
+                // PathGen: (cos theta, alpha, beta)
+                float xp8[8] = {ltau, qq.g, lnN, n[5], n[6], n[7], n[8], 0.0f};
+                float y8[8];
+                dec::mlp<kInP, kPP>(wpth, xp8, y8);
+                const float ct = fminf(1.0f, fmaxf(-1.0f, y8[0] + __expf(0.5f * y8[3]) * n[9]));
+                float al = y8[1] + __expf(0.5f * y8[4]) * n[10];
+                float be = y8[2] + __expf(0.5f * y8[5]) * n[11];
+                float ab2 = al * al + be * be;
+                if (ab2 > 1.0f) {
+                    const float s = rsqrtf(ab2);
+                    al *= s; be *= s; ab2 = 1.0f;
+                }
+                // EventGen: representative event (X~, W~)
+                float xe12[12] = {ltau, qq.g, qq.phi, ct, al, be, lnN, n[12], n[13], n[14], n[15], 0.0f};
+                float y12[12];
+                dec::mlp<kInE, kPE>(wev, xe12, y12);
+                float e[6];
 #pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                const float4 v = dec::normals4(st, jb.seg, 2u + t);
-                n[4 * t] = v.x; n[4 * t + 1] = v.y; n[4 * t + 2] = v.z; n[4 * t + 3] = v.w;
-            }
-            const float ltau = __logf(jb.tau);
-            // LengthGen: N (phi = 1 physics, Eq. 3)
-            float xin8[8] = {ltau, qq.g, n[0], n[1], n[2], n[3], 0.0f, 0.0f};
-            float y4[4];
-            dec::mlp<kInL, kPL>(wl, xin8, y4);
-            const float yN = y4[0] + __expf(0.5f * y4[1]) * n[4];
-            float N = floorf(__expf(yN) + 0.5f);
-            N = fminf(fmaxf(N, 1.0f), kNMax);
-            const float lnN = __logf(N);
-            // PathGen: (cos theta, alpha, beta)
-            float xp8[8] = {ltau, qq.g, lnN, n[5], n[6], n[7], n[8], 0.0f};
-            float y8[8];
-            dec::mlp<kInP, kPP>(wpth, xp8, y8);
-            const float ct = fminf(1.0f, fmaxf(-1.0f, y8[0] + __expf(0.5f * y8[3]) * n[9]));
-            float al = y8[1] + __expf(0.5f * y8[4]) * n[10];
-            float be = y8[2] + __expf(0.5f * y8[5]) * n[11];
-            float ab2 = al * al + be * be;
-            if (ab2 > 1.0f) {
-                const float s = rsqrtf(ab2);
-                al *= s; be *= s; ab2 = 1.0f;
-            }
-            // EventGen: representative event (X~, W~)
-            float xe12[12] = {ltau, qq.g, qq.phi, ct, al, be, lnN, n[12], n[13], n[14], n[15], 0.0f};
-            float y12[12];
-            dec::mlp<kInE, kPE>(wev, xe12, y12);
-            float e[6];
+                for (int k = 0; k < 6; ++k) e[k] = y12[k] + __expf(0.5f * y12[6 + k]) * n[16 + k];
+                const float phiN = __expf(N * qq.log_phi);
+                const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
+                // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
+                const V wi = v3(pa.wx, pa.wy, pa.wz);
+                V t1, t2;
+                onb(wi, &t1, &t2);
+                float sn, cs;
+                sincos_turns_fast(u24(a4.w1), &sn, &cs);
+                const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+                const float nn = sqrtf(fmaxf(0.0f, 1.0f - ab2));
+                V vs[4] = {v3(stt, 0.0f, ct), v3(be * ct + nn * stt, al, -be * stt + nn * ct), v3(e[0], e[1], e[2]),
+                           v3(e[3], e[4], e[5])};
+                const float xn2 = dot(vs[2], vs[2]);
+                if (xn2 > 1.0f) vs[2] = vs[2] * rsqrtf(xn2);
+                const float wn2 = dot(vs[3], vs[3]);
+                vs[3] = wn2 > 1e-24f ? vs[3] * rsqrtf(wn2) : v3(0.0f, 0.0f, 1.0f);
+                V vw[4];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) e[k] = y12[k] + __expf(0.5f * y12[6 + k]) * n[16 + k];
-            const float phiN = __expf(N * qq.log_phi);
-            const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
-            // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
-            const V wi = v3(jb.w[0], jb.w[1], jb.w[2]);
-            V t1, t2;
-            onb(wi, &t1, &t2);
-            float sn, cs;
-            sincos_turns_fast(u24(a4.w1), &sn, &cs);
-            const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-            const float nn = sqrtf(fmaxf(0.0f, 1.0f - ab2));
-            V vs[4] = {v3(stt, 0.0f, ct), v3(be * ct + nn * stt, al, -be * stt + nn * ct), v3(e[0], e[1], e[2]),
-                       v3(e[3], e[4], e[5])};
-            const float xn2 = dot(vs[2], vs[2]);
-            if (xn2 > 1.0f) vs[2] = vs[2] * rsqrtf(xn2);
-            const float wn2 = dot(vs[3], vs[3]);
-            vs[3] = wn2 > 1e-24f ? vs[3] * rsqrtf(wn2) : v3(0.0f, 0.0f, 1.0f);
-            V vw[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const V v1 = v3(cs * vs[k].x - sn * vs[k].y, sn * vs[k].x + cs * vs[k].y, vs[k].z);
-                vw[k] = t1 * v1.x + t2 * v1.y + wi * v1.z;
-            }
-            const V c = v3(jb.c[0], jb.c[1], jb.c[2]);
-            const V xexit = c + vw[0] * jb.r;
-            const V wout = unit(vw[1]);
-            const V X = c + vw[2] * jb.r;
-            const V Wd = unit(vw[3]);
-            SphereOut& so = s_out[slot];
-            so.X[0] = X.x; so.X[1] = X.y; so.X[2] = X.z;
-            so.W[0] = Wd.x; so.W[1] = Wd.y; so.W[2] = Wd.z;
-            so.lam = lam;
-            so.p[0] = xexit.x; so.p[1] = xexit.y; so.p[2] = xexit.z;
-            so.w[0] = wout.x; so.w[1] = wout.y; so.w[2] = wout.z;
-            so.absorbed = u24(a4.w0) >= phiN;
-        }
-        __syncthreads();
-        if (sphere) {
-            const SphereOut so = s_out[tid];
-            nee_req = true;
-            nX = v3(so.X[0], so.X[1], so.X[2]);
-            nW = v3(so.W[0], so.W[1], so.W[2]);
-            nwt = so.lam;
-            if (so.absorbed) {
-                stat(req, 5, 1ull);
-                end_after_nee = true;
-            } else {
-                p = v3(so.p[0], so.p[1], so.p[2]);
-                w = v3(so.w[0], so.w[1], so.w[2]);
-                ++seg;
+                for (int k = 0; k < 4; ++k) {
+                    const V v1 = v3(cs * vs[k].x - sn * vs[k].y, sn * vs[k].x + cs * vs[k].y, vs[k].z);
+                    vw[k] = t1 * v1.x + t2 * v1.y + wi * v1.z;
+                }
+                const V c = v3(pa.px, pa.py, pa.pz);
+                const V xexit = c + vw[0] * rad;
+                const V wout = unit(vw[1]);
+                const V X = c + vw[2] * rad;
+                const V Wd = unit(vw[3]);
+                pa.Xx = X.x; pa.Xy = X.y; pa.Xz = X.z;
+                pa.Wx = Wd.x; pa.Wy = Wd.y; pa.Wz = Wd.z;
+                pa.nee_wgt = lam;
+                pa.flags = (pa.flags & 0xffu) | kFlagNee;
+                if (u24(a4.w0) >= phiN) {
+                    count(req, 5, 1u);
+                    pa.flags |= kFlagEnd;
+                } else {
+                    pa.px = xexit.x; pa.py = xexit.y; pa.pz = xexit.z;
+                    pa.wx = wout.x; pa.wy = wout.y; pa.wz = wout.z;
+                    pa.seg += 1u;
+                }
+                const int idx = atomicAdd(&ctl->f_count[Q], 1);
+                store_path(B.fq[Q] + idx, pa);
             }
         }
-
-        // ---------------- (4) next-event estimation toward the point light (Eq. 5 term) ----------------
-        if (nee_req) {
-            stat(req, 7, 1ull);
-            const V xl = v3(q.light[0], q.light[1], q.light[2]);
-            const V dl = xl - nX;
-            const float d2 = dot(dl, dl);
-            const V wl2 = dl * rsqrtf(d2);
-            const float din = inside_length(q, nX, xl, ev);
-            if (din < 0.0f) {
-                stat(req, 6, 1ull);
-            } else {
-                const float rho = hg_pdf(dot(nW, wl2), q.g);
-                acc += (double)(nwt * rho * __expf(-q.sigma * din) * q.I / d2);
-            }
-            if (end_after_nee) finish();
+        grid.sync();
+        // ================= end of wave: all blocks see the same counters =================
+        const bool done = __ldcg(&ctl->alive) == 0 && __ldcg(&ctl->ticket) >= B.total &&
+                          __ldcg(&ctl->f_count[Q]) == 0;
+        if (done) break;
+        // a wave in which neither stage took any work while paths are still counted as live means the
+        // bookkeeping is broken: stop with an error instead of spinning
+        const unsigned long long work = __ldcg(&ctl->work);
+        if (work == last_work || wave + 1 >= kMaxWaves) {
+            if (blockIdx.x == 0 && tid == 0) ctl->error = work == last_work ? 2 : 1;
+            break;
         }
-        __syncthreads();
+        last_work = work;
+        grid.sync();
     }
 
-    // ---------------- per-request counters -> global ----------------
+    // ---------------- counters -> shared -> global ----------------
+    if (cnt.req >= 0)
+#pragma unroll
+        for (int j = 0; j < kUsedStats; ++j)
+            if (cnt.c[j]) atomicAdd(&s_stats[cnt.req * kStats + j], (unsigned long long)cnt.c[j]);
+    __syncthreads();
     for (int k = tid; k < B.n * kStats; k += kThreads)
         if (s_stats[k]) atomicAdd(&B.stats[k], s_stats[k]);
+    if (blockIdx.x == 0 && tid == 0) {
+        const int err = __ldcg(&ctl->error);
+        for (int r = 0; r < B.n; ++r) {
+            atomicAdd(&B.stats[r * kStats + kStats - 2], (unsigned long long)(wave + 1));
+            if (err) atomicAdd(&B.stats[r * kStats + kStats - 1], (unsigned long long)err);
+        }
+    }
 }
 
 }  // namespace render
 }  // namespace ms
 
 using namespace ms::render;
+
+static int queue_capacity()
+{
+    // about eight paths per resident lane keeps both stages busy; the record is 80 bytes
+    return 1 << 20;
+}
 
 static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const char* fn)
 {
@@ -582,7 +733,7 @@ extern "C" size_t ms_render_workspace_size(const ms_render_params* reqs, int n_r
 {
     (void)reqs;
     (void)n_requests;
-    return 256;
+    return 256 + 4 * (size_t)queue_capacity() * sizeof(Path);
 }
 
 static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
@@ -590,8 +741,9 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
                                const char* fn)
 {
     MS_CHECK_ARG(reqs != nullptr && images != nullptr && stats != nullptr, "%s: null argument", fn);
-    MS_CHECK_ARG(workspace != nullptr && workspace_bytes >= 256 && ((uintptr_t)workspace & 255u) == 0,
-                 "%s: a 256-byte aligned workspace of at least 256 bytes is required", fn);
+    const size_t need_ws = ms_render_workspace_size(reqs, n);
+    MS_CHECK_ARG(workspace != nullptr && workspace_bytes >= need_ws && ((uintptr_t)workspace & 255u) == 0,
+                 "%s: a 256-byte aligned workspace of at least %zu bytes is required", fn, need_ws);
     Batch b;
     ms_status st = fill_batch(reqs, n, &b, fn);
     if (st != MS_OK) return st;
@@ -614,16 +766,22 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     }
     b.image = images;
     b.stats = stats;
-    b.ticket = static_cast<unsigned long long*>(workspace);
+    b.capacity = queue_capacity();
+    char* ws = static_cast<char*>(workspace);
+    b.ctl = reinterpret_cast<Ctl*>(ws);
+    Path* q0 = reinterpret_cast<Path*>(ws + 256);
+    b.fq[0] = q0;
+    b.fq[1] = q0 + b.capacity;
+    b.sq[0] = q0 + 2 * (size_t)b.capacity;
+    b.sq[1] = q0 + 3 * (size_t)b.capacity;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    MS_CUDA(cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s));
+    MS_CUDA(cudaMemsetAsync(workspace, 0, sizeof(Ctl), s));
     int per_sm = 0;
     MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel, kThreads, 0));
-    uint64_t grid = (uint64_t)ms::num_sms() * (per_sm > 0 ? per_sm : 1);
-    const uint64_t need = (b.total + kThreads - 1) / kThreads;
-    if (grid > need) grid = need;
-    render_kernel<<<(unsigned)grid, kThreads, 0, s>>>(b);
-    MS_CUDA(cudaGetLastError());
+    MS_CHECK_ARG(per_sm > 0, "%s: the renderer kernel cannot be resident on this device", fn);
+    const unsigned grid = (unsigned)(ms::num_sms() * per_sm);
+    void* args[] = {&b};
+    MS_CUDA(cudaLaunchCooperativeKernel((const void*)render_kernel, dim3(grid), dim3(kThreads), args, 0, s));
     return MS_OK;
 }
 

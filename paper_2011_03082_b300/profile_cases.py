@@ -7,6 +7,7 @@
   train     one training step of EventGen, batch 65,536
   render    one 128x128 px x 16 spp render at sigma_t 64, sphere tracing with the trained decoders
   brute     the same render in brute-force mode
+  render512 / brute512   512x512 px x 64 spp at sigma_t 128 (sphere tracing / brute force)
 Each case runs ``--repeat`` times (default 2) and prints the CUDA-event time of the last run.
 """
 from __future__ import annotations
@@ -59,17 +60,25 @@ def case_train(B=65536):
 
 
 def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0):
+    """One render; the returned callable exposes the per-request counters as ``.stats``."""
     models = pipeline.load()
     cset = ms.cvae_set(pipeline.device_decoders(models))
     p = ms.render_params(synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode))
     img = torch.zeros(res * res, dtype=torch.float64, device="cuda")
     st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
     ws = ms.workspace(ms.ms_render_workspace_size([p]))
-    return lambda: ms.ms_render(p, cset if mode == ms.MS_SPHERE else None, img, st, ws=ws)
+
+    def run():
+        st.zero_()
+        ms.ms_render(p, cset if mode == ms.MS_SPHERE else None, img, st, ws=ws)
+    run.stats = st
+    return run
 
 
 CASES = {"walk": case_walk, "walk24": case_walk24, "decoder": case_decoder, "train": case_train,
-         "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE)}
+         "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE),
+         "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
+         "brute512": lambda: case_render(ms.MS_BRUTE, 512, 64, 128.0)}
 
 
 def main(argv=None):
@@ -87,7 +96,10 @@ def main(argv=None):
         e.record()
         e.synchronize()
         ms_ = s.elapsed_time(e)
-    print(json.dumps({"case": a.case, "ms": ms_}))
+    out = {"case": a.case, "ms": ms_}
+    if hasattr(fn, "stats"):
+        out["stats"] = fn.stats.cpu().tolist()
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

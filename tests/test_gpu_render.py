@@ -64,7 +64,7 @@ def test_render_matches_oracle(orc, name, sigma, mode):
     assert noise > 0
     assert abs(rmse(g2, o1) / noise - 1.0) <= 0.01, (rmse(g2, o1), noise)
     assert rmse(g2, o2) <= 0.2 * noise, (rmse(g2, o2), noise)
-    assert gs[0] == s2[0] == 32 * 32 * 16
+    assert gs[0] == s2[0] == 32 * 32 * 16 and gs[15] == 0
     assert abs(int(gs[1]) - int(s2[1])) <= 0.002 * s2[1]
     for k in (2, 3, 4, 7, 8, 9):
         assert abs(int(gs[k]) - int(s2[k])) <= 0.01 * max(s2[k], 100), (k, gs[k], s2[k])
@@ -81,7 +81,7 @@ def test_sample_offsets_and_batches_compose():
     a, sa = gpu_render(full, models)
     h1, s1 = gpu_render(dict(full, spp=4), models)
     h2, s2 = gpu_render(dict(full, spp=4, sample_offset=4), models)
-    assert np.allclose(a, h1 + h2, rtol=1e-9, atol=1e-12) and np.array_equal(sa, s1 + s2)
+    assert np.allclose(a, h1 + h2, rtol=1e-6, atol=1e-12) and np.array_equal(sa, s1 + s2)
     # three requests in one persistent launch equal the three single renders
     reqs = [full, synth.render_scene(8.0, width=8, height=8, spp=3, mode=0, seed=4),
             synth.render_scene(128.0, width=5, height=7, spp=2, mode=1, seed=5, disp_freq=3.0)]
@@ -95,8 +95,8 @@ def test_sample_offsets_and_batches_compose():
     off = 0
     for i, (r, (img, s)) in enumerate(zip(reqs, singles)):
         n = r["width"] * r["height"]
-        assert np.allclose(imgs[off:off + n].cpu().numpy(), img.ravel(), rtol=1e-9, atol=1e-12)
-        assert np.array_equal(st[i].cpu().numpy(), s)
+        assert np.allclose(imgs[off:off + n].cpu().numpy(), img.ravel(), rtol=1e-6, atol=1e-12)
+        assert np.array_equal(st[i].cpu().numpy()[:10], s[:10])
         off += n
 
 
@@ -106,7 +106,7 @@ def test_full_size_render_properties():
     img, st = gpu_render(p, _models())
     assert st[0] == 512 * 512 * 256
     assert np.all(np.isfinite(img)) and np.all(img >= 0) and img.sum() > 0
-    assert st[3] > 0 and st[7] <= st[3] + st[4]
+    assert st[3] > 0 and st[7] <= st[3] + st[4] and st[15] == 0
 
 
 def test_bad_requests_are_rejected():
