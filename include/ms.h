@@ -216,11 +216,9 @@ size_t ms_render_workspace_size(const ms_render_params* reqs, int n_requests);
 /* image: device [height][width] doubles, accumulated: the sum over the pixel's samples (divide by spp).
  * stats: device [MS_RENDER_STATS] accumulated: [0] camera paths, [1] paths entering the object, [2] flights,
  * [3] sphere steps, [4] brute-force events, [5] absorbed, [6] truncated paths or dropped estimates,
- * [7] next-event estimates, [8] SDF distance evaluations, [9] SDF gradient evaluations, [10..13] zero,
- * [14] waves (stage-A/stage-B rounds) of the launch, [15] launch status: 0 when the launch completed, nonzero when it stopped early (1: wave limit, 2: no
- * progress) — the image is then incomplete.  models: host struct with device weight pointers (ignored in
- * MS_BRUTE).  workspace: ms_render_workspace_size() bytes (path queues); the launch is cooperative (one
- * resident wave of blocks) and is asynchronous. */
+ * [7] next-event estimates, [8] SDF distance evaluations, [9] SDF gradient evaluations, [10..15] zero.
+ * models: host struct with device weight pointers (ignored in MS_BRUTE).  workspace:
+ * ms_render_workspace_size() bytes (the sample ticket).  One persistent launch; asynchronous. */
 #define MS_RENDER_STATS 16
 ms_status ms_render(const ms_render_params* p, const ms_cvae_set* models, double* image,
                     unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);

@@ -8,29 +8,23 @@
 // with weight Lambda^(N) — or, in thin regions and in brute-force mode, one scattering event with NEE weight
 // phi, Russian roulette and HG scattering.
 //
-// Kernel design: one cooperative persistent launch (any number of requests) that runs waves of two stages
-// separated by grid-wide barriers, over path records kept in global queues (the workspace):
-//  * stage A (marching): every lane runs a small state machine — camera march, free-flight march, re-entry
-//    march, shadow march — advancing ONE signed-distance step per loop iteration; when a lane's march ends
-//    it finishes that piece of work (brute-force event, NEE contribution, path end, hand-off) and takes new
-//    work at once (a path returning from stage B, else a new camera sample), so warps stay converged on the
-//    same short loop body however long the individual marches are.  A path stays in its lane through its
-//    brute-force events; it leaves when it needs a sphere step (-> sphere queue), after kSegPerVisit
-//    flights (-> flight queue, bounds the stage's tail) or when it ends;
-//  * stage B (decoders): the sphere queue is dense, so the three decoder MLPs run on full warps with weights
-//    in shared memory (broadcast float4 loads, decoder.cuh); results go back to the flight queue carrying a
-//    pending NEE request that stage A resolves first;
-//  * queue indices come from warp-aggregated atomics (__ballot_sync / __popc); the number of live paths is
-//    capped by the queue capacity; a path's NEE sum stays in its record and is added to its pixel (double)
-//    once; counters are per-lane registers flushed to shared, then global, memory;
-//  * everything is bounded: segments per path, steps per march, waves per launch (error flag if exceeded).
+// Kernel design (persistent; one launch for any number of requests; warps fully independent):
+//  * every lane owns one path and runs a small state machine — camera march, free-flight march, re-entry
+//    march, shadow march, decode — advancing one signed-distance step per loop iteration, so a warp stays
+//    converged on the same short loop body however long the individual marches are; a lane whose path ends
+//    takes the next camera sample at once (warp-aggregated ticket);
+//  * a lane that reaches a sphere step parks in the decode state; the warp runs the three decoder MLPs only
+//    when at least kDecodeBatch of its lanes are parked (or nothing else is marching), so the decoders —
+//    weights in shared memory, broadcast float4 loads (decoder.cuh) — run on mostly full warps while the
+//    other lanes keep marching, with no block or grid barrier in the loop;
+//  * a path's NEE sum is kept in a register and added to its pixel (double) once; counters are per-lane
+//    registers flushed to shared, then global, memory;
+//  * everything is bounded: segments per path, steps per march, and the loop ends when the ticket is drained
+//    and no lane holds a path.
 #include <cmath>
-#include <cooperative_groups.h>
 
 #include "decoder.cuh"
 #include "ms_device.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace ms {
 namespace render {
@@ -39,10 +33,9 @@ constexpr int kThreads = 256;
 constexpr int kMaxReq = 64;
 constexpr int kStats = MS_RENDER_STATS;
 constexpr float kEps = 1e-4f;       // distance from the boundary treated as on it
-constexpr int kMaxMarch = 1024;     // steps per march; running out ends the path
+constexpr int kMaxMarch = 1024;     // steps per march; running out ends the path (or drops the estimate)
 constexpr float kNMax = 16777216.0f;
-constexpr uint32_t kSegPerVisit = 64;
-constexpr uint64_t kMaxWaves = 1ull << 24;
+constexpr int kDecodeBatch = 16;    // parked lanes that trigger a decoder round
 
 struct Req {
     float cam[3], at[3], tan_half, aspect;
@@ -54,30 +47,8 @@ struct Req {
     uint64_t seed, sample_offset, image_offset, samples_begin;
 };
 
-// One path in a queue (80 bytes, five 16-byte words).
-struct __align__(16) Path {
-    float px, py, pz, wx;
-    float wy, wz;
-    uint32_t id_lo, id_hi;
-    uint32_t seg, flags;            // flags: request (bits 0-7), pending NEE (bit 8), ends after NEE (bit 9)
-    float acc, nee_wgt;
-    float Xx, Xy, Xz, Wx;           // pending NEE request (X, W); sphere jobs keep r, tau in Xx, Xy
-    float Wy, Wz, pad0, pad1;
-};
-constexpr uint32_t kFlagNee = 1u << 8, kFlagEnd = 1u << 9;
-
-struct Ctl {                         // in the workspace, zeroed before the launch
-    unsigned long long ticket;
-    unsigned long long work;         // items taken by either stage (progress check)
-    int alive;
-    int error;
-    int f_count[2], f_taken[2];
-    int s_count[2], s_taken[2];
-};
-
 struct Batch {
     int n;
-    int capacity;                    // paths per queue
     uint64_t total;
     Req r[kMaxReq];
     const float* wL;                 // decoder weights LengthGen, PathGen, EventGen (null: brute force only)
@@ -85,9 +56,7 @@ struct Batch {
     const float* wE;
     double* image;
     unsigned long long* stats;       // [n][kStats]
-    Ctl* ctl;
-    Path* fq[2];                     // flight queues (by wave parity)
-    Path* sq[2];                     // sphere queues (by wave parity)
+    unsigned long long* ticket;
 };
 
 // decoder shapes: LengthGen (2 + 4 -> 1), PathGen (3 + 4 -> 3), EventGen (7 + 4 -> 6)
@@ -175,37 +144,6 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
     return lo;
 }
 
-// Warp-aggregated slot reservation: each lane with `want` gets a distinct index from *counter.
-__device__ __forceinline__ int warp_push_index(int* counter, bool want)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (m == 0u) return -1;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return want ? base + __popc(m & ((1u << lane) - 1u)) : -1;
-}
-
-__device__ __forceinline__ void store_path(Path* dst, const Path& p)
-{
-    const float4* s = reinterpret_cast<const float4*>(&p);
-    float4* d = reinterpret_cast<float4*>(dst);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) d[k] = s[k];
-}
-
-__device__ __forceinline__ Path load_path(const Path* src)
-{
-    Path p;
-    const float4* s = reinterpret_cast<const float4*>(src);
-    float4* d = reinterpret_cast<float4*>(&p);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) d[k] = __ldcg(s + k);
-    return p;
-}
-
 // Per-lane counters of the request the lane is currently serving, flushed to shared memory on change.
 constexpr int kUsedStats = 10;
 struct Counters {
@@ -213,13 +151,12 @@ struct Counters {
     unsigned c[kUsedStats] = {};
 };
 
-enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow };
+enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow, kDecode };
 
 __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_constant__ Batch B)
 {
     __shared__ __align__(16) float sw[kSmemL + kSmemP + kSmemE];
     __shared__ unsigned long long s_stats[kMaxReq * kStats];
-    cg::grid_group grid = cg::this_grid();
     const int tid = threadIdx.x, lane = tid & 31;
     const bool learned = B.wL != nullptr;
     float* wl = sw;
@@ -233,7 +170,6 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     __syncthreads();
 
-    Ctl* ctl = B.ctl;
     Counters cnt;
     auto count = [&](int req, int k, unsigned v) {
         if (req != cnt.req) {
@@ -245,320 +181,106 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
         }
         cnt.c[k] += v;
     };
-    bool drained = false;   // warp-uniform: camera tickets exhausted
-    unsigned long long last_work = ~0ull;
 
-    uint64_t wave = 0;
-    for (;; ++wave) {
-        const int P = (int)(wave & 1ull), Q = P ^ 1;
-        // ================= stage A: marching state machine =================
-        if (blockIdx.x == 0 && tid == 0) { ctl->s_count[Q] = 0; ctl->s_taken[Q] = 0; }
+    // ---- the lane's path ----
+    int st = kIdle, req = 0;
+    uint32_t id_lo = 0, id_hi = 0, seg = 0;
+    V p = v3(0, 0, 0), w = v3(0, 0, 1);        // position and direction of the path
+    float acc = 0.0f;                           // NEE sum of the path
+    V nX = v3(0, 0, 0), nW = v3(0, 0, 1);       // pending NEE request
+    float nwt = 0.0f;
+    bool end_after = false;                     // the path ends after its pending NEE
+    float rad = 0.0f, tau = 0.0f;               // sphere of a parked (decode) lane
+    // ---- the lane's current march ----
+    V mo = v3(0, 0, 0), md = v3(0, 0, 1);
+    float mt = 0.0f, ml = 0.0f, din = 0.0f;
+    int mstep = 0;
+    bool inside = true;
+    bool drained = false;                       // warp-uniform: camera tickets exhausted
+
+    auto start_shadow = [&]() {
+        const Req& q = B.r[req];
+        mo = nX;
+        const V dl = v3(q.light[0], q.light[1], q.light[2]) - nX;
+        ml = sqrtf(dot(dl, dl));
+        md = dl * (1.0f / ml);
+        mt = 0.0f;
+        din = 0.0f;
+        inside = true;
+        mstep = 0;
+        st = kShadow;
+    };
+    // begins the next flight of the path, or ends it at the segment cap; returns false when the path ended
+    auto start_flight = [&]() -> bool {
+        const Req& q = B.r[req];
+        if (seg >= q.max_segments) {
+            count(req, 6, 1u);
+            return false;
+        }
+        count(req, 2, 1u);
+        const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
+        const Words u = rs.at(seg, 0u);
+        ml = -__logf(1.0f - u24(u.w0)) / q.sigma;
+        mo = p;
+        md = w;
+        mt = 0.0f;
+        mstep = 0;
+        st = kFlight;
+        return true;
+    };
+    auto end_path = [&]() {
+        if (acc != 0.0f) atomicAdd(&B.image[B.r[req].image_offset + id_hi], (double)acc);
+        st = kIdle;
+    };
+
+    for (;;) {
+        // ---------------- refill idle lanes with new camera samples ----------------
         {
-            Path pa;                                   // the lane's path
-            int st = kIdle;
-            int req = 0;
-            V mo = v3(0, 0, 0), md = v3(0, 0, 1);      // march origin / direction
-            float mt = 0.0f, ml = 0.0f, din = 0.0f;    // march parameter, flight length or segment length
-            int mstep = 0;
-            bool inside = true;
-            uint32_t visit = 0;                        // flights in this visit
-            const int f_in = __ldcg(&ctl->f_count[P]);
-            bool f_left = true;                        // warp-uniform: flight queue not yet drained
-            bool room = true;                          // warp-uniform: the queues can take new paths
-            for (;;) {
-                // ---------- refill idle lanes: returning paths first, then new camera samples ----------
-                bool need = st == kIdle;
-                unsigned m = __ballot_sync(0xffffffffu, need);
-                if (m && f_left) {
-                    const int leader = __ffs(m) - 1;
-                    int base = 0;
-                    if (lane == leader) base = atomicAdd(&ctl->f_taken[P], __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    const int avail = max(0, min(__popc(m), f_in - base));
-                    if (avail < __popc(m)) f_left = false;
-                    if (lane == leader && avail > 0) atomicAdd(&ctl->work, (unsigned long long)avail);
-                    const int rank = __popc(m & ((1u << lane) - 1u));
-                    if (need && rank < avail) {
-                        pa = load_path(B.fq[P] + base + rank);
-                        req = (int)(pa.flags & 0xffu);
-                        visit = 0;
-                        need = false;
-                        if (pa.flags & kFlagNee) {
-                            st = kShadow;
-                            mo = v3(pa.Xx, pa.Xy, pa.Xz);
-                            const Req& q = B.r[req];
-                            const V dl = v3(q.light[0], q.light[1], q.light[2]) - mo;
-                            ml = sqrtf(dot(dl, dl));
-                            md = dl * (1.0f / ml);
-                            mt = 0.0f; din = 0.0f; inside = true; mstep = 0;
-                        } else {
-                            st = kFlight;
-                            mstep = -1;                // start a flight below
-                        }
-                    }
-                    m = __ballot_sync(0xffffffffu, need);
+            const unsigned m = __ballot_sync(0xffffffffu, st == kIdle);
+            if (m && !drained) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long t0 = 0;
+                if (lane == leader) t0 = atomicAdd(B.ticket, (unsigned long long)__popc(m));
+                t0 = __shfl_sync(0xffffffffu, t0, leader);
+                if (t0 + __popc(m) >= B.total) drained = true;
+                const uint64_t t = t0 + __popc(m & ((1u << lane) - 1u));
+                if (st == kIdle && t < B.total) {
+                    req = find_req(B, t);
+                    const Req& q = B.r[req];
+                    const uint64_t local = t - q.samples_begin;
+                    id_hi = (uint32_t)(local / q.spp);
+                    id_lo = (uint32_t)(q.sample_offset + local % q.spp);
+                    const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
+                    const Words j = rs.at(0u, 8u);
+                    camera_ray(q, (int)(id_hi % (uint32_t)q.W), (int)(id_hi / (uint32_t)q.W), u24(j.w0), u24(j.w1),
+                               &mo, &md);
+                    seg = 0;
+                    acc = 0.0f;
+                    end_after = false;
+                    mt = 0.0f;
+                    mstep = 0;
+                    st = kCamera;
+                    count(req, 0, 1u);
                 }
-                if (m && !drained && room) {
-                    const int leader = __ffs(m) - 1;
-                    const int k = __popc(m);
-                    int got = 0, flags = 0;   // flags: 1 tickets exhausted, 2 queues full
-                    unsigned long long t0 = 0;
-                    if (lane == leader) {
-                        const int old = atomicAdd(&ctl->alive, k);
-                        const int grant = min(k, max(0, B.capacity - old));
-                        if (grant < k) {
-                            atomicSub(&ctl->alive, k - grant);
-                            flags |= 2;
-                        }
-                        if (grant > 0) {
-                            t0 = atomicAdd(&ctl->ticket, (unsigned long long)grant);
-                            const unsigned long long left = t0 < B.total ? B.total - t0 : 0ull;
-                            got = (int)min((unsigned long long)grant, left);
-                            if (got < grant) atomicSub(&ctl->alive, grant - got);
-                            if (t0 + (unsigned long long)grant >= B.total) flags |= 1;
-                            if (got > 0) atomicAdd(&ctl->work, (unsigned long long)got);
-                        }
-                    }
-                    got = __shfl_sync(0xffffffffu, got, leader);
-                    flags = __shfl_sync(0xffffffffu, flags, leader);
-                    t0 = __shfl_sync(0xffffffffu, t0, leader);
-                    if (flags & 1) drained = true;
-                    if (flags & 2) room = false;
-                    const int rank = __popc(m & ((1u << lane) - 1u));
-                    if (need && rank < got) {
-                        const uint64_t t = t0 + rank;
-                        req = find_req(B, t);
-                        const Req& q = B.r[req];
-                        const uint64_t local = t - q.samples_begin;
-                        const uint32_t pixel = (uint32_t)(local / q.spp);
-                        const uint32_t sample = (uint32_t)(q.sample_offset + local % q.spp);
-                        const Stream rs(q.seed, ((uint64_t)pixel << 32) | sample);
-                        const Words j = rs.at(0u, 8u);
-                        camera_ray(q, (int)(pixel % (uint32_t)q.W), (int)(pixel / (uint32_t)q.W), u24(j.w0),
-                                   u24(j.w1), &mo, &md);
-                        pa.id_lo = sample;
-                        pa.id_hi = pixel;
-                        pa.seg = 0;
-                        pa.flags = (uint32_t)req;
-                        pa.acc = 0.0f;
-                        count(req, 0, 1u);
-                        st = kCamera;
-                        mt = 0.0f;
-                        mstep = 0;
-                        visit = 0;
-                        need = false;
-                    }
-                }
-                if (!__any_sync(0xffffffffu, st != kIdle)) break;
-                if (st == kIdle) continue;
-
-                const Req& q = B.r[req];
-                // ---------- start a flight ----------
-                if (mstep < 0) {
-                    if (pa.seg >= q.max_segments) {
-                        count(req, 6, 1u);
-                        st = kIdle;
-                        goto path_end;
-                    }
-                    if (visit >= kSegPerVisit) {
-                        const int idx = atomicAdd(&ctl->f_count[Q], 1);
-                        pa.flags &= 0xffu;
-                        store_path(B.fq[Q] + idx, pa);
-                        st = kIdle;
-                        continue;
-                    }
-                    {
-                        count(req, 2, 1u);
-                        const Stream rs(q.seed, ((uint64_t)pa.id_hi << 32) | pa.id_lo);
-                        const Words u = rs.at(pa.seg, 0u);
-                        ml = -__logf(1.0f - u24(u.w0)) / q.sigma;
-                        mo = v3(pa.px, pa.py, pa.pz);
-                        md = v3(pa.wx, pa.wy, pa.wz);
-                        mt = 0.0f;
-                        mstep = 0;
-                        ++visit;
-                    }
-                }
-                // ---------- one signed-distance step of the current march ----------
-                {
-                    const V r = mo + md * mt;
-                    // escape and end-of-segment tests come before the distance evaluation
-                    const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
-                    const bool skip = (st == kShadow) ? (mt >= ml || (!inside && leaving))
-                                                      : ((st == kCamera || st == kReentry) && leaving);
-                    float f = 0.0f;
-                    if (!skip) {
-                        f = sdf(q, r);
-                        count(req, 8, 1u);
-                    }
-                    ++mstep;
-                    if (st == kFlight) {
-                        float d = -f / q.lip;
-                        bool exited = false;
-                        if (d < kEps) {
-                            count(req, 9, 1u);
-                            if (dot(sdf_grad(q, r), md) > 0.0f) exited = true;
-                            d = kEps;
-                        }
-                        if (exited) {
-                            st = kReentry;               // left the object at r: look for a re-entry
-                            mo = r;
-                            mt = 0.0f;
-                            mstep = 0;
-                        } else if (mt + d >= ml) {
-                            // ---------- collision at c ----------
-                            const V c = mo + md * ml;
-                            const Stream rs(q.seed, ((uint64_t)pa.id_hi << 32) | pa.id_lo);
-                            const Words u = rs.at(pa.seg, 0u);
-                            bool sphere = false;
-                            if (q.mode == MS_SPHERE && learned) {
-                                const float dc = -sdf(q, c) / q.lip;
-                                count(req, 8, 1u);
-                                const float rad = fminf(dc, q.tau_max / q.sigma);
-                                const float tau = q.sigma * rad;
-                                if (tau >= q.tau_min) {
-                                    sphere = true;
-                                    pa.px = c.x; pa.py = c.y; pa.pz = c.z;
-                                    pa.Xx = rad; pa.Xy = tau;
-                                    pa.flags &= 0xffu;
-                                    const int idx = atomicAdd(&ctl->s_count[P], 1);
-                                    store_path(B.sq[P] + idx, pa);
-                                    st = kIdle;
-                                }
-                            }
-                            if (!sphere) {
-                                // brute-force event: NEE at c with weight phi, roulette, HG scattering
-                                count(req, 4, 1u);
-                                pa.Xx = c.x; pa.Xy = c.y; pa.Xz = c.z;
-                                pa.Wx = pa.wx; pa.Wy = pa.wy; pa.Wz = pa.wz;
-                                pa.nee_wgt = q.phi;
-                                if (u24(u.w3) >= q.phi) {
-                                    count(req, 5, 1u);
-                                    pa.flags |= kFlagEnd;
-                                } else {
-                                    const V wn = scatter_dir(md, hg_cosine(u24(u.w1), q.g), u24(u.w2));
-                                    pa.px = c.x; pa.py = c.y; pa.pz = c.z;
-                                    pa.wx = wn.x; pa.wy = wn.y; pa.wz = wn.z;
-                                    pa.seg += 1u;
-                                }
-                                st = kShadow;
-                                mo = c;
-                                const V dl = v3(q.light[0], q.light[1], q.light[2]) - c;
-                                ml = sqrtf(dot(dl, dl));
-                                md = dl * (1.0f / ml);
-                                mt = 0.0f; din = 0.0f; inside = true; mstep = 0;
-                            }
-                        } else {
-                            mt += d;
-                            if (mstep >= kMaxMarch) { count(req, 6, 1u); st = kIdle; goto path_end; }
-                        }
-                    } else if (st == kCamera || st == kReentry) {
-                        // outside the medium: march until re-entry or until the bounding sphere is left
-                        if (leaving) {
-                            st = kIdle;                  // escaped: black background
-                            goto path_end;
-                        }
-                        float d = f / q.lip;
-                        bool entered = false;
-                        if (d < kEps) {
-                            count(req, 9, 1u);
-                            if (dot(sdf_grad(q, r), md) < 0.0f) entered = true;
-                            d = kEps;
-                        }
-                        if (entered) {
-                            if (st == kCamera) {
-                                count(req, 1, 1u);
-                                pa.wx = md.x; pa.wy = md.y; pa.wz = md.z;
-                            } else {
-                                pa.seg += 1u;
-                            }
-                            pa.px = r.x; pa.py = r.y; pa.pz = r.z;
-                            st = kFlight;
-                            mstep = -1;
-                        } else {
-                            mt += d;
-                            if (mstep >= kMaxMarch) { count(req, 6, 1u); st = kIdle; goto path_end; }
-                        }
-                    } else {   // kShadow: length of X -> light inside the medium (Sec. 4.3, d_t)
-                        bool done = skip;
-                        bool capped = false;
-                        if (!done) {
-                            if (inside) {
-                                float d = -f / q.lip;
-                                bool flip = false;
-                                if (d < kEps) {
-                                    count(req, 9, 1u);
-                                    if (dot(sdf_grad(q, r), md) > 0.0f) flip = true;
-                                    d = kEps;
-                                }
-                                if (flip) {
-                                    inside = false;
-                                } else {
-                                    const float step = fminf(d, ml - mt);
-                                    din += step;
-                                    mt += step;
-                                }
-                            } else {
-                                float d = f / q.lip;
-                                bool flip = false;
-                                if (d < kEps) {
-                                    count(req, 9, 1u);
-                                    if (dot(sdf_grad(q, r), md) < 0.0f) flip = true;
-                                    d = kEps;
-                                }
-                                if (flip) inside = true;
-                                else mt += fminf(d, ml - mt);
-                            }
-                            if (!done && mt >= ml) done = true;
-                            if (!done && mstep >= kMaxMarch) { done = true; capped = true; }
-                        }
-                        if (done) {
-                            count(req, 7, 1u);
-                            if (capped) {
-                                count(req, 6, 1u);
-                            } else {
-                                const V W = v3(pa.Wx, pa.Wy, pa.Wz);
-                                const float rho = hg_pdf(dot(W, md), q.g);
-                                pa.acc += pa.nee_wgt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
-                            }
-                            pa.flags &= ~kFlagNee;
-                            if (pa.flags & kFlagEnd) {
-                                st = kIdle;
-                                goto path_end;
-                            }
-                            st = kFlight;
-                            mstep = -1;
-                        }
-                    }
-                }
-                continue;
-            path_end:
-                // the path is over: its NEE sum goes to its pixel
-                if (pa.acc != 0.0f) atomicAdd(&B.image[B.r[req].image_offset + pa.id_hi], (double)pa.acc);
-                atomicSub(&ctl->alive, 1);
             }
         }
-        grid.sync();
+        const unsigned parked = __ballot_sync(0xffffffffu, st == kDecode);
+        const unsigned marching = __ballot_sync(0xffffffffu, st != kIdle && st != kDecode);
+        if (parked == 0u && marching == 0u) break;     // drained and no lane holds a path
 
-        // ================= stage B: the three decoders on the dense sphere queue =================
-        if (blockIdx.x == 0 && tid == 0) { ctl->f_count[P] = 0; ctl->f_taken[P] = 0; }
-        {
-            const int n_s = __ldcg(&ctl->s_count[P]);
-            if (blockIdx.x == 0 && tid == 0 && n_s > 0) atomicAdd(&ctl->work, (unsigned long long)n_s);
-            for (int i = blockIdx.x * kThreads + tid; i < n_s; i += gridDim.x * kThreads) {
-                Path pa = load_path(B.sq[P] + i);
-                const int req = (int)(pa.flags & 0xffu);
+        if (parked != 0u && (__popc(parked) >= kDecodeBatch || marching == 0u)) {
+            // ================= decoder round: the three learned samplers for the parked lanes =================
+            if (st == kDecode) {
                 const Req& qq = B.r[req];
                 count(req, 3, 1u);
-                const Stream st(qq.seed, ((uint64_t)pa.id_hi << 32) | pa.id_lo);
-                const Words a4 = st.at(pa.seg, 1u);
+                const Stream rs(qq.seed, ((uint64_t)id_hi << 32) | id_lo);
+                const Words a4 = rs.at(seg, 1u);
                 float n[24];
 #pragma unroll
                 for (int t = 0; t < 6; ++t) {
-                    const float4 v = dec::normals4(st, pa.seg, 2u + t);
+                    const float4 v = dec::normals4(rs, seg, 2u + t);
                     n[4 * t] = v.x; n[4 * t + 1] = v.y; n[4 * t + 2] = v.z; n[4 * t + 3] = v.w;
                 }
-                const float rad = pa.Xx, tau = pa.Xy;
                 const float ltau = __logf(tau);
                 // LengthGen: N (albedo-1 physics, Eq. 3)
                 float xin8[8] = {ltau, qq.g, n[0], n[1], n[2], n[3], 0.0f, 0.0f};
@@ -590,9 +312,8 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
                 const float phiN = __expf(N * qq.log_phi);
                 const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
                 // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
-                const V wi = v3(pa.wx, pa.wy, pa.wz);
                 V t1, t2;
-                onb(wi, &t1, &t2);
+                onb(w, &t1, &t2);
                 float sn, cs;
                 sincos_turns_fast(u24(a4.w1), &sn, &cs);
                 const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
@@ -607,43 +328,161 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const V v1 = v3(cs * vs[k].x - sn * vs[k].y, sn * vs[k].x + cs * vs[k].y, vs[k].z);
-                    vw[k] = t1 * v1.x + t2 * v1.y + wi * v1.z;
+                    vw[k] = t1 * v1.x + t2 * v1.y + w * v1.z;
                 }
-                const V c = v3(pa.px, pa.py, pa.pz);
-                const V xexit = c + vw[0] * rad;
-                const V wout = unit(vw[1]);
-                const V X = c + vw[2] * rad;
-                const V Wd = unit(vw[3]);
-                pa.Xx = X.x; pa.Xy = X.y; pa.Xz = X.z;
-                pa.Wx = Wd.x; pa.Wy = Wd.y; pa.Wz = Wd.z;
-                pa.nee_wgt = lam;
-                pa.flags = (pa.flags & 0xffu) | kFlagNee;
+                nX = p + vw[2] * rad;                   // p holds the collision point c
+                nW = unit(vw[3]);
+                nwt = lam;
                 if (u24(a4.w0) >= phiN) {
                     count(req, 5, 1u);
-                    pa.flags |= kFlagEnd;
+                    end_after = true;
                 } else {
-                    pa.px = xexit.x; pa.py = xexit.y; pa.pz = xexit.z;
-                    pa.wx = wout.x; pa.wy = wout.y; pa.wz = wout.z;
-                    pa.seg += 1u;
+                    const V xexit = p + vw[0] * rad;
+                    w = unit(vw[1]);
+                    p = xexit;
+                    seg += 1u;
                 }
-                const int idx = atomicAdd(&ctl->f_count[Q], 1);
-                store_path(B.fq[Q] + idx, pa);
+                start_shadow();
+            }
+            continue;
+        }
+
+        // ================= one signed-distance step of every marching lane =================
+        if (st != kIdle && st != kDecode) {
+            const Req& q = B.r[req];
+            const V r = mo + md * mt;
+            // escape and end-of-segment tests come before the distance evaluation
+            const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
+            const bool skip = (st == kShadow) ? (mt >= ml || (!inside && leaving))
+                                              : ((st == kCamera || st == kReentry) && leaving);
+            float f = 0.0f;
+            if (!skip) {
+                f = sdf(q, r);
+                count(req, 8, 1u);
+            }
+            ++mstep;
+            if (st == kFlight) {
+                float d = -f / q.lip;
+                bool exited = false;
+                if (d < kEps) {
+                    count(req, 9, 1u);
+                    if (dot(sdf_grad(q, r), md) > 0.0f) exited = true;
+                    d = kEps;
+                }
+                if (exited) {
+                    st = kReentry;                       // left the object at r: look for a re-entry
+                    mo = r;
+                    mt = 0.0f;
+                    mstep = 0;
+                } else if (mt + d >= ml) {
+                    // ---------- collision at c ----------
+                    const V c = mo + md * ml;
+                    bool sphere = false;
+                    if (q.mode == MS_SPHERE && learned) {
+                        const float dc = -sdf(q, c) / q.lip;
+                        count(req, 8, 1u);
+                        rad = fminf(dc, q.tau_max / q.sigma);
+                        tau = q.sigma * rad;
+                        if (tau >= q.tau_min) {
+                            sphere = true;
+                            p = c;
+                            st = kDecode;                // park until the warp runs a decoder round
+                        }
+                    }
+                    if (!sphere) {
+                        // brute-force event: NEE at c with weight phi, roulette, HG scattering
+                        count(req, 4, 1u);
+                        const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
+                        const Words u = rs.at(seg, 0u);
+                        nX = c;
+                        nW = md;
+                        nwt = q.phi;
+                        if (u24(u.w3) >= q.phi) {
+                            count(req, 5, 1u);
+                            end_after = true;
+                        } else {
+                            w = scatter_dir(md, hg_cosine(u24(u.w1), q.g), u24(u.w2));
+                            p = c;
+                            seg += 1u;
+                        }
+                        start_shadow();
+                    }
+                } else {
+                    mt += d;
+                    if (mstep >= kMaxMarch) { count(req, 6, 1u); end_path(); }
+                }
+            } else if (st == kCamera || st == kReentry) {
+                // outside the medium: march until re-entry or until the bounding sphere is left
+                if (leaving) {
+                    end_path();                          // escaped: black background
+                } else {
+                    float d = f / q.lip;
+                    bool entered = false;
+                    if (d < kEps) {
+                        count(req, 9, 1u);
+                        if (dot(sdf_grad(q, r), md) < 0.0f) entered = true;
+                        d = kEps;
+                    }
+                    if (entered) {
+                        if (st == kCamera) {
+                            count(req, 1, 1u);
+                            w = md;
+                        } else {
+                            seg += 1u;
+                        }
+                        p = r;
+                        if (!start_flight()) end_path();
+                    } else {
+                        mt += d;
+                        if (mstep >= kMaxMarch) { count(req, 6, 1u); end_path(); }
+                    }
+                }
+            } else {   // kShadow: length of X -> light inside the medium (Sec. 4.3, d_t)
+                bool done = skip;
+                bool capped = false;
+                if (!done) {
+                    if (inside) {
+                        float d = -f / q.lip;
+                        bool flip = false;
+                        if (d < kEps) {
+                            count(req, 9, 1u);
+                            if (dot(sdf_grad(q, r), md) > 0.0f) flip = true;
+                            d = kEps;
+                        }
+                        if (flip) {
+                            inside = false;
+                        } else {
+                            const float step = fminf(d, ml - mt);
+                            din += step;
+                            mt += step;
+                        }
+                    } else {
+                        float d = f / q.lip;
+                        bool flip = false;
+                        if (d < kEps) {
+                            count(req, 9, 1u);
+                            if (dot(sdf_grad(q, r), md) < 0.0f) flip = true;
+                            d = kEps;
+                        }
+                        if (flip) inside = true;
+                        else mt += fminf(d, ml - mt);
+                    }
+                    if (mt >= ml) done = true;
+                    else if (mstep >= kMaxMarch) { done = true; capped = true; }
+                }
+                if (done) {
+                    count(req, 7, 1u);
+                    if (capped) {
+                        count(req, 6, 1u);
+                    } else {
+                        const float rho = hg_pdf(dot(nW, md), q.g);
+                        acc += nwt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
+                    }
+                    if (end_after) end_path();
+                    else if (!start_flight()) end_path();
+                }
             }
         }
-        grid.sync();
-        // ================= end of wave: all blocks see the same counters =================
-        const bool done = __ldcg(&ctl->alive) == 0 && __ldcg(&ctl->ticket) >= B.total &&
-                          __ldcg(&ctl->f_count[Q]) == 0;
-        if (done) break;
-        // a wave in which neither stage took any work while paths are still counted as live means the
-        // bookkeeping is broken: stop with an error instead of spinning
-        const unsigned long long work = __ldcg(&ctl->work);
-        if (work == last_work || wave + 1 >= kMaxWaves) {
-            if (blockIdx.x == 0 && tid == 0) ctl->error = work == last_work ? 2 : 1;
-            break;
-        }
-        last_work = work;
-        grid.sync();
     }
 
     // ---------------- counters -> shared -> global ----------------
@@ -654,25 +493,12 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
     __syncthreads();
     for (int k = tid; k < B.n * kStats; k += kThreads)
         if (s_stats[k]) atomicAdd(&B.stats[k], s_stats[k]);
-    if (blockIdx.x == 0 && tid == 0) {
-        const int err = __ldcg(&ctl->error);
-        for (int r = 0; r < B.n; ++r) {
-            atomicAdd(&B.stats[r * kStats + kStats - 2], (unsigned long long)(wave + 1));
-            if (err) atomicAdd(&B.stats[r * kStats + kStats - 1], (unsigned long long)err);
-        }
-    }
 }
 
 }  // namespace render
 }  // namespace ms
 
 using namespace ms::render;
-
-static int queue_capacity()
-{
-    // about eight paths per resident lane keeps both stages busy; the record is 80 bytes
-    return 1 << 20;
-}
 
 static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const char* fn)
 {
@@ -733,7 +559,7 @@ extern "C" size_t ms_render_workspace_size(const ms_render_params* reqs, int n_r
 {
     (void)reqs;
     (void)n_requests;
-    return 256 + 4 * (size_t)queue_capacity() * sizeof(Path);
+    return 256;
 }
 
 static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
@@ -766,22 +592,16 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     }
     b.image = images;
     b.stats = stats;
-    b.capacity = queue_capacity();
-    char* ws = static_cast<char*>(workspace);
-    b.ctl = reinterpret_cast<Ctl*>(ws);
-    Path* q0 = reinterpret_cast<Path*>(ws + 256);
-    b.fq[0] = q0;
-    b.fq[1] = q0 + b.capacity;
-    b.sq[0] = q0 + 2 * (size_t)b.capacity;
-    b.sq[1] = q0 + 3 * (size_t)b.capacity;
+    b.ticket = static_cast<unsigned long long*>(workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    MS_CUDA(cudaMemsetAsync(workspace, 0, sizeof(Ctl), s));
+    MS_CUDA(cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s));
     int per_sm = 0;
     MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel, kThreads, 0));
-    MS_CHECK_ARG(per_sm > 0, "%s: the renderer kernel cannot be resident on this device", fn);
-    const unsigned grid = (unsigned)(ms::num_sms() * per_sm);
-    void* args[] = {&b};
-    MS_CUDA(cudaLaunchCooperativeKernel((const void*)render_kernel, dim3(grid), dim3(kThreads), args, 0, s));
+    uint64_t grid = (uint64_t)ms::num_sms() * (per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (b.total + kThreads - 1) / kThreads;
+    if (grid > need) grid = need;
+    render_kernel<<<(unsigned)grid, kThreads, 0, s>>>(b);
+    MS_CUDA(cudaGetLastError());
     return MS_OK;
 }
 

@@ -180,7 +180,9 @@ def ms_simulate_walks(media: torch.Tensor, n_photons: int, out: dict, *, seed=1,
 # ------------------------------------------------------------------------------------------------ decoders
 
 def decoder_struct(weights: torch.Tensor, p_in, p_out, latent=4, width=16, precision=MS_FP32) -> Decoder:
-    return Decoder(p_in, latent, width, p_out, precision, _ptr(weights).value)
+    d = Decoder(p_in, latent, width, p_out, precision, _ptr(weights).value)
+    d._owned = weights
+    return d
 
 
 def ms_cvae_infer(dec: Decoder, cond: torch.Tensor, n: int, *, z_eps=None, seed=7, offset=0, out_mean_logvar=None,
@@ -249,11 +251,13 @@ def render_params(d: dict) -> RenderParams:
 
 
 def cvae_set(models: dict, precision=MS_FP32) -> CvaeSet:
-    """models: {"length": (weights, p_in, p_out), "path": ..., "event": ...} with device float32 weights."""
+    """models: {"length": (weights, p_in, p_out), "path": ..., "event": ...} with device float32 weights.
+    The returned struct keeps the weight tensors alive (it holds only their device pointers otherwise)."""
     s = CvaeSet()
     for k in ("length", "path", "event"):
         w, p_in, p_out = models[k]
         setattr(s, k, decoder_struct(w, p_in, p_out, precision=precision))
+    s._owned = {k: models[k][0] for k in ("length", "path", "event")}
     return s
 
 
