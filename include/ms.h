@@ -167,6 +167,22 @@ ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, float* m, fl
                              float lr, float weight_decay, float* loss3, void* workspace,
                              size_t workspace_bytes, void* stream);
 
+/* The same training step with no workspace argument: its scratch is a fixed 16 MiB array inside the library
+ * (ms_cvae_static_scratch_bytes()), for callers that must not allocate device memory — for example code whose
+ * device memory is all owned by another framework's pool, or a plug-in that may not allocate while the host
+ * application runs.  The paper has no counterpart; this is a deployment convenience.
+ *  - Batches whose ms_cvae_workspace_size() exceeds the array are rejected with MS_ERR_INVALID_ARG.
+ *  - Nothing is allocated, by this library or anything it calls.
+ *  - Every device that loads the library keeps the array until the process exits.
+ *  - All calls share the array: calls whose work overlaps on the GPU race and corrupt each other's
+ *    gradients.  Nothing in it needs clearing between calls (each call overwrites what it reads).
+ *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress); make that first
+ *    call before any stream capture. */
+size_t ms_cvae_static_scratch_bytes(void);
+ms_status ms_cvae_train_step_static(const ms_cvae_shape* s, float* params, float* m, float* v, const float* x,
+                                    const float* c, const float* eps_z, uint64_t B, uint64_t seed, uint64_t step,
+                                    float lr, float weight_decay, float* loss3, void* stream);
+
 /* Walk records -> conditions and targets of the three CVAEs (Sec. 4.1, Eq. 3, Eq. 4 inverted).  Each record
  * is rotated about (0,0,1) by -psi, psi = atan2(x_y, x_x), so the exit point is (sin theta, 0, cos theta);
  * alpha = w~_y, beta = w~_x cos theta - w~_z sin theta.  N is dequantised as y = ln(N - 1/2 + u) with u the

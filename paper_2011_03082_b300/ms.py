@@ -24,7 +24,7 @@ MS_RENDER_STATS = 16
 # the C ABI's exported symbols (checked by the tests against include/ms.h)
 EXPORTS = ("ms_last_error", "ms_version", "ms_walk_workspace_size", "ms_simulate_walks", "ms_cvae_infer",
            "ms_cvae_num_params", "ms_cvae_workspace_size", "ms_cvae_forward_backward", "ms_adam_step",
-           "ms_cvae_train_step", "ms_training_records", "ms_render_workspace_size", "ms_render",
+           "ms_cvae_train_step", "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records", "ms_render_workspace_size", "ms_render",
            "ms_render_batch")
 
 
@@ -100,6 +100,8 @@ def lib():
         "ms_cvae_forward_backward": ([P, P, P, P, P, U64, U64, U64, P, P, P, C.c_size_t, P], C.c_int),
         "ms_adam_step": ([P, P, P, P, U64, U64, F, F, F, F, F, P], C.c_int),
         "ms_cvae_train_step": ([P, P, P, P, P, P, P, U64, U64, U64, F, F, P, P, C.c_size_t, P], C.c_int),
+        "ms_cvae_static_scratch_bytes": ([], C.c_size_t),
+        "ms_cvae_train_step_static": ([P, P, P, P, P, P, P, U64, U64, U64, F, F, P, P], C.c_int),
         "ms_training_records": ([U64, P, P, P, P, P, P, I32, U64, P, P, P, P, P, P, P], C.c_int),
         "ms_render_workspace_size": ([P, C.c_int], C.c_size_t),
         "ms_render": ([P, P, P, P, P, C.c_size_t, P], C.c_int),
@@ -226,6 +228,15 @@ def ms_cvae_train_step(shape, params, m, v, x, c, B, *, eps_z=None, seed=1, step
     return _check(lib().ms_cvae_train_step(C.byref(shape), _ptr(params), _ptr(m), _ptr(v), _ptr(x), _ptr(c),
                                            _ptr(eps_z), B, seed, step, lr, weight_decay, _ptr(loss3), _ptr(ws),
                                            ws.numel(), _stream(stream)), "ms_cvae_train_step")
+
+
+def ms_cvae_train_step_static(shape, params, m, v, x, c, B, *, eps_z=None, seed=1, step=1, lr=1e-3,
+                              weight_decay=0.0, loss3=None, stream=None):
+    """ms_cvae_train_step without a workspace: the scratch is a fixed array inside the library (for callers
+    that may not allocate device memory).  Calls overlapping on the GPU race on that array."""
+    return _check(lib().ms_cvae_train_step_static(C.byref(shape), _ptr(params), _ptr(m), _ptr(v), _ptr(x), _ptr(c),
+                                                  _ptr(eps_z), B, seed, step, lr, weight_decay, _ptr(loss3),
+                                                  _stream(stream)), "ms_cvae_train_step_static")
 
 
 def ms_training_records(n, n_events, exit_pos, exit_dir, rep_pos, rep_dir, media, seed, outs: dict, stream=None):
