@@ -144,14 +144,12 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
     return lo;
 }
 
-// Per-lane counters of the request the lane is currently serving, flushed to shared memory on change.
 constexpr int kUsedStats = 10;
-struct Counters {
-    int req = -1;
-    unsigned c[kUsedStats] = {};
-};
+constexpr int kTransBatch = 8;      // pending lanes that trigger a transition round
+constexpr int kRefillBatch = 8;     // idle lanes that trigger a refill round
 
-enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow, kDecode };
+enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow, kDecode, kPending };
+enum Event : int { kEvHit = 0, kEvReenter, kEvEscape, kEvCap, kEvExit, kEvCollide, kEvShadowDone };
 
 __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_constant__ Batch B)
 {
@@ -170,34 +168,37 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     __syncthreads();
 
-    Counters cnt;
-    auto count = [&](int req, int k, unsigned v) {
-        if (req != cnt.req) {
-            if (cnt.req >= 0)
+    // counters of the lane's current path (flushed into its request's shared counters when the path ends)
+    unsigned cnt[kUsedStats];
 #pragma unroll
-                for (int j = 0; j < kUsedStats; ++j)
-                    if (cnt.c[j]) { atomicAdd(&s_stats[cnt.req * kStats + j], (unsigned long long)cnt.c[j]); cnt.c[j] = 0u; }
-            cnt.req = req;
-        }
-        cnt.c[k] += v;
-    };
+    for (int j = 0; j < kUsedStats; ++j) cnt[j] = 0u;
 
     // ---- the lane's path ----
-    int st = kIdle, req = 0;
+    int st = kIdle, req = 0, ev = 0;
     uint32_t id_lo = 0, id_hi = 0, seg = 0;
     V p = v3(0, 0, 0), w = v3(0, 0, 1);        // position and direction of the path
     float acc = 0.0f;                           // NEE sum of the path
     V nX = v3(0, 0, 0), nW = v3(0, 0, 1);       // pending NEE request
     float nwt = 0.0f;
     bool end_after = false;                     // the path ends after its pending NEE
+    float u1 = 0.0f, u2 = 0.0f, u3 = 0.0f;      // this segment's HG cosine, azimuth and roulette uniforms
     float rad = 0.0f, tau = 0.0f;               // sphere of a parked (decode) lane
     // ---- the lane's current march ----
     V mo = v3(0, 0, 0), md = v3(0, 0, 1);
     float mt = 0.0f, ml = 0.0f, din = 0.0f;
     int mstep = 0;
-    bool inside = true;
+    bool inside = true, capped = false;
     bool drained = false;                       // warp-uniform: camera tickets exhausted
 
+    auto end_path = [&]() {
+        if (acc != 0.0f) atomicAdd(&B.image[B.r[req].image_offset + id_hi], (double)acc);
+#pragma unroll
+        for (int j = 0; j < kUsedStats; ++j) {
+            if (cnt[j]) atomicAdd(&s_stats[req * kStats + j], (unsigned long long)cnt[j]);
+            cnt[j] = 0u;
+        }
+        st = kIdle;
+    };
     auto start_shadow = [&]() {
         const Req& q = B.r[req];
         mo = nX;
@@ -207,72 +208,52 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
         mt = 0.0f;
         din = 0.0f;
         inside = true;
+        capped = false;
         mstep = 0;
         st = kShadow;
     };
-    // begins the next flight of the path, or ends it at the segment cap; returns false when the path ended
-    auto start_flight = [&]() -> bool {
-        const Req& q = B.r[req];
-        if (seg >= q.max_segments) {
-            count(req, 6, 1u);
-            return false;
-        }
-        count(req, 2, 1u);
-        const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
-        const Words u = rs.at(seg, 0u);
-        ml = -__logf(1.0f - u24(u.w0)) / q.sigma;
-        mo = p;
-        md = w;
-        mt = 0.0f;
-        mstep = 0;
-        st = kFlight;
-        return true;
-    };
-    auto end_path = [&]() {
-        if (acc != 0.0f) atomicAdd(&B.image[B.r[req].image_offset + id_hi], (double)acc);
-        st = kIdle;
-    };
 
     for (;;) {
-        // ---------------- refill idle lanes with new camera samples ----------------
-        {
-            const unsigned m = __ballot_sync(0xffffffffu, st == kIdle);
-            if (m && !drained) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long t0 = 0;
-                if (lane == leader) t0 = atomicAdd(B.ticket, (unsigned long long)__popc(m));
-                t0 = __shfl_sync(0xffffffffu, t0, leader);
-                if (t0 + __popc(m) >= B.total) drained = true;
-                const uint64_t t = t0 + __popc(m & ((1u << lane) - 1u));
-                if (st == kIdle && t < B.total) {
-                    req = find_req(B, t);
-                    const Req& q = B.r[req];
-                    const uint64_t local = t - q.samples_begin;
-                    id_hi = (uint32_t)(local / q.spp);
-                    id_lo = (uint32_t)(q.sample_offset + local % q.spp);
-                    const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
-                    const Words j = rs.at(0u, 8u);
-                    camera_ray(q, (int)(id_hi % (uint32_t)q.W), (int)(id_hi / (uint32_t)q.W), u24(j.w0), u24(j.w1),
-                               &mo, &md);
-                    seg = 0;
-                    acc = 0.0f;
-                    end_after = false;
-                    mt = 0.0f;
-                    mstep = 0;
-                    st = kCamera;
-                    count(req, 0, 1u);
-                }
+        unsigned idle = __ballot_sync(0xffffffffu, st == kIdle);
+        unsigned marching = __ballot_sync(0xffffffffu, st >= kCamera && st <= kShadow);
+        // ---------------- refill round: new camera samples for idle lanes ----------------
+        if (idle && !drained && (__popc(idle) >= kRefillBatch || __popc(marching) < 16)) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long t0 = 0;
+            if (lane == leader) t0 = atomicAdd(B.ticket, (unsigned long long)__popc(idle));
+            t0 = __shfl_sync(0xffffffffu, t0, leader);
+            if (t0 + __popc(idle) >= B.total) drained = true;
+            const uint64_t t = t0 + __popc(idle & ((1u << lane) - 1u));
+            if (st == kIdle && t < B.total) {
+                req = find_req(B, t);
+                const Req& q = B.r[req];
+                const uint64_t local = t - q.samples_begin;
+                id_hi = (uint32_t)(local / q.spp);
+                id_lo = (uint32_t)(q.sample_offset + local % q.spp);
+                const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
+                const Words j = rs.at(0u, 8u);
+                camera_ray(q, (int)(id_hi % (uint32_t)q.W), (int)(id_hi / (uint32_t)q.W), u24(j.w0), u24(j.w1),
+                           &mo, &md);
+                seg = 0;
+                acc = 0.0f;
+                end_after = false;
+                mt = 0.0f;
+                mstep = 0;
+                st = kCamera;
+                cnt[0] += 1u;
             }
+            continue;
         }
         const unsigned parked = __ballot_sync(0xffffffffu, st == kDecode);
-        const unsigned marching = __ballot_sync(0xffffffffu, st != kIdle && st != kDecode);
-        if (parked == 0u && marching == 0u) break;     // drained and no lane holds a path
+        const unsigned pending = __ballot_sync(0xffffffffu, st == kPending);
+        if (!parked && !pending && !marching) break;   // drained and no lane holds a path
+        const int n_active = __popc(marching);
 
-        if (parked != 0u && (__popc(parked) >= kDecodeBatch || marching == 0u)) {
+        if (parked && (__popc(parked) >= kDecodeBatch || n_active + __popc(pending) < kDecodeBatch)) {
             // ================= decoder round: the three learned samplers for the parked lanes =================
             if (st == kDecode) {
                 const Req& qq = B.r[req];
-                count(req, 3, 1u);
+                cnt[3] += 1u;
                 const Stream rs(qq.seed, ((uint64_t)id_hi << 32) | id_lo);
                 const Words a4 = rs.at(seg, 1u);
                 float n[24];
@@ -334,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
                 nW = unit(vw[3]);
                 nwt = lam;
                 if (u24(a4.w0) >= phiN) {
-                    count(req, 5, 1u);
+                    cnt[5] += 1u;
                     end_after = true;
                 } else {
                     const V xexit = p + vw[0] * rad;
@@ -347,40 +328,27 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
             continue;
         }
 
-        // ================= one signed-distance step of every marching lane =================
-        if (st != kIdle && st != kDecode) {
-            const Req& q = B.r[req];
-            const V r = mo + md * mt;
-            // escape and end-of-segment tests come before the distance evaluation
-            const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
-            const bool skip = (st == kShadow) ? (mt >= ml || (!inside && leaving))
-                                              : ((st == kCamera || st == kReentry) && leaving);
-            float f = 0.0f;
-            if (!skip) {
-                f = sdf(q, r);
-                count(req, 8, 1u);
-            }
-            ++mstep;
-            if (st == kFlight) {
-                float d = -f / q.lip;
-                bool exited = false;
-                if (d < kEps) {
-                    count(req, 9, 1u);
-                    if (dot(sdf_grad(q, r), md) > 0.0f) exited = true;
-                    d = kEps;
-                }
-                if (exited) {
-                    st = kReentry;                       // left the object at r: look for a re-entry
-                    mo = r;
-                    mt = 0.0f;
-                    mstep = 0;
-                } else if (mt + d >= ml) {
-                    // ---------- collision at c ----------
+        if (pending && (__popc(pending) >= kTransBatch || n_active < 16)) {
+            // ================= transition round: what follows each finished march =================
+            if (st == kPending) {
+                const Req& q = B.r[req];
+                bool need_flight = false;
+                if (ev == kEvShadowDone) {
+                    cnt[7] += 1u;
+                    if (capped) {
+                        cnt[6] += 1u;
+                    } else {
+                        const float rho = hg_pdf(dot(nW, md), q.g);
+                        acc += nwt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
+                    }
+                    if (end_after) end_path();
+                    else need_flight = true;
+                } else if (ev == kEvCollide) {
                     const V c = mo + md * ml;
                     bool sphere = false;
                     if (q.mode == MS_SPHERE && learned) {
                         const float dc = -sdf(q, c) / q.lip;
-                        count(req, 8, 1u);
+                        cnt[8] += 1u;
                         rad = fminf(dc, q.tau_max / q.sigma);
                         tau = q.sigma * rad;
                         if (tau >= q.tau_min) {
@@ -390,106 +358,133 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
                         }
                     }
                     if (!sphere) {
-                        // brute-force event: NEE at c with weight phi, roulette, HG scattering
-                        count(req, 4, 1u);
-                        const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
-                        const Words u = rs.at(seg, 0u);
+                        // brute-force event: NEE at c with weight phi, roulette, HG scattering (Sec. 3.1)
+                        cnt[4] += 1u;
                         nX = c;
                         nW = md;
                         nwt = q.phi;
-                        if (u24(u.w3) >= q.phi) {
-                            count(req, 5, 1u);
+                        if (u3 >= q.phi) {
+                            cnt[5] += 1u;
                             end_after = true;
                         } else {
-                            w = scatter_dir(md, hg_cosine(u24(u.w1), q.g), u24(u.w2));
+                            w = scatter_dir(md, hg_cosine(u1, q.g), u2);
                             p = c;
                             seg += 1u;
                         }
                         start_shadow();
                     }
+                } else if (ev == kEvExit) {
+                    st = kReentry;                       // left the object at mo: look for a re-entry
+                    mt = 0.0f;
+                    mstep = 0;
+                } else if (ev == kEvHit || ev == kEvReenter) {
+                    need_flight = true;
+                } else {
+                    if (ev == kEvCap) cnt[6] += 1u;
+                    end_path();
+                }
+                if (need_flight) {
+                    if (seg >= q.max_segments) {
+                        cnt[6] += 1u;
+                        end_path();
+                    } else {
+                        cnt[2] += 1u;
+                        const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
+                        const Words u = rs.at(seg, 0u);
+                        ml = -__logf(1.0f - u24(u.w0)) / q.sigma;
+                        u1 = u24(u.w1);
+                        u2 = u24(u.w2);
+                        u3 = u24(u.w3);
+                        mo = p;
+                        md = w;
+                        mt = 0.0f;
+                        mstep = 0;
+                        st = kFlight;
+                    }
+                }
+            }
+            continue;
+        }
+
+        // ================= one signed-distance step of every marching lane =================
+        if (st >= kCamera && st <= kShadow) {
+            const Req& q = B.r[req];
+            const V r = mo + md * mt;
+            // escape and end-of-segment tests come before the distance evaluation
+            const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
+            const bool skip = (st == kShadow) ? (mt >= ml || (!inside && leaving))
+                                              : ((st == kCamera || st == kReentry) && leaving);
+            float f = 0.0f;
+            if (!skip) {
+                f = sdf(q, r);
+                cnt[8] += 1u;
+            }
+            ++mstep;
+            // the sign and threshold tests of the three kinds of march share one evaluation
+            const bool in_medium = st == kFlight || (st == kShadow && inside);
+            float d = in_medium ? -f / q.lip : f / q.lip;
+            bool at_boundary = false, crossing = false;
+            if (!skip && d < kEps) {
+                cnt[9] += 1u;
+                const float gd = dot(sdf_grad(q, r), md);
+                at_boundary = true;
+                crossing = in_medium ? gd > 0.0f : gd < 0.0f;
+                d = kEps;
+            }
+            if (st == kFlight) {
+                if (crossing) {
+                    mo = r;
+                    ev = kEvExit;
+                    st = kPending;
+                } else if (mt + d >= ml) {
+                    ev = kEvCollide;
+                    st = kPending;
                 } else {
                     mt += d;
-                    if (mstep >= kMaxMarch) { count(req, 6, 1u); end_path(); }
+                    if (mstep >= kMaxMarch) { ev = kEvCap; st = kPending; }
                 }
             } else if (st == kCamera || st == kReentry) {
-                // outside the medium: march until re-entry or until the bounding sphere is left
                 if (leaving) {
-                    end_path();                          // escaped: black background
-                } else {
-                    float d = f / q.lip;
-                    bool entered = false;
-                    if (d < kEps) {
-                        count(req, 9, 1u);
-                        if (dot(sdf_grad(q, r), md) < 0.0f) entered = true;
-                        d = kEps;
-                    }
-                    if (entered) {
-                        if (st == kCamera) {
-                            count(req, 1, 1u);
-                            w = md;
-                        } else {
-                            seg += 1u;
-                        }
-                        p = r;
-                        if (!start_flight()) end_path();
+                    ev = kEvEscape;                      // escaped: black background
+                    st = kPending;
+                } else if (crossing) {
+                    if (st == kCamera) {
+                        cnt[1] += 1u;
+                        w = md;
+                        ev = kEvHit;
                     } else {
-                        mt += d;
-                        if (mstep >= kMaxMarch) { count(req, 6, 1u); end_path(); }
+                        seg += 1u;
+                        ev = kEvReenter;
                     }
+                    p = r;
+                    st = kPending;
+                } else {
+                    mt += d;
+                    if (mstep >= kMaxMarch) { ev = kEvCap; st = kPending; }
                 }
             } else {   // kShadow: length of X -> light inside the medium (Sec. 4.3, d_t)
                 bool done = skip;
-                bool capped = false;
                 if (!done) {
-                    if (inside) {
-                        float d = -f / q.lip;
-                        bool flip = false;
-                        if (d < kEps) {
-                            count(req, 9, 1u);
-                            if (dot(sdf_grad(q, r), md) > 0.0f) flip = true;
-                            d = kEps;
-                        }
-                        if (flip) {
-                            inside = false;
-                        } else {
-                            const float step = fminf(d, ml - mt);
-                            din += step;
-                            mt += step;
-                        }
+                    if (crossing) {
+                        inside = !inside;
                     } else {
-                        float d = f / q.lip;
-                        bool flip = false;
-                        if (d < kEps) {
-                            count(req, 9, 1u);
-                            if (dot(sdf_grad(q, r), md) < 0.0f) flip = true;
-                            d = kEps;
-                        }
-                        if (flip) inside = true;
-                        else mt += fminf(d, ml - mt);
+                        const float step = fminf(d, ml - mt);
+                        if (inside) din += step;
+                        mt += step;
                     }
                     if (mt >= ml) done = true;
                     else if (mstep >= kMaxMarch) { done = true; capped = true; }
                 }
                 if (done) {
-                    count(req, 7, 1u);
-                    if (capped) {
-                        count(req, 6, 1u);
-                    } else {
-                        const float rho = hg_pdf(dot(nW, md), q.g);
-                        acc += nwt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
-                    }
-                    if (end_after) end_path();
-                    else if (!start_flight()) end_path();
+                    ev = kEvShadowDone;
+                    st = kPending;
                 }
             }
+            (void)at_boundary;
         }
     }
 
-    // ---------------- counters -> shared -> global ----------------
-    if (cnt.req >= 0)
-#pragma unroll
-        for (int j = 0; j < kUsedStats; ++j)
-            if (cnt.c[j]) atomicAdd(&s_stats[cnt.req * kStats + j], (unsigned long long)cnt.c[j]);
+    // ---------------- block counters -> global ----------------
     __syncthreads();
     for (int k = tid; k < B.n * kStats; k += kThreads)
         if (s_stats[k]) atomicAdd(&B.stats[k], s_stats[k]);
