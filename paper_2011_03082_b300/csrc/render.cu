@@ -40,7 +40,7 @@ constexpr int kDecodeBatch = 16;    // parked lanes that trigger a decoder round
 struct Req {
     float cam[3], at[3], tan_half, aspect;
     float light[3], I;
-    float sigma, g, phi, log_phi, A, k, lip, rb2;
+    float sigma, g, phi, log_phi, A, k, lip, inv_lip, rb2;
     float tau_min, tau_max;
     int32_t W, H, mode;
     uint32_t spp, max_segments;
@@ -76,7 +76,9 @@ __device__ __forceinline__ V unit(V a) { return a * rsqrtf(dot(a, a)); }
 // ---- the displaced sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz) (negative inside) ----
 __device__ __forceinline__ float sdf(const Req& q, V p)
 {
-    return sqrtf(dot(p, p)) - 1.0f - q.A * __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z);
+    const float d2 = dot(p, p);
+    const float r = d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f;
+    return r - 1.0f - q.A * __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z);
 }
 
 __device__ __forceinline__ V sdf_grad(const Req& q, V p)
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
                     const V c = mo + md * ml;
                     bool sphere = false;
                     if (q.mode == MS_SPHERE && learned) {
-                        const float dc = -sdf(q, c) / q.lip;
+                        const float dc = -sdf(q, c) * q.inv_lip;
                         cnt[8] += 1u;
                         rad = fminf(dc, q.tau_max / q.sigma);
                         tau = q.sigma * rad;
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
             ++mstep;
             // the sign and threshold tests of the three kinds of march share one evaluation
             const bool in_medium = st == kFlight || (st == kShadow && inside);
-            float d = in_medium ? -f / q.lip : f / q.lip;
+            float d = (in_medium ? -f : f) * q.inv_lip;
             bool at_boundary = false, crossing = false;
             if (!skip && d < kEps) {
                 cnt[9] += 1u;
@@ -530,6 +532,7 @@ static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const
         q.A = p.disp_amp;
         q.k = p.disp_freq;
         q.lip = 1.0f + p.disp_amp * p.disp_freq;
+        q.inv_lip = 1.0f / q.lip;
         const float rb = 1.0f + p.disp_amp + 1e-3f;
         q.rb2 = rb * rb;
         q.tau_min = p.min_optical_radius;
