@@ -5,6 +5,7 @@
 // shared memory once (decoder.cuh); z and eps are read from the caller or drawn in registers from the query's
 // Philox counter.  Half precision (FP16/BF16 with FP32 accumulation) is decoder_mma.cu.
 #include "decoder.cuh"
+#include "decoder_mma.cuh"
 
 namespace ms {
 namespace dec {
@@ -94,6 +95,82 @@ cudaError_t dispatch_p(const ms_decoder& d, const float* c, const float* z, uint
     }
 }
 
+// Half precision: 32 queries per warp on the tensor cores (decoder_mma.cuh).  The weights are rounded once to
+// FP16 / BF16; inputs and hidden activations are carried as head + tail halves (two products per tile), and
+// accumulation is FP32, so the result is that of the rounded weights to about 1e-4.
+constexpr int kMmaThreads = 128;
+
+template <int NT3, bool kBF16>
+__global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict__ wts, int p_in, int latent, int p_out,
+                                                         const float* __restrict__ cond, const float* __restrict__ z_eps,
+                                                         uint64_t seed, uint64_t offset, uint64_t n,
+                                                         float* __restrict__ mlv, float* __restrict__ smp)
+{
+    __shared__ __align__(16) unsigned char wsm[mmadec::smem_bytes(8)];
+    __shared__ float stage[kMmaThreads / 32][mmadec::kStageFloats];
+    __shared__ float rows[kMmaThreads][41];   // [0,16) inputs, [16,24) eps, [24,40) outputs
+    mmadec::stage_weights<kBF16>(wsm, wts, p_in + latent, p_out);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* my = rows[threadIdx.x];
+    const int nz = latent + p_out;
+    const uint64_t n_chunks = (n + 31) / 32;
+    const uint64_t warps = (uint64_t)gridDim.x * (kMmaThreads / 32);
+    for (uint64_t ch = (uint64_t)blockIdx.x * (kMmaThreads / 32) + warp; ch < n_chunks; ch += warps) {
+        const uint64_t q = ch * 32 + lane;
+        const bool live = q < n;
+        for (int k = 0; k < 24; ++k) my[k] = 0.0f;
+        if (live) {
+            for (int k = 0; k < p_in; ++k) my[k] = cond[q * p_in + k];
+            if (z_eps) {
+                for (int m = 0; m < nz; ++m) my[m < latent ? p_in + m : 16 + m - latent] = z_eps[q * nz + m];
+            } else {
+                const Stream st(seed, offset + q);
+                for (int j = 0; 4 * j < nz; ++j) {
+                    const float4 v = normals4(st, (uint32_t)j, 0xD0u);
+                    const int m = 4 * j;
+                    if (m < nz) my[m < latent ? p_in + m : 16 + m - latent] = v.x;
+                    if (m + 1 < nz) my[m + 1 < latent ? p_in + m + 1 : 16 + m + 1 - latent] = v.y;
+                    if (m + 2 < nz) my[m + 2 < latent ? p_in + m + 2 : 16 + m + 2 - latent] = v.z;
+                    if (m + 3 < nz) my[m + 3 < latent ? p_in + m + 3 : 16 + m + 3 - latent] = v.w;
+                }
+            }
+        }
+        float x[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = my[k];
+        float y[8 * NT3];
+        mmadec::warp_mlp<NT3, 2, kBF16>(wsm, stage[warp], x, y);
+        if (live) {
+#pragma unroll
+            for (int j = 0; j < 8 * NT3; ++j) my[24 + j] = y[j];
+            if (mlv)
+                for (int o = 0; o < 2 * p_out; ++o) mlv[q * (2 * p_out) + o] = my[24 + o];
+            if (smp)
+                for (int o = 0; o < p_out; ++o)
+                    smp[q * p_out + o] = my[24 + o] + __expf(0.5f * my[24 + p_out + o]) * my[16 + o];
+        }
+    }
+}
+
+cudaError_t launch_infer_mma(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
+                             uint64_t n, float* mlv, float* smp, cudaStream_t stream)
+{
+    const bool bf16 = d.precision == MS_BF16;
+    const int nt3 = mmadec::n_tiles_out(d.p_out);
+    auto kern = bf16 ? (nt3 == 1 ? infer_mma<1, true> : infer_mma<2, true>)
+                     : (nt3 == 1 ? infer_mma<1, false> : infer_mma<2, false>);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMmaThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (n + kMmaThreads - 1) / kMmaThreads;
+    if (grid > need) grid = need;
+    kern<<<(unsigned)grid, kMmaThreads, 0, stream>>>(d.weights, d.p_in, d.latent, d.p_out, cond, z_eps, seed, offset,
+                                                      n, mlv, smp);
+    return cudaGetLastError();
+}
+
 }  // namespace dec
 }  // namespace ms
 
@@ -111,8 +188,10 @@ extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const
     MS_CHECK_ARG(n == 0 || cond != nullptr, "ms_cvae_infer: cond is null");
     if (n == 0 || (out_mean_logvar == nullptr && out_sample == nullptr)) return MS_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (d->precision != MS_FP32)
-        return ms::set_error(MS_ERR_UNSUPPORTED, "ms_cvae_infer: half-precision decoders are not built yet");
+    if (d->precision != MS_FP32) {
+        MS_CUDA(ms::dec::launch_infer_mma(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s));
+        return MS_OK;
+    }
     const int in4 = ms::dec::pad4(d->p_in + d->latent);
     cudaError_t e;
     switch (in4) {

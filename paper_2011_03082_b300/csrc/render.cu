@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "decoder.cuh"
+#include "decoder_mma.cuh"
 #include "ms_device.cuh"
 
 namespace ms {
@@ -59,10 +60,9 @@ struct Batch {
     unsigned long long* ticket;
 };
 
-// decoder shapes: LengthGen (2 + 4 -> 1), PathGen (3 + 4 -> 3), EventGen (7 + 4 -> 6)
-constexpr int kInL = 8, kPL = 1, kInP = 8, kPP = 3, kInE = 12, kPE = 6;
-constexpr int kSmemL = dec::smem_floats(kInL, kPL), kSmemP = dec::smem_floats(kInP, kPP),
-              kSmemE = dec::smem_floats(kInE, kPE);
+// decoder shapes: LengthGen (2 + 4 -> 1), PathGen (3 + 4 -> 3), EventGen (7 + 4 -> 6); tensor-core fragment
+// layouts in shared memory (decoder_mma.cuh)
+constexpr int kBytesL = mmadec::smem_bytes(1), kBytesP = mmadec::smem_bytes(3), kBytesE = mmadec::smem_bytes(6);
 
 struct V { float x, y, z; };
 __device__ __forceinline__ V v3(float x, float y, float z) { return V{x, y, z}; }
@@ -155,17 +155,19 @@ enum Event : int { kEvHit = 0, kEvReenter, kEvEscape, kEvCap, kEvExit, kEvCollid
 
 __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_constant__ Batch B)
 {
-    __shared__ __align__(16) float sw[kSmemL + kSmemP + kSmemE];
+    __shared__ __align__(16) unsigned char sw[kBytesL + kBytesP + kBytesE];
+    __shared__ float s_stage[kThreads / 32][mmadec::kStageFloats];
     __shared__ unsigned long long s_stats[kMaxReq * kStats];
     const int tid = threadIdx.x, lane = tid & 31;
     const bool learned = B.wL != nullptr;
-    float* wl = sw;
-    float* wpth = sw + kSmemL;
-    float* wev = sw + kSmemL + kSmemP;
+    unsigned char* wl = sw;
+    unsigned char* wpth = sw + kBytesL;
+    unsigned char* wev = sw + kBytesL + kBytesP;
+    float* stage = s_stage[tid >> 5];
     if (learned) {
-        dec::stage_weights(wl, B.wL, 2 + 4, kInL, kPL);
-        dec::stage_weights(wpth, B.wP, 3 + 4, kInP, kPP);
-        dec::stage_weights(wev, B.wE, 7 + 4, kInE, kPE);
+        mmadec::stage_weights<false>(wl, B.wL, 2 + 4, 1);
+        mmadec::stage_weights<false>(wpth, B.wP, 3 + 4, 3);
+        mmadec::stage_weights<false>(wev, B.wE, 7 + 4, 6);
     }
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     __syncthreads();
@@ -253,45 +255,59 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
 
         if (parked && (__popc(parked) >= kDecodeBatch || n_active + __popc(pending) < kDecodeBatch)) {
             // ================= decoder round: the three learned samplers for the parked lanes =================
-            if (st == kDecode) {
-                const Req& qq = B.r[req];
+            // The MLPs run on the tensor cores for all 32 rows of the warp (a lane that is not parked feeds
+            // zeros and ignores its outputs); everything per path stays in the lane's registers.
+            const bool mine = st == kDecode;
+            const Req& qq = B.r[req];
+            const Stream rs(qq.seed, ((uint64_t)id_hi << 32) | id_lo);
+            float n[24];
+            Words a4{0u, 0u, 0u, 0u};
+            float ltau = 0.0f;
+            if (mine) {
                 cnt[3] += 1u;
-                const Stream rs(qq.seed, ((uint64_t)id_hi << 32) | id_lo);
-                const Words a4 = rs.at(seg, 1u);
-                float n[24];
+                a4 = rs.at(seg, 1u);
 #pragma unroll
                 for (int t = 0; t < 6; ++t) {
                     const float4 v = dec::normals4(rs, seg, 2u + t);
                     n[4 * t] = v.x; n[4 * t + 1] = v.y; n[4 * t + 2] = v.z; n[4 * t + 3] = v.w;
                 }
-                const float ltau = __logf(tau);
-                // LengthGen: N (albedo-1 physics, Eq. 3)
-                float xin8[8] = {ltau, qq.g, n[0], n[1], n[2], n[3], 0.0f, 0.0f};
-                float y4[4];
-                dec::mlp<kInL, kPL>(wl, xin8, y4);
-                const float yN = y4[0] + __expf(0.5f * y4[1]) * n[4];
-                float N = floorf(__expf(yN) + 0.5f);
-                N = fminf(fmaxf(N, 1.0f), kNMax);
-                const float lnN = __logf(N);
-                // PathGen: (cos theta, alpha, beta)
-                float xp8[8] = {ltau, qq.g, lnN, n[5], n[6], n[7], n[8], 0.0f};
-                float y8[8];
-                dec::mlp<kInP, kPP>(wpth, xp8, y8);
-                const float ct = fminf(1.0f, fmaxf(-1.0f, y8[0] + __expf(0.5f * y8[3]) * n[9]));
-                float al = y8[1] + __expf(0.5f * y8[4]) * n[10];
-                float be = y8[2] + __expf(0.5f * y8[5]) * n[11];
-                float ab2 = al * al + be * be;
-                if (ab2 > 1.0f) {
-                    const float s = rsqrtf(ab2);
-                    al *= s; be *= s; ab2 = 1.0f;
-                }
-                // EventGen: representative event (X~, W~)
-                float xe12[12] = {ltau, qq.g, qq.phi, ct, al, be, lnN, n[12], n[13], n[14], n[15], 0.0f};
-                float y12[12];
-                dec::mlp<kInE, kPE>(wev, xe12, y12);
+                ltau = __logf(tau);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) n[k] = 0.0f;
+            }
+            // LengthGen: N (albedo-1 physics, Eq. 3)
+            float xin[16] = {ltau, mine ? qq.g : 0.0f, n[0], n[1], n[2], n[3]};
+            float yL[8];
+            mmadec::warp_mlp<1, 3, false>(wl, stage, xin, yL);
+            const float yN = yL[0] + __expf(0.5f * yL[1]) * n[4];
+            float N = floorf(__expf(yN) + 0.5f);
+            N = fminf(fmaxf(N, 1.0f), kNMax);
+            const float lnN = mine ? __logf(N) : 0.0f;
+            // PathGen: (cos theta, alpha, beta)
+            float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, n[5], n[6], n[7], n[8]};
+            float yP[8];
+            mmadec::warp_mlp<1, 3, false>(wpth, stage, xp, yP);
+            const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * n[9]));
+            float al = yP[1] + __expf(0.5f * yP[4]) * n[10];
+            float be = yP[2] + __expf(0.5f * yP[5]) * n[11];
+            float ab2 = al * al + be * be;
+            if (ab2 > 1.0f) {
+                const float s = rsqrtf(ab2);
+                al *= s; be *= s; ab2 = 1.0f;
+            }
+            // EventGen: representative event (X~, W~)
+            float xe[16] = {ltau, mine ? qq.g : 0.0f, mine ? qq.phi : 0.0f, ct, al, be, lnN, n[12], n[13], n[14], n[15]};
+            if (!mine) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) xe[k] = 0.0f;
+            }
+            float yE[16];
+            mmadec::warp_mlp<2, 3, false>(wev, stage, xe, yE);
+            if (mine) {
                 float e[6];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) e[k] = y12[k] + __expf(0.5f * y12[6 + k]) * n[16 + k];
+                for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * n[16 + k];
                 const float phiN = __expf(N * qq.log_phi);
                 const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
                 // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r

@@ -81,3 +81,38 @@ def test_decoder_rejects_bad_shapes():
         d = ms.decoder_struct(w, kw["p_in"], kw["p_out"], width=kw.get("width", 16))
         with pytest.raises(ms.MsError):
             ms.ms_cvae_infer(d, c, 4, out_mean_logvar=out)
+
+
+def _round_bf16(a):
+    """Round float32 values to bfloat16 (nearest, ties to even), returned as float64."""
+    b = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("p_in,p_out", [(4, 1), (4, 6), (7, 6), (3, 3)])
+def test_half_precision_decoder(p_in, p_out, prec):
+    """Tensor-core decoder (FP16 or BF16 weights and activations, FP32 accumulation): max |error| <= 3e-3
+    against the FP64 oracle given the same rounded weights; the error against the FP32 weights is bounded
+    too (rounding of the weights themselves)."""
+    n = 40000
+    w = synth.xavier_decoder(7, p_in, p_out)
+    cond = synth.decoder_queries(7, n)[:, :p_in] if p_in <= 4 else \
+        np.random.default_rng(2).uniform(-1, 2, (n, p_in)).astype(np.float32)
+    ze = synth.standard_normals(3, (n, 4 + p_out))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    mlv = torch.zeros(n, 2 * p_out, device="cuda")
+    smp = torch.zeros(n, p_out, device="cuda")
+    d = ms.decoder_struct(dev(w), p_in, p_out, precision=ms.MS_FP16 if prec == "fp16" else ms.MS_BF16)
+    ms.ms_cvae_infer(d, dev(cond), n, z_eps=dev(ze), out_mean_logvar=mlv, out_sample=smp)
+    torch.cuda.synchronize()
+    wq = w.astype(np.float16).astype(np.float64) if prec == "fp16" else _round_bf16(w)
+    shape = cvae.Shape(p_in, p_out)
+    mu, lv = cvae.decoder_forward(wq, shape, cond, ze[:, :4])
+    got = mlv.cpu().numpy()
+    assert np.abs(got[:, :p_out] - mu).max() <= 3e-3
+    assert np.abs(got[:, p_out:] - lv).max() <= 3e-3
+    mu32, _ = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :4])
+    assert np.abs(got[:, :p_out] - mu32).max() <= (2e-2 if prec == "bf16" else 3e-3)
+    assert np.allclose(smp.cpu().numpy(), mu + np.exp(0.5 * lv) * ze[:, 4:], atol=1e-2)
