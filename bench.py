@@ -218,6 +218,11 @@ def main(argv=None):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # autotune the renderer's scheduling variant on a reduced sample of the same requests (untimed)
+    tune_reqs = [ms.render_params(dict(r, spp=max(1, spp // 16))) for r in reqs]
+    variant, variant_ms = ms.ms_render_autotune(tune_reqs, cset, images, stats, repeats=1, ws=ws)
+    for r in preqs:
+        r.variant = variant
     for _ in range(args.warmup):
         images.zero_()
         stats.zero_()
@@ -306,7 +311,7 @@ def main(argv=None):
     # ---------------- brute force on the same workload (context: paths/s at equal spp) ----------------
     brute = None
     if not args.no_brute:
-        breqs = [ms.render_params(dict(r, mode=ms.MS_BRUTE)) for r in reqs]
+        breqs = [ms.render_params(dict(r, mode=ms.MS_BRUTE, variant=variant)) for r in reqs]
         images.zero_()
         stats.zero_()
         ms.ms_render_batch(breqs, None, images, stats, ws=ws)   # warm-up
@@ -337,7 +342,9 @@ def main(argv=None):
                 "config": {"workload": WORKLOAD, "width": W, "height": H, "spp": spp, "sigma_t": list(SIGMAS),
                            "g": 0.8, "albedo": 0.999, "mode": "sphere", "launch": "one ms_render_batch per step",
                            "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1
-                           else "single GPU", "stats_per_request": per_req},
+                           else "single GPU", "stats_per_request": per_req,
+                           "kernel_variant": dict(index=variant, **ms.ms_render_variant_info(variant)),
+                           "autotune_ms": [round(t, 2) for t in variant_ms]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clocks, "brute_force": brute, "step_ms": step_ms}
         print(json.dumps(line), flush=True)

@@ -219,6 +219,9 @@ typedef struct {
     float min_optical_radius;   /* smallest sigma_t * r for a sphere step (thin-region fallback)      */
     float max_optical_radius;   /* largest sigma_t * r (the training range of the models)             */
     uint64_t seed, sample_offset;
+    int32_t variant;            /* kernel variant (scheduling constants), 0..ms_render_variants()-1, 0 by
+                                   default; in a batch the first request's variant is used           */
+    int32_t reserved_;
 } ms_render_params;
 
 typedef struct {
@@ -244,6 +247,19 @@ ms_status ms_render(const ms_render_params* p, const ms_cvae_set* models, double
  * starts at the sum of the previous requests' h*w; stats: device [n][MS_RENDER_STATS]. */
 ms_status ms_render_batch(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
                           unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Kernel variants of the renderer and a native autotuner.  A variant fixes the renderer's scheduling
+ * constants (how many parked lanes trigger a decoder round, how many finished marches trigger a transition
+ * round, signed-distance steps between scheduling decisions, resident blocks per SM).  ms_render_autotune
+ * renders `reqs` (a representative, usually reduced, set of requests) `repeats` times with every variant,
+ * timed with CUDA events on `stream`, and returns the fastest in *best_variant (and each variant's time in
+ * ms_per_variant[ms_render_variants()] if not NULL).  It waits for the stream; `images` and `stats` are used
+ * as scratch (they hold accumulated results of all the runs afterwards). */
+int ms_render_variants(void);
+ms_status ms_render_variant_info(int i, int* decode_batch, int* trans_batch, int* steps, int* min_blocks);
+ms_status ms_render_autotune(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
+                             unsigned long long* stats, void* workspace, size_t workspace_bytes, int repeats,
+                             int* best_variant, float* ms_per_variant, void* stream);
 
 #ifdef __cplusplus
 }

@@ -36,7 +36,6 @@ constexpr int kStats = MS_RENDER_STATS;
 constexpr float kEps = 1e-4f;       // distance from the boundary treated as on it
 constexpr int kMaxMarch = 1024;     // steps per march; running out ends the path (or drops the estimate)
 constexpr float kNMax = 16777216.0f;
-constexpr int kDecodeBatch = 16;    // parked lanes that trigger a decoder round
 
 struct Req {
     float cam[3], at[3], tan_half, aspect;
@@ -73,15 +72,20 @@ __device__ __forceinline__ float dot(V a, V b) { return fmaf(a.x, b.x, fmaf(a.y,
 __device__ __forceinline__ V cross(V a, V b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
 __device__ __forceinline__ V unit(V a) { return a * rsqrtf(dot(a, a)); }
 
+// The constants of the march held in registers for the lane's current request.
+struct Geo {
+    float A, k, inv_lip, rb2;
+};
+
 // ---- the displaced sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz) (negative inside) ----
-__device__ __forceinline__ float sdf(const Req& q, V p)
+__device__ __forceinline__ float sdf(const Geo& q, V p)
 {
     const float d2 = dot(p, p);
     const float r = d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f;
     return r - 1.0f - q.A * __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z);
 }
 
-__device__ __forceinline__ V sdf_grad(const Req& q, V p)
+__device__ __forceinline__ V sdf_grad(const Geo& q, V p)
 {
     float sx, cx, sy, cy, sz, cz;
     __sincosf(q.k * p.x, &sx, &cx);
@@ -147,14 +151,18 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
 }
 
 constexpr int kUsedStats = 10;
-constexpr int kTransBatch = 8;      // pending lanes that trigger a transition round
-constexpr int kRefillBatch = 8;     // idle lanes that trigger a refill round
+
+// Scheduling constants of a kernel variant (see ms_render_autotune): kDecodeBatch parked lanes trigger a
+// decoder round, kTransBatch pending (or idle) lanes a transition (or refill) round, and between two
+// scheduling decisions each marching lane advances kSteps signed-distance steps.
 
 enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow, kDecode, kPending };
 enum Event : int { kEvHit = 0, kEvReenter, kEvEscape, kEvCap, kEvExit, kEvCollide, kEvShadowDone };
 
-__global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_constant__ Batch B)
+template <int kDecodeBatch, int kTransBatch, int kSteps, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __grid_constant__ Batch B)
 {
+    constexpr int kRefillBatch = kTransBatch;
     __shared__ __align__(16) unsigned char sw[kBytesL + kBytesP + kBytesE];
     __shared__ float s_stage[kThreads / 32][mmadec::kStageFloats];
     __shared__ unsigned long long s_stats[kMaxReq * kStats];
@@ -192,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
     float mt = 0.0f, ml = 0.0f, din = 0.0f;
     int mstep = 0;
     bool inside = true, capped = false;
+    Geo geo{0.0f, 0.0f, 1.0f, 1.0f};
     bool drained = false;                       // warp-uniform: camera tickets exhausted
 
     auto end_path = [&]() {
@@ -244,6 +253,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
                 mt = 0.0f;
                 mstep = 0;
                 st = kCamera;
+                geo = Geo{q.A, q.k, q.inv_lip, q.rb2};
                 cnt[0] += 1u;
             }
             continue;
@@ -365,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
                     const V c = mo + md * ml;
                     bool sphere = false;
                     if (q.mode == MS_SPHERE && learned) {
-                        const float dc = -sdf(q, c) * q.inv_lip;
+                        const float dc = -sdf(geo, c) * geo.inv_lip;
                         cnt[8] += 1u;
                         rad = fminf(dc, q.tau_max / q.sigma);
                         tau = q.sigma * rad;
@@ -424,9 +434,11 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
             continue;
         }
 
-        // ================= one signed-distance step of every marching lane =================
+        // ================= kSteps signed-distance steps of every marching lane =================
+#pragma unroll 1
+        for (int step = 0; step < kSteps; ++step) {
         if (st >= kCamera && st <= kShadow) {
-            const Req& q = B.r[req];
+            const Geo& q = geo;
             const V r = mo + md * mt;
             // escape and end-of-segment tests come before the distance evaluation
             const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
@@ -500,6 +512,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
             }
             (void)at_boundary;
         }
+        }
     }
 
     // ---------------- block counters -> global ----------------
@@ -513,9 +526,25 @@ __global__ void __launch_bounds__(kThreads, 2) render_kernel(const __grid_consta
 
 using namespace ms::render;
 
+// Compiled kernel variants (scheduling constants); index 0 is the default.
+struct Variant {
+    const void* fn;
+    int decode_batch, trans_batch, steps, min_blocks;
+};
+template <int D, int T, int S, int M>
+Variant make_variant() { return Variant{(const void*)render_kernel<D, T, S, M>, D, T, S, M}; }
+static const Variant kVariants[] = {
+    make_variant<20, 12, 8, 3>(), make_variant<16, 8, 1, 2>(), make_variant<16, 8, 4, 2>(),
+    make_variant<16, 8, 8, 3>(), make_variant<20, 12, 16, 3>(), make_variant<24, 16, 8, 3>(),
+    make_variant<16, 12, 16, 3>(), make_variant<20, 12, 8, 4>(), make_variant<24, 16, 16, 3>(),
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
 static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const char* fn)
 {
     if (n < 1 || n > kMaxReq) return ms::set_error(MS_ERR_INVALID_ARG, "%s: 1..%d requests per call", fn, kMaxReq);
+    if (reqs[0].variant < 0 || reqs[0].variant >= kNumVariants)
+        return ms::set_error(MS_ERR_INVALID_ARG, "%s: variant must be in 0..%d", fn, kNumVariants - 1);
     uint64_t samples = 0, pixels = 0;
     b->n = n;
     for (int i = 0; i < n; ++i) {
@@ -609,13 +638,14 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     b.ticket = static_cast<unsigned long long*>(workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MS_CUDA(cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s));
+    const Variant& v = kVariants[reqs[0].variant];
     int per_sm = 0;
-    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel, kThreads, 0));
+    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, kThreads, 0));
     uint64_t grid = (uint64_t)ms::num_sms() * (per_sm > 0 ? per_sm : 1);
     const uint64_t need = (b.total + kThreads - 1) / kThreads;
     if (grid > need) grid = need;
-    render_kernel<<<(unsigned)grid, kThreads, 0, s>>>(b);
-    MS_CUDA(cudaGetLastError());
+    void* args[] = {&b};
+    MS_CUDA(cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(kThreads), args, 0, s));
     return MS_OK;
 }
 
@@ -630,4 +660,60 @@ extern "C" ms_status ms_render_batch(const ms_render_params* reqs, int n, const 
                                      void* stream)
 {
     return render_launch(reqs, n, models, images, stats, workspace, workspace_bytes, stream, "ms_render_batch");
+}
+
+extern "C" int ms_render_variants(void) { return kNumVariants; }
+
+extern "C" ms_status ms_render_variant_info(int i, int* decode_batch, int* trans_batch, int* steps, int* min_blocks)
+{
+    MS_CHECK_ARG(i >= 0 && i < kNumVariants, "ms_render_variant_info: variant must be in 0..%d", kNumVariants - 1);
+    if (decode_batch) *decode_batch = kVariants[i].decode_batch;
+    if (trans_batch) *trans_batch = kVariants[i].trans_batch;
+    if (steps) *steps = kVariants[i].steps;
+    if (min_blocks) *min_blocks = kVariants[i].min_blocks;
+    return MS_OK;
+}
+
+extern "C" ms_status ms_render_autotune(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
+                                        unsigned long long* stats, void* workspace, size_t workspace_bytes,
+                                        int repeats, int* best_variant, float* ms_per_variant, void* stream)
+{
+    MS_CHECK_ARG(reqs != nullptr && n >= 1 && n <= kMaxReq && best_variant != nullptr,
+                 "ms_render_autotune: need 1..%d requests and best_variant", kMaxReq);
+    MS_CHECK_ARG(repeats >= 1, "ms_render_autotune: repeats must be >= 1");
+    ms_render_params local[kMaxReq];
+    for (int i = 0; i < n; ++i) local[i] = reqs[i];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    MS_CUDA(cudaEventCreate(&e0));
+    MS_CUDA(cudaEventCreate(&e1));
+    float best = 0.0f;
+    int best_i = -1;
+    ms_status st = MS_OK;
+    for (int v = 0; v < kNumVariants && st == MS_OK; ++v) {
+        local[0].variant = v;
+        st = render_launch(local, n, models, images, stats, workspace, workspace_bytes, stream, "ms_render_autotune");
+        if (st != MS_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < repeats && st == MS_OK; ++r)
+            st = render_launch(local, n, models, images, stats, workspace, workspace_bytes, stream, "ms_render_autotune");
+        cudaEventRecord(e1, s);
+        if (st != MS_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = ms::cuda_status(cudaGetLastError(), "ms_render_autotune: cudaEventSynchronize");
+            break;
+        }
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        t /= (float)repeats;
+        if (ms_per_variant) ms_per_variant[v] = t;
+        if (best_i < 0 || t < best) {
+            best = t;
+            best_i = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == MS_OK) *best_variant = best_i;
+    return st;
 }

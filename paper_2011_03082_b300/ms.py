@@ -25,7 +25,7 @@ MS_RENDER_STATS = 16
 EXPORTS = ("ms_last_error", "ms_version", "ms_walk_workspace_size", "ms_simulate_walks", "ms_cvae_infer",
            "ms_cvae_num_params", "ms_cvae_workspace_size", "ms_cvae_forward_backward", "ms_adam_step",
            "ms_cvae_train_step", "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records", "ms_render_workspace_size", "ms_render",
-           "ms_render_batch")
+           "ms_render_batch", "ms_render_variants", "ms_render_variant_info", "ms_render_autotune")
 
 
 class MsError(RuntimeError):
@@ -70,7 +70,8 @@ class RenderParams(C.Structure):
                 ("sigma_t", C.c_float), ("g", C.c_float), ("albedo", C.c_float),
                 ("disp_amp", C.c_float), ("disp_freq", C.c_float), ("mode", C.c_int32),
                 ("min_optical_radius", C.c_float), ("max_optical_radius", C.c_float),
-                ("seed", C.c_uint64), ("sample_offset", C.c_uint64)]
+                ("seed", C.c_uint64), ("sample_offset", C.c_uint64), ("variant", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class CvaeSet(C.Structure):
@@ -106,6 +107,9 @@ def lib():
         "ms_render_workspace_size": ([P, C.c_int], C.c_size_t),
         "ms_render": ([P, P, P, P, P, C.c_size_t, P], C.c_int),
         "ms_render_batch": ([P, C.c_int, P, P, P, P, C.c_size_t, P], C.c_int),
+        "ms_render_variants": ([], C.c_int),
+        "ms_render_variant_info": ([C.c_int, P, P, P, P], C.c_int),
+        "ms_render_autotune": ([P, C.c_int, P, P, P, P, C.c_size_t, C.c_int, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         if not hasattr(L, name):
@@ -291,3 +295,23 @@ def ms_render_batch(reqs, models: CvaeSet | None, images, stats, ws=None, stream
     return _check(lib().ms_render_batch(arr, len(reqs), C.byref(models) if models is not None else None,
                                         _ptr(images), _ptr(stats), _ptr(ws), ws.numel(), _stream(stream)),
                   "ms_render_batch")
+
+
+def ms_render_autotune(reqs, models: CvaeSet | None, images, stats, repeats=1, ws=None, stream=None):
+    """Time every renderer variant on ``reqs`` and return (best variant, per-variant milliseconds)."""
+    arr = (RenderParams * len(reqs))(*reqs)
+    if ws is None:
+        ws = workspace(ms_render_workspace_size(reqs), images.device)
+    nv = int(lib().ms_render_variants())
+    times = (C.c_float * nv)()
+    best = C.c_int(-1)
+    _check(lib().ms_render_autotune(arr, len(reqs), C.byref(models) if models is not None else None, _ptr(images),
+                                    _ptr(stats), _ptr(ws), ws.numel(), repeats, C.byref(best), times,
+                                    _stream(stream)), "ms_render_autotune")
+    return best.value, list(times)
+
+
+def ms_render_variant_info(i):
+    vals = [C.c_int() for _ in range(4)]
+    _check(lib().ms_render_variant_info(i, *[C.byref(v) for v in vals]), "ms_render_variant_info")
+    return dict(zip(("decode_batch", "trans_batch", "steps", "min_blocks"), (v.value for v in vals)))

@@ -118,3 +118,24 @@ def test_bad_requests_are_rejected():
             ms.ms_render(ms.render_params(p), None, img, st)
     with pytest.raises(ms.MsError, match="decoders"):
         ms.ms_render(ms.render_params(synth.render_scene(8.0, width=2, height=2, spp=1, mode=1)), None, img, st)
+
+
+def test_kernel_variants_agree_and_autotune():
+    """Every scheduling variant traces the same paths (same counters, images equal up to the order of the
+    per-pixel additions); the autotuner returns one of them."""
+    models = _models()
+    p = synth.render_scene(64.0, width=32, height=32, spp=8, mode=1, seed=9)
+    ref_img, ref_st = None, None
+    for v in range(ms.lib().ms_render_variants()):
+        img, st = gpu_render(dict(p, variant=v), models)
+        if ref_img is None:
+            ref_img, ref_st = img, st
+        assert np.array_equal(st[:10], ref_st[:10]), v
+        assert np.allclose(img, ref_img, rtol=1e-6, atol=1e-12), v
+    dm = {k: (torch.from_numpy(w).cuda(), pi, po) for k, (w, pi, po) in models.items()}
+    imgs = torch.zeros(32 * 32, dtype=torch.float64, device="cuda")
+    st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    best, times = ms.ms_render_autotune([ms.render_params(p)], ms.cvae_set(dm), imgs, st)
+    assert 0 <= best < len(times) and min(times) == times[best] and all(t > 0 for t in times)
+    with pytest.raises(ms.MsError, match="variant"):
+        gpu_render(dict(p, variant=99), models)
