@@ -3,7 +3,7 @@
 ``python -m paper_2011_03082_b300.profile_cases CASE [--repeat R]`` with CASE one of:
   walk      65,536 photons, optical radius 8, g 0.8, albedo 0.999, isotropic start (FP32)
   walk24    2^24 walks with the training media (FP32, reservoir)
-  decoder   2^22 decoder queries, P_out 6 (FP32, Philox normals)
+  decoder   2^22 decoder queries, P_out 6 (FP32, Philox normals); decoder16: the same in FP16 (tensor cores)
   train     one training step of EventGen, batch 65,536
   render    one 128x128 px x 16 spp render at sigma_t 64, sphere tracing with the trained decoders
   brute     the same render in brute-force mode
@@ -37,12 +37,12 @@ def case_walk24():
     return case_walk(n, 2, media)
 
 
-def case_decoder(n=1 << 22, p_out=6):
+def case_decoder(n=1 << 22, p_out=6, precision=ms.MS_FP32):
     w = torch.from_numpy(synth.xavier_decoder(7, 4, p_out)).cuda()
     c = torch.from_numpy(synth.decoder_queries(7, n)).cuda()
     mlv = torch.empty(n, 2 * p_out, device="cuda")
     smp = torch.empty(n, p_out, device="cuda")
-    d = ms.decoder_struct(w, 4, p_out)
+    d = ms.decoder_struct(w, 4, p_out, precision=precision)
     return lambda: ms.ms_cvae_infer(d, c, n, seed=7, out_mean_logvar=mlv, out_sample=smp)
 
 
@@ -76,6 +76,7 @@ def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0):
 
 
 CASES = {"walk": case_walk, "walk24": case_walk24, "decoder": case_decoder, "train": case_train,
+         "decoder16": lambda: case_decoder(precision=ms.MS_FP16),
          "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE),
          "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
          "brute512": lambda: case_render(ms.MS_BRUTE, 512, 64, 128.0)}
