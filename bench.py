@@ -177,6 +177,7 @@ def main(argv=None):
     ap.add_argument("--no-brute", action="store_true", help="skip the brute-force context measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-equal-rmse", action="store_true", help="skip the equal-RMSE comparison")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -330,6 +331,15 @@ def main(argv=None):
                  "speedup_equal_spp": (bpaths / (bt / 1e3)) and value / world / (bpaths / (bt / 1e3)),
                  "events_per_path": float(stats[:, 4].sum().item()) / max(1.0, float(stats[:, 1].sum().item()))}
 
+    # ---------------- equal-RMSE comparison with brute force (context; after the timed region) ----------------
+    equal = None
+    if rank == 0 and not args.no_equal_rmse:
+        from paper_2011_03082_b300 import experiments
+        rows = experiments.equal_rmse(res=128, ref_spp=8192, st_spp=256, cset=cset, variant=variant)
+        equal = {"res": 128, "ref_spp": 8192, "st_spp": 256,
+                 "per_sigma": [{k: r[k] for k in ("sigma_t", "rmse_st", "spp_bf_equal", "t_st_s", "t_bf_equal_s",
+                                                  "speedup", "note")} for r in rows]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         dec_np = {k: pipeline.decoder_part(k, models[k]["params"]) for k in pipeline.MODELS}
@@ -346,7 +356,7 @@ def main(argv=None):
                            "kernel_variant": dict(index=variant, **ms.ms_render_variant_info(variant)),
                            "autotune_ms": [round(t, 2) for t in variant_ms]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clocks, "brute_force": brute, "step_ms": step_ms}
+                "clocks": clocks, "brute_force": brute, "equal_rmse": equal, "step_ms": step_ms}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

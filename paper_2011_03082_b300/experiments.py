@@ -1,0 +1,85 @@
+"""Equal-error comparison of sphere tracing (learned decoders) against brute-force path tracing on the GPU.
+
+For each density (the density-doubling protocol of Fig. 1 and Sec. 5.2, synthetic displaced-sphere scene):
+
+1. a brute-force reference image at ``ref_spp`` samples per pixel;
+2. the sphere-traced image at ``st_spp`` and its RMSE against the reference;
+3. brute-force images at doubling spp until their RMSE drops below the sphere tracer's; the spp at equal RMSE
+   is interpolated with RMSE ~ spp^(-1/2) between the two bracketing runs;
+4. time per path of both methods (CUDA events), hence the time each needs for that RMSE and the speed-up.
+
+The sphere tracer is biased (its samplers are learned approximations): when its error is above the brute-force
+error of the smallest ladder run, the speed-up is bounded above by that run, and the result says so.
+
+``python -m paper_2011_03082_b300.experiments [--res 128] [--ref-spp 8192] [--st-spp 256]``
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import ms, pipeline, synth
+
+
+def _render(p: dict, cset, variant=0):
+    img = torch.zeros(p["width"] * p["height"], dtype=torch.float64, device="cuda")
+    st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    rp = ms.render_params(dict(p, variant=variant))
+    ws = ms.workspace(ms.ms_render_workspace_size([rp]))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ms.ms_render(rp, cset if p["mode"] == ms.MS_SPHERE else None, img, st, ws=ws)
+    b.record()
+    b.synchronize()
+    return img.cpu().numpy() / p["spp"], a.elapsed_time(b) / 1e3
+
+
+def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=256, cset=None, variant=0):
+    if cset is None:
+        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    out = []
+    for s in sigmas:
+        base = synth.render_scene(s, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101)
+        ref, _ = _render(base, cset, variant)
+        st_img, t_st = _render(dict(base, mode=ms.MS_SPHERE, spp=st_spp, seed=202), cset, variant)
+        rmse_st = float(np.sqrt(np.mean((st_img - ref) ** 2)))
+        ladder = []
+        spp = 16
+        while spp <= ref_spp // 2:
+            img, t = _render(dict(base, spp=spp, seed=303 + spp), cset, variant)
+            ladder.append((spp, float(np.sqrt(np.mean((img - ref) ** 2))), t))
+            if ladder[-1][1] <= rmse_st:
+                break
+            spp *= 2
+        per_spp_bf = ladder[-1][2] / ladder[-1][0]
+        if ladder[0][1] <= rmse_st:
+            spp_eq, note = float(ladder[0][0]), "sphere-tracing error above the smallest brute-force run (upper bound)"
+        elif ladder[-1][1] > rmse_st:
+            spp_eq, note = float(ladder[-1][0]), "brute force did not reach the sphere-tracing error (lower bound)"
+        else:
+            (s0, e0, _), (s1, e1, _) = ladder[-2], ladder[-1]
+            # RMSE = c / sqrt(spp): fit through the bracketing pair (geometric mean of the two estimates)
+            spp_eq = float(np.sqrt(s0 * (e0 / rmse_st) ** 2 * s1 * (e1 / rmse_st) ** 2))
+            note = "interpolated"
+        t_bf = per_spp_bf * spp_eq
+        out.append(dict(sigma_t=s, res=res, ref_spp=ref_spp, st_spp=st_spp, rmse_st=rmse_st, spp_bf_equal=spp_eq,
+                        t_st_s=t_st, t_bf_equal_s=t_bf, speedup=t_bf / t_st, note=note,
+                        ladder=[dict(spp=a, rmse=b, t_s=c) for a, b, c in ladder]))
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--res", type=int, default=128)
+    ap.add_argument("--ref-spp", type=int, default=8192)
+    ap.add_argument("--st-spp", type=int, default=256)
+    a = ap.parse_args(argv)
+    for r in equal_rmse(res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp):
+        print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()
