@@ -435,49 +435,42 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         }
 
         // ================= kSteps signed-distance steps of every marching lane =================
+        // One body for every kind of march (selects, no per-kind branches), so lanes in different kinds of
+        // march stay converged; only boundary crossings, which are rare, branch.
 #pragma unroll 1
         for (int step = 0; step < kSteps; ++step) {
-        if (st >= kCamera && st <= kShadow) {
-            const Geo& q = geo;
+            if (st < kCamera || st > kShadow) continue;
             const V r = mo + md * mt;
-            // escape and end-of-segment tests come before the distance evaluation
-            const bool leaving = dot(r, r) > q.rb2 && dot(r, md) >= 0.0f;
-            const bool skip = (st == kShadow) ? (mt >= ml || (!inside && leaving))
-                                              : ((st == kCamera || st == kReentry) && leaving);
-            float f = 0.0f;
-            if (!skip) {
-                f = sdf(q, r);
-                cnt[8] += 1u;
-            }
+            const bool shadow = st == kShadow, flight = st == kFlight;
+            const bool in_medium = flight || (shadow && inside);
+            // outside the medium the march ends when it leaves the bounding sphere (escape, or the rest of
+            // a shadow segment); the end of a shadow segment is tested before the distance evaluation
+            const bool leaving = !in_medium && dot(r, r) > geo.rb2 && dot(r, md) >= 0.0f;
             ++mstep;
-            // the sign and threshold tests of the three kinds of march share one evaluation
-            const bool in_medium = st == kFlight || (st == kShadow && inside);
-            float d = (in_medium ? -f : f) * q.inv_lip;
-            bool at_boundary = false, crossing = false;
-            if (!skip && d < kEps) {
+            if ((shadow && mt >= ml) || leaving) {
+                ev = shadow ? kEvShadowDone : kEvEscape;
+                st = kPending;
+                continue;
+            }
+            const float f = sdf(geo, r);
+            cnt[8] += 1u;
+            float d = (in_medium ? -f : f) * geo.inv_lip;
+            bool crossing = false;
+            if (d < kEps) {
                 cnt[9] += 1u;
-                const float gd = dot(sdf_grad(q, r), md);
-                at_boundary = true;
+                const float gd = dot(sdf_grad(geo, r), md);
                 crossing = in_medium ? gd > 0.0f : gd < 0.0f;
                 d = kEps;
             }
-            if (st == kFlight) {
-                if (crossing) {
-                    mo = r;
+            if (crossing) {
+                if (shadow) {
+                    inside = !inside;                        // same point, other side: no step
+                    if (mstep >= kMaxMarch) { capped = true; ev = kEvShadowDone; st = kPending; }
+                } else if (flight) {
+                    mo = r;                                  // left the object at r
                     ev = kEvExit;
                     st = kPending;
-                } else if (mt + d >= ml) {
-                    ev = kEvCollide;
-                    st = kPending;
                 } else {
-                    mt += d;
-                    if (mstep >= kMaxMarch) { ev = kEvCap; st = kPending; }
-                }
-            } else if (st == kCamera || st == kReentry) {
-                if (leaving) {
-                    ev = kEvEscape;                      // escaped: black background
-                    st = kPending;
-                } else if (crossing) {
                     if (st == kCamera) {
                         cnt[1] += 1u;
                         w = md;
@@ -488,30 +481,23 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                     }
                     p = r;
                     st = kPending;
-                } else {
-                    mt += d;
-                    if (mstep >= kMaxMarch) { ev = kEvCap; st = kPending; }
                 }
-            } else {   // kShadow: length of X -> light inside the medium (Sec. 4.3, d_t)
-                bool done = skip;
-                if (!done) {
-                    if (crossing) {
-                        inside = !inside;
-                    } else {
-                        const float step = fminf(d, ml - mt);
-                        if (inside) din += step;
-                        mt += step;
-                    }
-                    if (mt >= ml) done = true;
-                    else if (mstep >= kMaxMarch) { done = true; capped = true; }
-                }
-                if (done) {
-                    ev = kEvShadowDone;
-                    st = kPending;
-                }
+                continue;
             }
-            (void)at_boundary;
-        }
+            // a flight ends at its free path, a shadow march at the light; outside marches have no limit
+            const float lim = (flight || shadow) ? ml : 3.0e38f;
+            const bool reach = mt + d >= lim;
+            const float adv = reach ? lim - mt : d;
+            if (shadow && inside) din += adv;
+            mt += adv;
+            if (reach) {
+                ev = flight ? kEvCollide : kEvShadowDone;
+                st = kPending;
+            } else if (mstep >= kMaxMarch) {
+                capped = shadow;
+                ev = shadow ? kEvShadowDone : kEvCap;
+                st = kPending;
+            }
         }
     }
 
