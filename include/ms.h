@@ -168,6 +168,18 @@ ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, float* m, fl
                              float lr, float weight_decay, float* loss3, void* workspace,
                              size_t workspace_bytes, void* stream);
 
+/* A training step whose every input lives on the device, so that one captured CUDA graph can be replayed
+ * step after step: `step` (device, the Adam step t >= 1) is read by the kernels and incremented at the end.
+ * The mini-batch is drawn with replacement from the n_records records (x_all [n][p_out], c_all [n][p_in]):
+ * sample b of step t takes record (w * n_records) >> 32, w = word 0 of counter (t_hi, t_lo, b, 0xB0) under
+ * key seed; its latent normals come from counter (0, b, t, 0xE0) as in ms_cvae_forward_backward.  Adam
+ * uses beta 0.9 / 0.999 and eps 1e-8 with bias corrections 1 - beta^t computed on the device. */
+size_t ms_cvae_train_step_dev_workspace_size(const ms_cvae_shape* s, uint64_t batch);
+ms_status ms_cvae_train_step_dev(const ms_cvae_shape* s, float* params, float* m, float* v, const float* x_all,
+                                 const float* c_all, uint64_t n_records, uint64_t B, uint64_t seed,
+                                 unsigned long long* step, float lr, float weight_decay, float* loss3,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
 /* The same training step with no workspace argument: its scratch is a fixed 16 MiB array inside the library
  * (ms_cvae_static_scratch_bytes()), for callers that must not allocate device memory — for example code whose
  * device memory is all owned by another framework's pool, or a plug-in that may not allocate while the host
@@ -236,9 +248,11 @@ size_t ms_render_workspace_size(const ms_render_params* reqs, int n_requests);
 /* image: device [height][width] doubles, accumulated: the sum over the pixel's samples (divide by spp).
  * stats: device [MS_RENDER_STATS] accumulated: [0] camera paths, [1] paths entering the object, [2] flights,
  * [3] sphere steps, [4] brute-force events, [5] absorbed, [6] truncated paths or dropped estimates,
- * [7] next-event estimates, [8] SDF distance evaluations, [9] SDF gradient evaluations, [10..15] zero.
+ * [7] next-event estimates, [8] SDF distance evaluations, [9] SDF gradient evaluations, [10] completion time
+ * of the request in ns after the launch's first block started (written, not accumulated), [11..15] zero.
  * models: host struct with device weight pointers (ignored in MS_BRUTE).  workspace:
- * ms_render_workspace_size() bytes (the sample ticket).  One persistent launch; asynchronous. */
+ * ms_render_workspace_size() bytes (sample ticket, start time, finished-path counters).  One persistent
+ * launch; asynchronous; capturable in a CUDA graph (a memset and a kernel). */
 #define MS_RENDER_STATS 16
 ms_status ms_render(const ms_render_params* p, const ms_cvae_set* models, double* image,
                     unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream);

@@ -275,6 +275,53 @@ __global__ void adam(float* __restrict__ p, float* __restrict__ m, float* __rest
     p[i] = w - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// ---- graph-replayable step: everything keyed by a step counter in device memory ----
+
+// Mini-batch b of step t: record index mulhi(w, n) with w word 0 of counter (t, b, 0, 0xB0) (uniform, with
+// replacement), and the latent normals of counter (0, b, t, 0xE0) (the same as the host-step path).
+__global__ void gather_batch(const float* __restrict__ x_all, const float* __restrict__ c_all, uint64_t n, int p_out,
+                             int p_in, uint64_t B, uint64_t seed, const unsigned long long* __restrict__ step,
+                             float* __restrict__ xb, float* __restrict__ cb, float* __restrict__ eps)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const unsigned long long t = *step;
+    const Stream pick(seed, ((uint64_t)(uint32_t)t) | (b << 32));
+    const Words w = pick.at((uint32_t)(t >> 32), 0xB0u);
+    const uint64_t i = ((uint64_t)w.w0 * n) >> 32;
+    for (int j = 0; j < p_out; ++j) xb[b * p_out + j] = x_all[i * p_out + j];
+    for (int j = 0; j < p_in; ++j) cb[b * p_in + j] = c_all[i * p_in + j];
+    const Stream st(seed, (t << 32) | (b & 0xffffffffull));
+    const Words e = st.at(0u, 0xE0u);
+    const float2 p0 = box_muller(e.w0, e.w1), p1 = box_muller(e.w2, e.w3);
+    eps[b * kL] = p0.x; eps[b * kL + 1] = p0.y; eps[b * kL + 2] = p1.x; eps[b * kL + 3] = p1.y;
+}
+
+// Adam with the step t read from device memory (bias corrections computed here).
+__global__ void adam_dev(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                         const float* __restrict__ g, uint64_t n, float lr, float b1, float b2, float eps, float wd,
+                         const unsigned long long* __restrict__ step)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double t = (double)*step;
+    const float c1 = (float)(1.0 - pow((double)b1, t));
+    const float c2 = (float)(1.0 - pow((double)b2, t));
+    float w = p[i];
+    if (wd != 0.0f) w = w - lr * wd * w;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] = w - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void bump_step(unsigned long long* step)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1ull;
+}
+
 struct Plan {
     int np = 0;
     cudaError_t (*launch)(const float*, const float*, const float*, const float*, uint64_t, uint64_t, uint64_t,
@@ -406,4 +453,53 @@ extern "C" ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, f
                                   stream);
     if (st != MS_OK) return st;
     return ms_adam_step(params, m, v, grad, (uint64_t)pl.np, step, lr, 0.9f, 0.999f, 1e-8f, weight_decay, stream);
+}
+
+// Scratch of the device-step training step: the ms_cvae_train_step workspace, then the gathered batch and its
+// latent normals.
+static size_t dev_step_extra(const ms_cvae_shape* s, uint64_t B)
+{
+    const size_t f = (size_t)B * (size_t)(s->p_out + s->p_in + kL) * sizeof(float);
+    return (f + 255) & ~(size_t)255;
+}
+
+extern "C" size_t ms_cvae_train_step_dev_workspace_size(const ms_cvae_shape* s, uint64_t batch)
+{
+    if (!s) return 0;
+    return ms_cvae_workspace_size(s, batch) + dev_step_extra(s, batch);
+}
+
+extern "C" ms_status ms_cvae_train_step_dev(const ms_cvae_shape* s, float* params, float* m, float* v,
+                                            const float* x_all, const float* c_all, uint64_t n_records, uint64_t B,
+                                            uint64_t seed, unsigned long long* step, float lr, float weight_decay,
+                                            float* loss3, void* workspace, size_t workspace_bytes, void* stream)
+{
+    Plan pl;
+    ms_status st = check_shape(s, "ms_cvae_train_step_dev", &pl);
+    if (st != MS_OK) return st;
+    MS_CHECK_ARG(x_all && c_all && step && params && m && v, "ms_cvae_train_step_dev: null argument");
+    MS_CHECK_ARG(n_records >= 1 && n_records < (1ull << 32), "ms_cvae_train_step_dev: 1 <= n_records < 2^32");
+    MS_CHECK_ARG(B >= 1 && B < (1ull << 31), "ms_cvae_train_step_dev: batch must be in [1, 2^31)");
+    const size_t base = ms_cvae_workspace_size(s, B);
+    MS_CHECK_ARG(workspace && workspace_bytes >= base + dev_step_extra(s, B) && ((uintptr_t)workspace & 255u) == 0,
+                 "ms_cvae_train_step_dev: a 256-byte aligned workspace of ms_cvae_train_step_dev_workspace_size() "
+                 "bytes is required");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    float* xb = reinterpret_cast<float*>(static_cast<char*>(workspace) + base);
+    float* cb = xb + B * s->p_out;
+    float* eps = cb + B * s->p_in;
+    gather_batch<<<(unsigned)((B + 255) / 256), 256, 0, cs>>>(x_all, c_all, n_records, s->p_out, s->p_in, B, seed,
+                                                                step, xb, cb, eps);
+    MS_CUDA(cudaGetLastError());
+    const size_t nblk = (size_t)((B + kSamples - 1) / kSamples);
+    const size_t partial_bytes = ((nblk * (pl.np + 2) * sizeof(float)) + 255) & ~(size_t)255;
+    float* grad = reinterpret_cast<float*>(static_cast<char*>(workspace) + partial_bytes);
+    st = ms_cvae_forward_backward(s, params, xb, cb, eps, B, seed, 0, grad, loss3, workspace, base, stream);
+    if (st != MS_OK) return st;
+    adam_dev<<<(unsigned)((pl.np + 255) / 256), 256, 0, cs>>>(params, m, v, grad, (uint64_t)pl.np, lr, 0.9f, 0.999f,
+                                                               1e-8f, weight_decay, step);
+    MS_CUDA(cudaGetLastError());
+    bump_step<<<1, 32, 0, cs>>>(step);
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
 }

@@ -56,8 +56,17 @@ struct Batch {
     const float* wE;
     double* image;
     unsigned long long* stats;       // [n][kStats]
-    unsigned long long* ticket;
+    unsigned long long* ticket;      // workspace: sample ticket, start time, finished paths per request
+    unsigned long long* t_start;
+    unsigned long long* done;        // [kMaxReq]
 };
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // decoder shapes: LengthGen (2 + 4 -> 1), PathGen (3 + 4 -> 3), EventGen (7 + 4 -> 6); tensor-core fragment
 // layouts in shared memory (decoder_mma.cuh)
@@ -178,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         mmadec::stage_weights<false>(wev, B.wE, 7 + 4, 6);
     }
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
+    if (tid == 0) atomicMin(B.t_start, global_ns());
     __syncthreads();
 
     // counters of the lane's current path (flushed into its request's shared counters when the path ends)
@@ -204,7 +214,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     bool drained = false;                       // warp-uniform: camera tickets exhausted
 
     auto end_path = [&]() {
-        if (acc != 0.0f) atomicAdd(&B.image[B.r[req].image_offset + id_hi], (double)acc);
+        const Req& qe = B.r[req];
+        if (acc != 0.0f) atomicAdd(&B.image[qe.image_offset + id_hi], (double)acc);
+        // the request's last path: record its completion time (ns after the first block started)
+        const unsigned long long total_r = (unsigned long long)qe.W * qe.H * qe.spp;
+        if (atomicAdd(&B.done[req], 1ull) + 1ull == total_r)
+            atomicExch(&B.stats[req * kStats + 10], global_ns() - *((volatile unsigned long long*)B.t_start));
 #pragma unroll
         for (int j = 0; j < kUsedStats; ++j) {
             if (cnt[j]) atomicAdd(&s_stats[req * kStats + j], (unsigned long long)cnt[j]);
@@ -588,7 +603,7 @@ extern "C" size_t ms_render_workspace_size(const ms_render_params* reqs, int n_r
 {
     (void)reqs;
     (void)n_requests;
-    return 256;
+    return 1024;   // ticket, start time, finished-path counters of up to 64 requests
 }
 
 static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
@@ -622,8 +637,11 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     b.image = images;
     b.stats = stats;
     b.ticket = static_cast<unsigned long long*>(workspace);
+    b.t_start = b.ticket + 1;
+    b.done = b.ticket + 2;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    MS_CUDA(cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s));
+    MS_CUDA(cudaMemsetAsync(workspace, 0, (2 + kMaxReq) * sizeof(unsigned long long), s));
+    MS_CUDA(cudaMemsetAsync(b.t_start, 0xff, sizeof(unsigned long long), s));
     const Variant& v = kVariants[reqs[0].variant];
     int per_sm = 0;
     MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, kThreads, 0));

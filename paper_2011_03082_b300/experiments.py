@@ -11,7 +11,8 @@ For each density (the density-doubling protocol of Fig. 1 and Sec. 5.2, syntheti
 The sphere tracer is biased (its samplers are learned approximations): when its error is above the brute-force
 error of the smallest ladder run, the speed-up is bounded above by that run, and the result says so.
 
-``python -m paper_2011_03082_b300.experiments [--res 128] [--ref-spp 8192] [--st-spp 256]``
+``python -m paper_2011_03082_b300.experiments [--res 128] [--ref-spp 8192] [--st-spp 256]``, and
+``python -m paper_2011_03082_b300.experiments --batched [--scale 0.25]`` for the 64-request batch.
 """
 from __future__ import annotations
 
@@ -71,12 +72,69 @@ def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=2
     return out
 
 
+def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None):
+    """The heterogeneous batch: ``n`` requests (resolution, spp, density, g, albedo, displacement frequency
+    drawn with ``seed``; ``scale`` shrinks resolution and spp) in one persistent launch, autotuned, captured in
+    a CUDA graph and replayed; reports light paths per second, per-request completion p50 / p99 and the time
+    of the same requests rendered one launch at a time."""
+    if cset is None:
+        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    reqs = [ms.render_params(r) for r in synth.batch_requests(seed, n, scale=scale)]
+    npx = sum(r.width * r.height for r in reqs)
+    paths = sum(r.width * r.height * r.spp for r in reqs)
+    imgs = torch.zeros(npx, dtype=torch.float64, device="cuda")
+    st = torch.zeros(n, ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    ws = ms.workspace(ms.ms_render_workspace_size(reqs))
+    tune = [ms.render_params(dict(synth.batch_requests(seed, n, scale=scale)[i], spp=max(1, reqs[i].spp // 16)))
+            for i in range(n)]
+    variant, _ = ms.ms_render_autotune(tune, cset, imgs, st, ws=ws)
+    for r in reqs:
+        r.variant = variant
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            imgs.zero_()
+            st.zero_()
+            ms.ms_render_batch(reqs, cset, imgs, st, ws=ws)
+    g.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    done_ms = st[:, 10].double().cpu().numpy() / 1e6
+    # the same requests, one launch each
+    one = torch.zeros(max(r.width * r.height for r in reqs), dtype=torch.float64, device="cuda")
+    ost = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for r in reqs:
+        ms.ms_render(r, cset, one, ost, ws=ws)
+    b.record()
+    b.synchronize()
+    t = float(np.median(times))
+    return dict(requests=n, scale=scale, paths=paths, seconds=t, paths_per_s=paths / t, variant=variant,
+                p50_ms=float(np.percentile(done_ms, 50)), p99_ms=float(np.percentile(done_ms, 99)),
+                sequential_seconds=a.elapsed_time(b) / 1e3)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--res", type=int, default=128)
     ap.add_argument("--ref-spp", type=int, default=8192)
     ap.add_argument("--st-spp", type=int, default=256)
+    ap.add_argument("--batched", action="store_true", help="run the 64-request batch instead")
+    ap.add_argument("--scale", type=float, default=0.25)
     a = ap.parse_args(argv)
+    if a.batched:
+        print(json.dumps(batched(scale=a.scale)))
+        return
     for r in equal_rmse(res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp):
         print(json.dumps(r))
 

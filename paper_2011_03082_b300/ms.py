@@ -24,7 +24,8 @@ MS_RENDER_STATS = 16
 # the C ABI's exported symbols (checked by the tests against include/ms.h)
 EXPORTS = ("ms_last_error", "ms_version", "ms_walk_workspace_size", "ms_simulate_walks", "ms_cvae_infer",
            "ms_cvae_num_params", "ms_cvae_workspace_size", "ms_cvae_forward_backward", "ms_adam_step",
-           "ms_cvae_train_step", "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records", "ms_render_workspace_size", "ms_render",
+           "ms_cvae_train_step", "ms_cvae_train_step_dev_workspace_size", "ms_cvae_train_step_dev",
+           "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records", "ms_render_workspace_size", "ms_render",
            "ms_render_batch", "ms_render_variants", "ms_render_variant_info", "ms_render_autotune")
 
 
@@ -101,6 +102,8 @@ def lib():
         "ms_cvae_forward_backward": ([P, P, P, P, P, U64, U64, U64, P, P, P, C.c_size_t, P], C.c_int),
         "ms_adam_step": ([P, P, P, P, U64, U64, F, F, F, F, F, P], C.c_int),
         "ms_cvae_train_step": ([P, P, P, P, P, P, P, U64, U64, U64, F, F, P, P, C.c_size_t, P], C.c_int),
+        "ms_cvae_train_step_dev_workspace_size": ([P, U64], C.c_size_t),
+        "ms_cvae_train_step_dev": ([P, P, P, P, P, P, U64, U64, U64, P, F, F, P, P, C.c_size_t, P], C.c_int),
         "ms_cvae_static_scratch_bytes": ([], C.c_size_t),
         "ms_cvae_train_step_static": ([P, P, P, P, P, P, P, U64, U64, U64, F, F, P, P], C.c_int),
         "ms_training_records": ([U64, P, P, P, P, P, P, I32, U64, P, P, P, P, P, P, P], C.c_int),
@@ -232,6 +235,18 @@ def ms_cvae_train_step(shape, params, m, v, x, c, B, *, eps_z=None, seed=1, step
     return _check(lib().ms_cvae_train_step(C.byref(shape), _ptr(params), _ptr(m), _ptr(v), _ptr(x), _ptr(c),
                                            _ptr(eps_z), B, seed, step, lr, weight_decay, _ptr(loss3), _ptr(ws),
                                            ws.numel(), _stream(stream)), "ms_cvae_train_step")
+
+
+def ms_cvae_train_step_dev(shape, params, m, v, x_all, c_all, n_records, B, step_dev, *, seed=1, lr=1e-3,
+                           weight_decay=0.0, loss3=None, ws=None, stream=None):
+    """One graph-replayable training step: batch sampling, normals and Adam's t all on the device; step_dev is
+    a one-element int64 device tensor holding t (incremented by the call's kernels)."""
+    if ws is None:
+        ws = workspace(int(lib().ms_cvae_train_step_dev_workspace_size(C.byref(shape), B)), params.device)
+    return _check(lib().ms_cvae_train_step_dev(C.byref(shape), _ptr(params), _ptr(m), _ptr(v), _ptr(x_all),
+                                               _ptr(c_all), n_records, B, seed, _ptr(step_dev), lr, weight_decay,
+                                               _ptr(loss3), _ptr(ws), ws.numel(), _stream(stream)),
+                  "ms_cvae_train_step_dev")
 
 
 def ms_cvae_train_step_static(shape, params, m, v, x, c, B, *, eps_z=None, seed=1, step=1, lr=1e-3,

@@ -5,8 +5,9 @@
    (optical radius log-uniform in [1,256], g U[0,0.95], albedo U[0.9,1]); the path follows the albedo-1
    physics and the representative event is chosen with weights albedo^k (``reservoir=2``); the records are
    turned into the conditions and targets of LengthGen, PathGen and EventGen by ``ms_training_records``.
-2. ``train``: each CVAE is trained with the library's forward/backward/Adam kernels (``ms_cvae_train_step``)
-   on random mini-batches.
+2. ``train``: each CVAE is trained with the library's kernels: one step (mini-batch drawn on the device,
+   forward, backward, deterministic reduction, Adam) is captured in a CUDA graph and replayed
+   (``ms_cvae_train_step_dev``).
 3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder) and
    the training log.
 
@@ -46,24 +47,29 @@ def generate_records(n_walks: int, seed: int = 1, device="cuda") -> dict:
 
 def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch: int, lr: float, seed: int,
               log_every: int = 100):
+    """Train one CVAE: one training step (device-side batch sampling, forward, backward, deterministic
+    reduction, Adam with its step counter on the device) is captured in a CUDA graph and replayed."""
     p_in, p_out = synth.MODEL_SHAPES[name]
     shape = ms.cvae_shape(p_in, p_out)
-    params = torch.from_numpy(synth.xavier_cvae(seed, p_in, p_out)).to(c.device)
+    dev = c.device
+    params = torch.from_numpy(synth.xavier_cvae(seed, p_in, p_out)).to(dev)
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
-    ws = ms.workspace(ms.ms_cvae_workspace_size(shape, batch), c.device)
-    loss3 = torch.zeros(3, device=c.device)
-    gen = torch.Generator(device=c.device)
-    gen.manual_seed(seed)
+    step = torch.ones(1, dtype=torch.int64, device=dev)
+    loss3 = torch.zeros(3, device=dev)
+    ws = ms.workspace(int(ms.lib().ms_cvae_train_step_dev_workspace_size(ms.C.byref(shape), batch)), dev)
+    x = x.contiguous()
+    c = c.contiguous()
     n = c.shape[0]
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph):
+            ms.ms_cvae_train_step_dev(shape, params, m, v, x, c, n, batch, step, seed=seed, lr=lr, loss3=loss3, ws=ws)
     log = []
-    xb = torch.empty(batch, p_out, device=c.device)
-    cb = torch.empty(batch, p_in, device=c.device)
     for t in range(1, steps + 1):
-        idx = torch.randint(0, n, (batch,), device=c.device, generator=gen)
-        torch.index_select(x, 0, idx, out=xb)
-        torch.index_select(c, 0, idx, out=cb)
-        ms.ms_cvae_train_step(shape, params, m, v, xb, cb, batch, seed=seed, step=t, lr=lr, loss3=loss3, ws=ws)
+        graph.replay()
         if t % log_every == 0 or t == 1 or t == steps:
             log.append((t, *[float(v_) for v_ in loss3.tolist()]))
     return params, log

@@ -113,3 +113,50 @@ def test_unsupported_shape_is_rejected():
     with pytest.raises(ms.MsError, match="not built"):
         ms.ms_cvae_forward_backward(shape, torch.zeros(10, device="cuda"), torch.zeros(10, device="cuda"),
                                     torch.zeros(10, device="cuda"), 2, ws=ms.workspace(1 << 20))
+
+
+def _dev_step_reference(orc, p0, xa, ca, shape, B, seed, steps, lr):
+    """Oracle training with the device-step sampling rule: record (w * n) >> 32 with w = word 0 of counter
+    (0, t, b, 0xB0), latent normals from counter (0, b, t, 0xE0)."""
+    n = xa.shape[0]
+    p, m, v = p0.astype(np.float64), np.zeros(p0.size), np.zeros(p0.size)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for t in range(1, steps + 1):
+        idx = np.array([(int(orc.philox([0, t, b, 0xB0], key)[0]) * n) >> 32 for b in range(B)])
+        eps = orc.normals_from_words(orc.philox_words(seed, t << 32, B, 0, 0xE0))
+        _, _, _, g = cvae.neg_elbo_grad(p, shape, xa[idx], ca[idx], eps)
+        p, m, v = cvae.adam_step(p, m, v, g, t, lr)
+    return p
+
+
+def test_device_step_training_matches_oracle_and_replays_in_a_graph(orc):
+    p_in, p_out, n, B, steps, seed, lr = 3, 3, 5000, 1024, 5, 21, 1e-2
+    p0, xa, ca, _ = _data(p_in, p_out, n, 8)
+    shape = ms.cvae_shape(p_in, p_out)
+    ref = _dev_step_reference(orc, p0, xa, ca, cvae.Shape(p_in, p_out), B, seed, steps, lr)
+
+    def run(graph: bool):
+        p, m, v = _dev(p0.copy()), torch.zeros(p0.size, device="cuda"), torch.zeros(p0.size, device="cuda")
+        step = torch.ones(1, dtype=torch.int64, device="cuda")
+        loss3 = torch.zeros(3, device="cuda")
+        ws = ms.workspace(ms.lib().ms_cvae_train_step_dev_workspace_size(ms.C.byref(shape), B))
+        x, c = _dev(xa), _dev(ca)
+        if not graph:
+            for _ in range(steps):
+                ms.ms_cvae_train_step_dev(shape, p, m, v, x, c, n, B, step, seed=seed, lr=lr, loss3=loss3, ws=ws)
+        else:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g):
+                    ms.ms_cvae_train_step_dev(shape, p, m, v, x, c, n, B, step, seed=seed, lr=lr, loss3=loss3, ws=ws)
+            for _ in range(steps):
+                g.replay()
+        torch.cuda.synchronize()
+        assert int(step.item()) == steps + 1
+        return p.cpu().numpy()
+
+    direct, replayed = run(False), run(True)
+    assert np.array_equal(direct, replayed)
+    assert np.abs(direct - ref).max() <= 2e-4 * max(1.0, np.abs(ref).max()), np.abs(direct - ref).max()
