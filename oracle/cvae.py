@@ -8,6 +8,9 @@ Plain restatement of Sec. 3.2 of the paper ("Model architectures and inference")
   negative ELBO averaged over the batch, with one reparameterised latent sample z = mu + sqrt(Sigma) eps.
 * Inference draws z ~ N(0, I) and returns x = sqrt(Sigma_Dec) eps + mu_Dec.
 * The optimiser is Adam (AdamW's decoupled weight decay is a flag), as named in Sec. 3.2.
+* A BF16 training variant (not in the paper; a precision choice of the training step): weight matrices and
+  every layer's input are rounded to bfloat16 (nearest even), everything else stays FP64 here; the gradient
+  with respect to the master weights is the gradient with respect to the rounded ones.
 
 Parameter packing (float arrays, row-major [out][in] matrices):
   encoder  E1[W][P_out+P_in] e1[W] E2[W][W] e2[W] E3[2L][W] e3[2L]     input order [x ; c]
@@ -78,13 +81,25 @@ def sigmoid(a):
     return 0.5 * (1.0 + np.tanh(0.5 * a))
 
 
-def mlp3(Wa, ba, Wb, bb, Wc, bc, inp):
+def round_bf16(a):
+    """Round to bfloat16, nearest even (through float32, whose top 16 bits are bfloat16)."""
+    b = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _q(a, bf16):
+    return round_bf16(a) if bf16 else a
+
+
+def mlp3(Wa, ba, Wb, bb, Wc, bc, inp, bf16=False):
     """Three weight layers with Softplus after the first two (Sec. 3.2, Fig. 3b)."""
-    a1 = inp @ Wa.T + ba
-    h1 = softplus(a1)
-    a2 = h1 @ Wb.T + bb
-    h2 = softplus(a2)
-    out = h2 @ Wc.T + bc
+    inp = _q(inp, bf16)
+    a1 = inp @ _q(Wa, bf16).T + ba
+    h1 = _q(softplus(a1), bf16)
+    a2 = h1 @ _q(Wb, bf16).T + bb
+    h2 = _q(softplus(a2), bf16)
+    out = h2 @ _q(Wc, bf16).T + bc
     return out, (inp, a1, h1, a2, h2)
 
 
@@ -102,7 +117,7 @@ def decoder_sample(dec_params, shape: Shape, c, z, eps):
     return mu + np.exp(0.5 * lv) * np.asarray(eps, np.float64)
 
 
-def neg_elbo(params, shape: Shape, x, c, eps_z):
+def neg_elbo(params, shape: Shape, x, c, eps_z, bf16=False):
     """Negative ELBO averaged over the batch; returns (loss, rec, kl, cache)."""
     enc, dec = split_cvae(np.asarray(params, np.float64), shape)
     x = np.asarray(x, np.float64)
@@ -110,19 +125,19 @@ def neg_elbo(params, shape: Shape, x, c, eps_z):
     eps_z = np.asarray(eps_z, np.float64)
     L, P = shape.latent, shape.p_out
     eo, ecache = mlp3(enc["E1"], enc["e1"], enc["E2"], enc["e2"], enc["E3"], enc["e3"],
-                      np.concatenate([x, c], axis=1))
+                      np.concatenate([x, c], axis=1), bf16)
     mu_e, lv_e = eo[:, :L], eo[:, L:]
     sd_e = np.exp(0.5 * lv_e)
     z = mu_e + sd_e * eps_z
     do, dcache = mlp3(dec["D1"], dec["d1"], dec["D2"], dec["d2"], dec["D3"], dec["d3"],
-                      np.concatenate([c, z], axis=1))
+                      np.concatenate([c, z], axis=1), bf16)
     mu_d, lv_d = do[:, :P], do[:, P:]
     r = x - mu_d
     inv_var = np.exp(-lv_d)
     rec = 0.5 * np.sum(lv_d + r * r * inv_var + LOG_2PI, axis=1)
     kl = 0.5 * np.sum(mu_e * mu_e + np.exp(lv_e) - lv_e - 1.0, axis=1)
     cache = dict(enc=enc, dec=dec, ecache=ecache, dcache=dcache, mu_e=mu_e, lv_e=lv_e, sd_e=sd_e,
-                 r=r, inv_var=inv_var, eps_z=eps_z)
+                 r=r, inv_var=inv_var, eps_z=eps_z, bf16=bf16)
     return float(np.mean(rec + kl)), float(np.mean(rec)), float(np.mean(kl)), cache
 
 
@@ -142,19 +157,22 @@ def _mlp3_backward(Wa, Wb, Wc, cache, dout):
     return (gWa, gba, gWb, gbb, gWc, gbc), dinp
 
 
-def neg_elbo_grad(params, shape: Shape, x, c, eps_z):
+def neg_elbo_grad(params, shape: Shape, x, c, eps_z, bf16=False):
     """Analytic gradient of neg_elbo with respect to the packed parameters; returns (loss, rec, kl, grad)."""
-    loss, rec, kl, C = neg_elbo(params, shape, x, c, eps_z)
+    loss, rec, kl, C = neg_elbo(params, shape, x, c, eps_z, bf16)
+    qw = lambda W: _q(W, bf16)
     B = x.shape[0]
     L = shape.latent
     enc, dec = C["enc"], C["dec"]
     dmu_d = -C["r"] * C["inv_var"] / B
     dlv_d = 0.5 * (1.0 - C["r"] * C["r"] * C["inv_var"]) / B
-    gdec, dinp = _mlp3_backward(dec["D1"], dec["D2"], dec["D3"], C["dcache"], np.concatenate([dmu_d, dlv_d], 1))
+    gdec, dinp = _mlp3_backward(qw(dec["D1"]), qw(dec["D2"]), qw(dec["D3"]), C["dcache"],
+                                np.concatenate([dmu_d, dlv_d], 1))
     dz = dinp[:, shape.p_in:]
     dmu_e = dz + C["mu_e"] / B
     dlv_e = dz * C["eps_z"] * 0.5 * C["sd_e"] + 0.5 * (np.exp(C["lv_e"]) - 1.0) / B
-    genc, _ = _mlp3_backward(enc["E1"], enc["E2"], enc["E3"], C["ecache"], np.concatenate([dmu_e, dlv_e], 1))
+    genc, _ = _mlp3_backward(qw(enc["E1"]), qw(enc["E2"]), qw(enc["E3"]), C["ecache"],
+                             np.concatenate([dmu_e, dlv_e], 1))
     grad = np.concatenate([g.ravel() for g in genc] + [g.ravel() for g in gdec])
     assert grad.size == shape.n_params and L == shape.latent
     return loss, rec, kl, grad

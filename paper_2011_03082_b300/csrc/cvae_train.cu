@@ -14,7 +14,12 @@
 //  * reduce: one thread per parameter sums the block partials in block order and writes the gradient and
 //    the loss terms.
 //  * adam: element-wise bias-corrected Adam (AdamW decay when weight_decay > 0).
+// Precision: MS_FP32, or MS_BF16 — weight matrices and every layer's input rounded to BF16 (round to nearest
+// even) in the forward and backward passes, with biases, pre-activations, accumulation, losses, gradients,
+// master weights and Adam in FP32 (mixed-precision training numerics).
 #include <cmath>
+
+#include <cuda_bf16.h>
 
 #include "ms_device.cuh"
 
@@ -40,7 +45,15 @@ struct Shape {
 
 __device__ __forceinline__ float sigmoidf_fast(float a) { return __fdividef(1.0f, 1.0f + __expf(-a)); }
 
-template <int K, int O>
+// value as the layer sees it: unchanged in FP32, rounded to BF16 (nearest even) in the BF16 variant
+template <bool kBF16>
+__device__ __forceinline__ float rq(float x)
+{
+    if constexpr (kBF16) return __bfloat162float(__float2bfloat16_rn(x));
+    else return x;
+}
+
+template <int K, int O, bool kBF16>
 __device__ __forceinline__ void fwd_layer(const float* __restrict__ Wm, const float* __restrict__ b,
                                           const float (&x)[K], float (&a)[O])
 {
@@ -48,13 +61,13 @@ __device__ __forceinline__ void fwd_layer(const float* __restrict__ Wm, const fl
     for (int o = 0; o < O; ++o) {
         float acc = __ldg(b + o);
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc = fmaf(__ldg(Wm + o * K + k), x[k], acc);
+        for (int k = 0; k < K; ++k) acc = fmaf(rq<kBF16>(__ldg(Wm + o * K + k)), x[k], acc);
         a[o] = acc;
     }
 }
 
 // dx = W^T da
-template <int K, int O>
+template <int K, int O, bool kBF16>
 __device__ __forceinline__ void bwd_layer(const float* __restrict__ Wm, const float (&da)[O], float (&dx)[K])
 {
 #pragma unroll
@@ -62,10 +75,10 @@ __device__ __forceinline__ void bwd_layer(const float* __restrict__ Wm, const fl
 #pragma unroll
     for (int o = 0; o < O; ++o)
 #pragma unroll
-        for (int k = 0; k < K; ++k) dx[k] = fmaf(__ldg(Wm + o * K + k), da[o], dx[k]);
+        for (int k = 0; k < K; ++k) dx[k] = fmaf(rq<kBF16>(__ldg(Wm + o * K + k)), da[o], dx[k]);
 }
 
-template <int PI, int PO>
+template <int PI, int PO, bool kBF16>
 __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ prm, const float* __restrict__ X,
                                                     const float* __restrict__ Cc, const float* __restrict__ EPS,
                                                     uint64_t B, uint64_t seed, uint64_t step,
@@ -87,9 +100,9 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
 #pragma unroll
     for (int j = 0; j < PI; ++j) c[j] = live ? Cc[b * PI + j] : 0.0f;
 #pragma unroll
-    for (int j = 0; j < PO; ++j) xin[j] = x[j];
+    for (int j = 0; j < PO; ++j) xin[j] = rq<kBF16>(x[j]);
 #pragma unroll
-    for (int j = 0; j < PI; ++j) xin[PO + j] = c[j];
+    for (int j = 0; j < PI; ++j) xin[PO + j] = rq<kBF16>(c[j]);
     float eps[kL];
     if (EPS) {
 #pragma unroll
@@ -101,13 +114,13 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
         eps[0] = p0.x; eps[1] = p0.y; eps[2] = p1.x; eps[3] = p1.y;
     }
     float a1e[kW], h1e[kW], a2e[kW], h2e[kW], oe[2 * kL];
-    fwd_layer<S::IE, kW>(prm + S::E1, prm + S::e1, xin, a1e);
+    fwd_layer<S::IE, kW, kBF16>(prm + S::E1, prm + S::e1, xin, a1e);
 #pragma unroll
-    for (int o = 0; o < kW; ++o) h1e[o] = softplus(a1e[o]);
-    fwd_layer<kW, kW>(prm + S::E2, prm + S::e2, h1e, a2e);
+    for (int o = 0; o < kW; ++o) h1e[o] = rq<kBF16>(softplus(a1e[o]));
+    fwd_layer<kW, kW, kBF16>(prm + S::E2, prm + S::e2, h1e, a2e);
 #pragma unroll
-    for (int o = 0; o < kW; ++o) h2e[o] = softplus(a2e[o]);
-    fwd_layer<kW, 2 * kL>(prm + S::E3, prm + S::e3, h2e, oe);
+    for (int o = 0; o < kW; ++o) h2e[o] = rq<kBF16>(softplus(a2e[o]));
+    fwd_layer<kW, 2 * kL, kBF16>(prm + S::E3, prm + S::e3, h2e, oe);
     float sd_e[kL], z[kL];
 #pragma unroll
     for (int l = 0; l < kL; ++l) {
@@ -116,17 +129,17 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     }
     float din[S::ID];
 #pragma unroll
-    for (int j = 0; j < PI; ++j) din[j] = c[j];
+    for (int j = 0; j < PI; ++j) din[j] = rq<kBF16>(c[j]);
 #pragma unroll
-    for (int l = 0; l < kL; ++l) din[PI + l] = z[l];
+    for (int l = 0; l < kL; ++l) din[PI + l] = rq<kBF16>(z[l]);
     float a1d[kW], h1d[kW], a2d[kW], h2d[kW], y[2 * PO];
-    fwd_layer<S::ID, kW>(prm + S::D1, prm + S::d1, din, a1d);
+    fwd_layer<S::ID, kW, kBF16>(prm + S::D1, prm + S::d1, din, a1d);
 #pragma unroll
-    for (int o = 0; o < kW; ++o) h1d[o] = softplus(a1d[o]);
-    fwd_layer<kW, kW>(prm + S::D2, prm + S::d2, h1d, a2d);
+    for (int o = 0; o < kW; ++o) h1d[o] = rq<kBF16>(softplus(a1d[o]));
+    fwd_layer<kW, kW, kBF16>(prm + S::D2, prm + S::d2, h1d, a2d);
 #pragma unroll
-    for (int o = 0; o < kW; ++o) h2d[o] = softplus(a2d[o]);
-    fwd_layer<kW, 2 * PO>(prm + S::D3, prm + S::d3, h2d, y);
+    for (int o = 0; o < kW; ++o) h2d[o] = rq<kBF16>(softplus(a2d[o]));
+    fwd_layer<kW, 2 * PO, kBF16>(prm + S::D3, prm + S::d3, h2d, y);
 
     const float invB = 1.0f / (float)B;
     float rec = 0.0f, kl = 0.0f;
@@ -144,13 +157,13 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
 
     // ---------------- backward ----------------
     float dh[kW], da2d[kW], da1d[kW], ddin[S::ID];
-    bwd_layer<kW, 2 * PO>(prm + S::D3, dy, dh);
+    bwd_layer<kW, 2 * PO, kBF16>(prm + S::D3, dy, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da2d[o] = dh[o] * sigmoidf_fast(a2d[o]);
-    bwd_layer<kW, kW>(prm + S::D2, da2d, dh);
+    bwd_layer<kW, kW, kBF16>(prm + S::D2, da2d, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da1d[o] = dh[o] * sigmoidf_fast(a1d[o]);
-    bwd_layer<S::ID, kW>(prm + S::D1, da1d, ddin);
+    bwd_layer<S::ID, kW, kBF16>(prm + S::D1, da1d, ddin);
     float doe[2 * kL];
 #pragma unroll
     for (int l = 0; l < kL; ++l) {
@@ -159,10 +172,10 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
         doe[kL + l] = live ? dz * eps[l] * 0.5f * sd_e[l] + 0.5f * (sd_e[l] * sd_e[l] - 1.0f) * invB : 0.0f;
     }
     float da2e[kW], da1e[kW];
-    bwd_layer<kW, 2 * kL>(prm + S::E3, doe, dh);
+    bwd_layer<kW, 2 * kL, kBF16>(prm + S::E3, doe, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da2e[o] = dh[o] * sigmoidf_fast(a2e[o]);
-    bwd_layer<kW, kW>(prm + S::E2, da2e, dh);
+    bwd_layer<kW, kW, kBF16>(prm + S::E2, da2e, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da1e[o] = dh[o] * sigmoidf_fast(a1e[o]);
 
@@ -328,16 +341,16 @@ struct Plan {
                           float*, cudaStream_t) = nullptr;
 };
 
-template <int PI, int PO>
+template <int PI, int PO, bool kBF16>
 cudaError_t launch_fb(const float* prm, const float* X, const float* C, const float* E, uint64_t B, uint64_t seed,
                       uint64_t step, float* partial, cudaStream_t s)
 {
     using S = Shape<PI, PO>;
     const size_t smem = (size_t)S::NSLOT * kSamples * S::R * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO, kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned nblk = (unsigned)((B + kSamples - 1) / kSamples);
-    fwd_bwd<PI, PO><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
+    fwd_bwd<PI, PO, kBF16><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
     return cudaGetLastError();
 }
 
@@ -350,7 +363,7 @@ Plan plan_for(const ms_cvae_shape& sh)
 #define MS_CASE(pi, po)                                                                                        \
     if (sh.p_in == pi && sh.p_out == po) {                                                                    \
         pl.np = Shape<pi, po>::NP;                                                                            \
-        pl.launch = launch_fb<pi, po>;                                                                        \
+        pl.launch = sh.precision == MS_BF16 ? launch_fb<pi, po, true> : launch_fb<pi, po, false>;           \
     }
     MS_TRAIN_SHAPES(MS_CASE)
 #undef MS_CASE
@@ -384,8 +397,8 @@ extern "C" size_t ms_cvae_workspace_size(const ms_cvae_shape* s, uint64_t batch)
 static ms_status check_shape(const ms_cvae_shape* s, const char* fn, Plan* out)
 {
     if (!s) return ms::set_error(MS_ERR_INVALID_ARG, "%s: null shape", fn);
-    if (s->precision != MS_FP32)
-        return ms::set_error(MS_ERR_UNSUPPORTED, "%s: only MS_FP32 training is built", fn);
+    if (s->precision != MS_FP32 && s->precision != MS_BF16)
+        return ms::set_error(MS_ERR_UNSUPPORTED, "%s: training precision must be MS_FP32 or MS_BF16", fn);
     *out = plan_for(*s);
     if (!out->launch)
         return ms::set_error(MS_ERR_UNSUPPORTED,

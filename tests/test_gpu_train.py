@@ -160,3 +160,21 @@ def test_device_step_training_matches_oracle_and_replays_in_a_graph(orc):
     direct, replayed = run(False), run(True)
     assert np.array_equal(direct, replayed)
     assert np.abs(direct - ref).max() <= 2e-4 * max(1.0, np.abs(ref).max()), np.abs(direct - ref).max()
+
+
+@pytest.mark.parametrize("p_in,p_out", [(3, 3), (7, 6)])
+def test_bf16_training_matches_oracle(p_in, p_out):
+    """BF16 numerics (weight matrices and layer inputs rounded to BF16, FP32 accumulation and master weights)
+    against the oracle with the same rounding: loss and gradient within 2e-2 of the largest component."""
+    B = 4096
+    p, x, c, e = _data(p_in, p_out, B, 12)
+    shape = ms.cvae_shape(p_in, p_out, precision=ms.MS_BF16)
+    grad = torch.zeros(p.size, device="cuda")
+    loss3 = torch.zeros(3, device="cuda")
+    ms.ms_cvae_forward_backward(shape, _dev(p), _dev(x), _dev(c), B, eps_z=_dev(e), grad=grad, loss3=loss3)
+    torch.cuda.synchronize()
+    loss, rec, kl, g = cvae.neg_elbo_grad(p.astype(np.float64), cvae.Shape(p_in, p_out), x, c, e, bf16=True)
+    assert np.allclose(loss3.cpu().numpy(), [loss, rec, kl], rtol=2e-3, atol=2e-3)
+    assert np.abs(grad.cpu().numpy() - g).max() <= 2e-2 * np.abs(g).max()
+    _, _, _, g32 = cvae.neg_elbo_grad(p.astype(np.float64), cvae.Shape(p_in, p_out), x, c, e)
+    assert np.abs(grad.cpu().numpy() - g).max() < np.abs(g32 - g).max()   # closer to its own precision

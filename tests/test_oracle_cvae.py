@@ -140,3 +140,49 @@ def test_training_targets_invert_eq4():
     Nb = np.floor(np.exp(t["xL"][:, 0]) + 0.5)
     assert np.array_equal(Nb, N) and np.allclose(t["cP"][:, 2], np.log(N))
     assert np.allclose(t["cE"][:, 3:6], t["xP"])
+
+
+def test_bf16_rounding_and_variant():
+    """round_bf16 is round-to-nearest-even (checked against torch's bfloat16 cast); the BF16 variant's loss and
+    analytic gradient equal torch autograd through a float64 CVAE that rounds the same tensors with a
+    straight-through cast (value rounded, derivative 1); and it differs from the FP64 gradient by a
+    BF16-sized amount."""
+    rng = np.random.default_rng(9)
+    a = rng.standard_normal(10000) * 10 ** rng.uniform(-3, 3, 10000)
+    ref = torch.tensor(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cvae.round_bf16(a), ref)
+    shape = cvae.Shape(3, 3)
+    p, x, c, eps = _batch(shape, 64, 10)
+    _, _, _, g32 = cvae.neg_elbo_grad(p, shape, x, c, eps)
+    loss16, _, _, g16 = cvae.neg_elbo_grad(p, shape, x, c, eps, bf16=True)
+    rel = np.abs(g16 - g32).max() / np.abs(g32).max()
+    assert 1e-5 < rel < 5e-2
+
+    F = torch.nn.functional
+    q = lambda t: t + (t.to(torch.float32).to(torch.bfloat16).to(torch.float64) - t).detach()
+    tp = torch.tensor(p, requires_grad=True)
+    sizes = shape.enc_sizes() + shape.dec_sizes()
+    parts, off = {}, 0
+    for name, shp in sizes:
+        n = int(np.prod(shp))
+        parts[name] = tp[off:off + n].reshape(shp)
+        off += n
+    T = lambda v: torch.tensor(v, dtype=torch.float64)
+
+    def net(P, k, inp):
+        h = F.softplus(F.linear(q(inp), q(P[k + "1"]), P[k.lower() + "1"]))
+        h = F.softplus(F.linear(q(h), q(P[k + "2"]), P[k.lower() + "2"]))
+        return F.linear(q(h), q(P[k + "3"]), P[k.lower() + "3"])
+
+    L, Po = shape.latent, shape.p_out
+    eo = net(parts, "E", torch.cat([T(x), T(c)], 1))
+    mu_e, lv_e = eo[:, :L], eo[:, L:]
+    z = mu_e + torch.exp(0.5 * lv_e) * T(eps)
+    do = net(parts, "D", torch.cat([T(c), z], 1))
+    nll = -torch.distributions.Normal(do[:, :Po], torch.exp(0.5 * do[:, Po:])).log_prob(T(x)).sum(1)
+    kl = torch.distributions.kl_divergence(torch.distributions.Normal(mu_e, torch.exp(0.5 * lv_e)),
+                                           torch.distributions.Normal(0.0, 1.0)).sum(1)
+    loss = (nll + kl).mean()
+    loss.backward()
+    assert abs(loss.item() - loss16) < 1e-12
+    assert np.allclose(tp.grad.numpy(), g16, rtol=1e-10, atol=1e-13)
