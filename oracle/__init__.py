@@ -92,6 +92,8 @@ def lib():
         L.om_scatter_dir.argtypes = [P, C.c_double, C.c_double, P]
         L.om_inside_length.argtypes = [C.c_double, C.c_double, P, P]
         L.om_inside_length.restype = C.c_double
+        L.om_ray_crossing.argtypes = [C.c_double, C.c_double, P, P, P]
+        L.om_ray_crossing.restype = C.c_int
         _lib = L
     return _lib
 
@@ -240,3 +242,13 @@ def inside_length(A, k, X, xl):
     X = np.ascontiguousarray(X, np.float64)
     xl = np.ascontiguousarray(xl, np.float64)
     return lib().om_inside_length(A, k, _ptr(X), _ptr(xl))
+
+
+def ray_crossing(A, k, p, w):
+    """First boundary crossing along p + t w of the displaced sphere: (status, t) with status 1 crossing,
+    0 escape (outside rays only), 2 step cap."""
+    p = np.ascontiguousarray(p, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    t = np.zeros(1)
+    r = lib().om_ray_crossing(A, k, _ptr(p), _ptr(w), _ptr(t))
+    return r, float(t[0])

@@ -89,6 +89,41 @@ static ov3 sdf_grad(const scene* S, ov3 p)
     return v3(p.x / n - ak * cx * sy * sz, p.y / n - ak * sx * cy * sz, p.z / n - ak * sx * sy * cz);
 }
 
+/*
+ * Ray queries of the synthetic scene (the paper traces rays against meshes; this scene is an SDF, and the
+ * march is sphere tracing, Hart 1996, with a step bound taken from the form of f).
+ * Along p + s w, write f = |p + s w| - R(p + s w) with R(q) = 1 + A sin(kx) sin(ky) sin(kz).  The gradient
+ * of sin(kx) sin(ky) sin(kz) has length at most k, so R changes by at most lam s with lam = A k, while the
+ * radial term |p + s w| is known exactly along the ray.  Hence, with R0 = R(p) = |p| - f(p):
+ *   outside (f > 0):  f(p + s w) >= |p + s w| - R0 - lam s, positive until |p + s w| = R0 + lam s;
+ *   inside  (f < 0):  f(p + s w) <= |p + s w| - R0 + lam s, negative until |p + s w| = R0 - lam s.
+ * Squaring either equation gives a s^2 + 2 B s + c = 0 with a = 1 - lam^2, c = |p|^2 - R0^2 = f (|p| + R0)
+ * and B = p.w -/+ R0 lam; the step is its first positive root, in whichever of the two algebraically equal
+ * forms has no cancellation for the sign of B.  Inside there is always exactly one positive root (B < 0 can
+ * only happen with lam < 1).  Outside, no positive root (no real root, or B >= 0 with lam <= 1) means the
+ * surface cannot be reached along the ray at all: the step is then INFINITY.
+ * Every such step is at least the Lipschitz step |f| / (1 + lam), and the callers take the larger of the two.
+ */
+static double safe_step(const scene* S, ov3 p, ov3 w, double f)
+{
+    double rp = sqrt(dot(p, p));
+    double lam = S->A * S->k;
+    double R0 = rp - f;
+    double a = 1.0 - lam * lam;
+    double c = f * (rp + R0);
+    if (f < 0.0) {
+        double B = dot(p, w) + R0 * lam;
+        double sq = sqrt(fmax(B * B - a * c, 0.0));
+        return B >= 0.0 ? -c / (B + sq) : (sq - B) / a;
+    }
+    double B = dot(p, w) - R0 * lam;
+    double disc = B * B - a * c;
+    if (disc < 0.0 || (B >= 0.0 && a >= 0.0))
+        return INFINITY;
+    double sq = sqrt(disc);
+    return B < 0.0 ? c / (sq - B) : (B + sq) / -a;
+}
+
 /* March inside the medium from p along w for at most l.  Returns 1 on a collision (*q = p + l w), 0 when
  * the boundary is crossed outward at *q, 2 when the step cap runs out. */
 static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
@@ -96,13 +131,16 @@ static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
     double t = 0.0;
     for (int it = 0; it < R_MAX_MARCH; ++it) {
         ov3 r = add(p, mul(w, t));
-        double d = -sdf(S, r) / S->lip;
+        double f = sdf(S, r);
+        double d = -f / S->lip;
         if (d < R_EPS) {
             if (dot(sdf_grad(S, r), w) > 0.0) {
                 *q = r;
                 return 0;
             }
             d = R_EPS;
+        } else {
+            d = fmax(d, safe_step(S, r, w, f));
         }
         if (t + d >= l) {
             *q = add(p, mul(w, l));
@@ -122,13 +160,19 @@ static int march_outside(const scene* S, ov3 p, ov3 w, ov3* q)
         ov3 r = add(p, mul(w, t));
         if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
             return 0;
-        double d = sdf(S, r) / S->lip;
+        double f = sdf(S, r);
+        double d = f / S->lip;
         if (d < R_EPS) {
             if (dot(sdf_grad(S, r), w) < 0.0) {
                 *q = r;
                 return 1;
             }
             d = R_EPS;
+        } else {
+            double h = safe_step(S, r, w, f);
+            if (h == INFINITY)
+                return 0;
+            d = fmax(d, h);
         }
         t = t + d;
     }
@@ -149,13 +193,16 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
             return din;
         ov3 r = add(X, mul(w, t));
         if (inside) {
-            double d = -sdf(S, r) / S->lip;
+            double f = sdf(S, r);
+            double d = -f / S->lip;
             if (d < R_EPS) {
                 if (dot(sdf_grad(S, r), w) > 0.0) {
                     inside = 0;
                     continue;
                 }
                 d = R_EPS;
+            } else {
+                d = fmax(d, safe_step(S, r, w, f));
             }
             double step = fmin(d, D - t);
             din = din + step;
@@ -163,13 +210,19 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
         } else {
             if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
                 return din;
-            double d = sdf(S, r) / S->lip;
+            double f = sdf(S, r);
+            double d = f / S->lip;
             if (d < R_EPS) {
                 if (dot(sdf_grad(S, r), w) < 0.0) {
                     inside = 1;
                     continue;
                 }
                 d = R_EPS;
+            } else {
+                double h = safe_step(S, r, w, f);
+                if (h == INFINITY)
+                    return din;
+                d = fmax(d, h);
             }
             t = t + fmin(d, D - t);
         }
@@ -496,6 +549,24 @@ int om_render(const om_render_params* P, const om_decoder* dec3, double* image, 
 void om_decoder_sample(const om_decoder* D, const double* c, const double* z, const double* eps, double* x)
 {
     decoder_sample(D, c, z, eps, x);
+}
+
+/* First boundary crossing along p + t w, exposed for the tests: from outside (f(p) > 0) the re-entry
+ * march, from inside the exit march with no collision.  Returns 1 with *t at the crossing, 0 when an
+ * outside ray escapes, 2 when the step cap runs out. */
+int om_ray_crossing(double A, double k, const double* p, const double* w, double* t)
+{
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    ov3 o = v3(p[0], p[1], p[2]), d = v3(w[0], w[1], w[2]), q = o;
+    int r;
+    if (sdf(&S, o) > 0.0) {
+        r = march_outside(&S, o, d, &q);
+    } else {
+        r = march_inside(&S, o, d, INFINITY, &q);
+        r = r == 0 ? 1 : 2;
+    }
+    *t = sqrt(dot(sub(q, o), sub(q, o)));
+    return r;
 }
 
 /* Inside length of one segment, exposed for the tests. */

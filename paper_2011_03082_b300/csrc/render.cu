@@ -86,12 +86,42 @@ struct Geo {
     float A, k, inv_lip, rb2;
 };
 
-// ---- the displaced sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz) (negative inside) ----
-__device__ __forceinline__ float sdf(const Geo& q, V p)
+// ---- the displaced sphere f(p) = |p| - R(p), R(p) = 1 + A sin(kx) sin(ky) sin(kz) (negative inside) ----
+__device__ __forceinline__ float sdf_parts(const Geo& q, V p, float* rp, float* R0)
 {
     const float d2 = dot(p, p);
-    const float r = d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f;
-    return r - 1.0f - q.A * __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z);
+    *rp = d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f;
+    *R0 = fmaf(q.A, __sinf(q.k * p.x) * __sinf(q.k * p.y) * __sinf(q.k * p.z), 1.0f);
+    return *rp - *R0;
+}
+
+__device__ __forceinline__ float sdf(const Geo& q, V p)
+{
+    float rp, R0;
+    return sdf_parts(q, p, &rp, &R0);
+}
+
+// Step along w from p that cannot cross the surface: the displacement A sin sin sin is (A k)-Lipschitz and
+// the radial term |p + s w| is exact along the ray, so with lam = A k and R0 = R(p) the surface is not
+// reached before |p + s w| = R0 + lam s (outside) or R0 - lam s (inside).  Squared, that is
+// a s^2 + 2 B s + c = 0 with a = 1 - lam^2, B = p.w -/+ R0 lam, c = |p|^2 - R0^2 = f (|p| + R0); the step is
+// its first positive root, in the form without cancellation for the sign of B.  Outside, no positive root
+// means the surface cannot be reached along the ray at all (*escape).
+__device__ __forceinline__ float safe_step(const Geo& q, V p, V w, float rp, float R0, float f, bool in_medium,
+                                           bool* escape)
+{
+    const float lam = q.A * q.k;
+    const float a = fmaf(-lam, lam, 1.0f);
+    const float c = f * (rp + R0);
+    const float B = dot(p, w) + (in_medium ? R0 * lam : -R0 * lam);
+    const float disc = fmaf(B, B, -a * c);
+    const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
+    const bool pos = B >= 0.0f;
+    // inside: B >= 0 ? -c / (B + sq) : (sq - B) / a;   outside: B < 0 ? c / (sq - B) : (B + sq) / -a
+    const float num = in_medium ? (pos ? -c : sq - B) : (pos ? B + sq : c);
+    const float den = in_medium ? (pos ? B + sq : a) : (pos ? -a : sq - B);
+    *escape = !in_medium && (disc < 0.0f || (pos && a >= 0.0f));
+    return __fdividef(num, den);
 }
 
 __device__ __forceinline__ V sdf_grad(const Geo& q, V p)
@@ -467,15 +497,23 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 st = kPending;
                 continue;
             }
-            const float f = sdf(geo, r);
+            float rp, R0;
+            const float f = sdf_parts(geo, r, &rp, &R0);
             cnt[8] += 1u;
             float d = (in_medium ? -f : f) * geo.inv_lip;
-            bool crossing = false;
+            bool crossing = false, escape = false;
             if (d < kEps) {
                 cnt[9] += 1u;
                 const float gd = dot(sdf_grad(geo, r), md);
                 crossing = in_medium ? gd > 0.0f : gd < 0.0f;
                 d = kEps;
+            } else {
+                d = fmaxf(d, safe_step(geo, r, md, rp, R0, f, in_medium, &escape));
+            }
+            if (escape) {                                    // the surface is out of reach along the ray
+                ev = shadow ? kEvShadowDone : kEvEscape;
+                st = kPending;
+                continue;
             }
             if (crossing) {
                 if (shadow) {

@@ -19,10 +19,13 @@ def test_inside_length_undisplaced_sphere_is_the_chord(orc):
         assert abs(orc.inside_length(0.0, 6.0, X, xl) - chord) < 2e-4
 
 
-def test_inside_length_displaced_sphere_against_dense_sampling(orc):
-    A, k = 0.1, 6.0
+@pytest.mark.parametrize("A,k", [(0.1, 6.0), (0.1, 10.0), (0.15, 10.0)])
+def test_inside_length_displaced_sphere_against_dense_sampling(orc, A, k):
+    """Inside length of a segment against dense sampling of f.  A march stops where |f| / (1 + A k) < 1e-4,
+    which at a grazing crossing (|df/dt| small) lies up to about 2e-4 / |df/dt| from the crossing, so segments
+    with a crossing slope below 0.2 are skipped."""
     rng = np.random.default_rng(1)
-    f = lambda p: np.linalg.norm(p, axis=-1) - 1 - A * np.sin(k * p[..., 0]) * np.sin(k * p[..., 1]) * np.sin(k * p[..., 2])
+    f = _disp_sdf(A, k)
     checked = 0
     for _ in range(60):
         X = rng.uniform(-0.8, 0.8, 3)
@@ -30,12 +33,65 @@ def test_inside_length_displaced_sphere_against_dense_sampling(orc):
             continue
         xl = rng.uniform(-3, 3, 3) * np.array([1, 1, 0]) + np.array([0, 0, 3.0])
         t = np.linspace(0, 1, 400001)
-        pts = X + t[:, None] * (xl - X)
-        inside = f(pts) < 0
-        ref = inside[:-1].mean() * np.linalg.norm(xl - X)
+        D = np.linalg.norm(xl - X)
+        fv = f(X + t[:, None] * (xl - X))
+        inside = fv < 0
+        ch = np.nonzero(inside[1:] != inside[:-1])[0]
+        if np.any(np.abs(fv[ch + 1] - fv[ch]) / ((t[1] - t[0]) * D) < 0.2):
+            continue
+        ref = inside[:-1].mean() * D
         assert abs(orc.inside_length(A, k, X, xl) - ref) < 1e-3
         checked += 1
     assert checked > 20
+
+
+def _disp_sdf(A, k):
+    return lambda p: (np.linalg.norm(p, axis=-1) - 1
+                      - A * np.sin(k * p[..., 0]) * np.sin(k * p[..., 1]) * np.sin(k * p[..., 2]))
+
+
+@pytest.mark.parametrize("A,k", [(0.1, 2.0), (0.1, 6.0), (0.1, 10.0), (0.3, 4.0), (0.15, 10.0)])
+def test_ray_crossing_against_dense_sampling(orc, A, k):
+    """The march (sphere tracing with the radial-plus-Lipschitz step, including its early escape) finds the
+    first sign change of f along the ray, found here by sampling f every 4e-5 (A k from 0.2 to 1.5, so the
+    step's quadratic has positive, zero and negative leading coefficient).  Grazing crossings and near misses,
+    which sampling cannot resolve, are skipped."""
+    f = _disp_sdf(A, k)
+    rng = np.random.default_rng(int(100 * A + k))
+    t = np.linspace(0.0, 8.0, 200001)
+    dt = t[1] - t[0]
+    n_hit = n_escape = n_inside = 0
+    for _ in range(150):
+        if rng.random() < 0.6:          # from outside, aimed near the object
+            p = rng.standard_normal(3)
+            p *= rng.uniform(1.25, 3.0) / np.linalg.norm(p)
+            w = rng.uniform(-1.3, 1.3, 3) - p
+        else:                           # from inside
+            p = rng.uniform(-0.85, 0.85, 3)
+            if f(p) > -0.01:
+                continue
+            w = rng.standard_normal(3)
+        w /= np.linalg.norm(w)
+        fv = f(p + t[:, None] * w)
+        outside = fv[0] > 0
+        change = np.nonzero((fv[1:] > 0) != outside)[0]
+        status, tc = orc.ray_crossing(A, k, p, w)
+        if change.size == 0:
+            if np.min(np.abs(fv)) < 2e-3:
+                continue                # near miss
+            assert outside and status == 0, (p, w, status)
+            n_escape += 1
+            continue
+        i = change[0]
+        slope = abs(fv[i + 1] - fv[i]) / dt
+        if slope < 0.05 or (outside and np.min(fv[:i + 1]) < 2e-3 and np.argmin(fv[:i + 1]) < i - 50):
+            continue                    # grazing crossing, or a near miss before the crossing
+        assert status == 1, (p, w, status)
+        # the march stops where |f| / (1 + A k) < 1e-4, i.e. up to (1 + A k) 1e-4 / slope before the crossing
+        assert abs(tc - t[i]) < 1.2 * (1 + A * k) * 1e-4 / slope + 2 * dt, (p, w, tc, t[i])
+        n_inside += not outside
+        n_hit += outside
+    assert n_hit > 15 and n_escape > 5 and n_inside > 15, (n_hit, n_escape, n_inside)
 
 
 def _render(orc, **kw):
