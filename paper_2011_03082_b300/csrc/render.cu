@@ -198,7 +198,9 @@ constexpr int kUsedStats = 10;
 enum State : int { kIdle = 0, kCamera, kFlight, kReentry, kShadow, kDecode, kPending };
 enum Event : int { kEvHit = 0, kEvReenter, kEvEscape, kEvCap, kEvExit, kEvCollide, kEvShadowDone };
 
-template <int kDecodeBatch, int kTransBatch, int kSteps, int kMinBlocks>
+// kLearned: the launch holds at least one sphere-tracing request (decoder weights present); the brute-force
+// instantiation carries no decoder code, which leaves its march and transitions free of register spills.
+template <int kDecodeBatch, int kTransBatch, int kSteps, int kMinBlocks, bool kLearned>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __grid_constant__ Batch B)
 {
     constexpr int kRefillBatch = kTransBatch;
@@ -206,12 +208,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     __shared__ float s_stage[kThreads / 32][mmadec::kStageFloats];
     __shared__ unsigned long long s_stats[kMaxReq * kStats];
     const int tid = threadIdx.x, lane = tid & 31;
-    const bool learned = B.wL != nullptr;
+    constexpr bool learned = kLearned;
     unsigned char* wl = sw;
     unsigned char* wpth = sw + kBytesL;
     unsigned char* wev = sw + kBytesL + kBytesP;
     float* stage = s_stage[tid >> 5];
-    if (learned) {
+    if constexpr (learned) {
         mmadec::stage_weights<false>(wl, B.wL, 2 + 4, 1);
         mmadec::stage_weights<false>(wpth, B.wP, 3 + 4, 3);
         mmadec::stage_weights<false>(wev, B.wE, 7 + 4, 6);
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         if (!parked && !pending && !marching) break;   // drained and no lane holds a path
         const int n_active = __popc(marching);
 
-        if (parked && (__popc(parked) >= kDecodeBatch || n_active + __popc(pending) < kDecodeBatch)) {
+        if (learned && parked && (__popc(parked) >= kDecodeBatch || n_active + __popc(pending) < kDecodeBatch)) {
             // ================= decoder round: the three learned samplers for the parked lanes =================
             // The MLPs run on the tensor cores for all 32 rows of the warp (a lane that is not parked feeds
             // zeros and ignores its outputs); everything per path stays in the lane's registers.
@@ -567,11 +569,15 @@ using namespace ms::render;
 
 // Compiled kernel variants (scheduling constants); index 0 is the default.
 struct Variant {
-    const void* fn;
+    const void* fn;          // with the decoders (any sphere-tracing request)
+    const void* fn_brute;    // brute force only
     int decode_batch, trans_batch, steps, min_blocks;
 };
 template <int D, int T, int S, int M>
-Variant make_variant() { return Variant{(const void*)render_kernel<D, T, S, M>, D, T, S, M}; }
+Variant make_variant()
+{
+    return Variant{(const void*)render_kernel<D, T, S, M, true>, (const void*)render_kernel<D, T, S, M, false>, D, T, S, M};
+}
 static const Variant kVariants[] = {
     make_variant<20, 12, 8, 3>(), make_variant<16, 8, 1, 2>(), make_variant<16, 8, 4, 2>(),
     make_variant<16, 8, 8, 3>(), make_variant<20, 12, 16, 3>(), make_variant<24, 16, 8, 3>(),
@@ -681,13 +687,14 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     MS_CUDA(cudaMemsetAsync(workspace, 0, (2 + kMaxReq) * sizeof(unsigned long long), s));
     MS_CUDA(cudaMemsetAsync(b.t_start, 0xff, sizeof(unsigned long long), s));
     const Variant& v = kVariants[reqs[0].variant];
+    const void* kfn = any_sphere ? v.fn : v.fn_brute;
     int per_sm = 0;
-    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, kThreads, 0));
+    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, 0));
     uint64_t grid = (uint64_t)ms::num_sms() * (per_sm > 0 ? per_sm : 1);
     const uint64_t need = (b.total + kThreads - 1) / kThreads;
     if (grid > need) grid = need;
     void* args[] = {&b};
-    MS_CUDA(cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(kThreads), args, 0, s));
+    MS_CUDA(cudaLaunchKernel(kfn, dim3((unsigned)grid), dim3(kThreads), args, 0, s));
     return MS_OK;
 }
 
