@@ -105,6 +105,21 @@ def measured_peaks():
     return {}
 
 
+def recorded_traffic(variant: dict):
+    """DRAM bytes per launch of the render kernel from the committed one-pass ncu capture of the benchmark
+    launch, or None when the kernel sources or the selected variant differ from those it was taken on."""
+    import hashlib
+    rec = json.loads((ROOT / "paper_2011_03082_b300" / "measured_traffic.json").read_text())["render_kernel"]
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        h.update((ROOT / f).read_bytes())
+    want = {k: rec["variant"][k] for k in ("decode_batch", "trans_batch", "steps", "min_blocks")}
+    got = {k: variant.get(k) for k in want}
+    if h.hexdigest() != rec["sha256"] or got != want:
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
 # --------------------------------------------------------------------------------------------- CPU oracle
 
 def oracle_paths_per_second(models_np, budget_s: float, sigmas=SIGMAS, mode=1):
@@ -272,7 +287,9 @@ def main(argv=None):
                 + st[7] * MUFU_PER_NEE + st[2] * 2)
     achieved = mufu_ops / (t_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
-                "frac": achieved / mufu_peak, "traffic": None, "kernel": "render_kernel",
+                "frac": achieved / mufu_peak, "traffic": recorded_traffic(ms.ms_render_variant_info(variant)),
+                "traffic_unit": "DRAM bytes per launch (committed ncu capture; null if the kernel changed)",
+                "kernel": "render_kernel",
                 "peak_source": f"{n_sm} SMs x 16 MUFU ops/clk x {sm_mhz_max:.0f} MHz (recipe unit counts, max clock)"}
 
     # ---------------- end to end through the C ABI with host buffers ----------------
