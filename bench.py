@@ -295,7 +295,7 @@ def main(argv=None):
     # ---------------- end to end through the C ABI with host buffers ----------------
     host_w = {k: (torch.from_numpy(pipeline.decoder_part(k, models[k]["params"])).pin_memory(), *synth.MODEL_SHAPES[k])
               for k in pipeline.MODELS}
-    dev_w = {k: (torch.empty_like(v[0], device=dev), v[1], v[2]) for k, v in host_w.items()}
+    dev_w = {k: (torch.empty_like(v[0], device=dev), *v[1:]) for k, v in host_w.items()}
     cset_e2e = ms.cvae_set(dev_w)
     host_img = torch.empty(npx, dtype=torch.float64).pin_memory()
     host_stats = torch.empty_like(stats, device="cpu").pin_memory()

@@ -118,7 +118,7 @@ ms_status ms_simulate_walks(const ms_walk_params* p, const ms_walk_out* out, voi
 typedef struct {
     int32_t p_in;               /* condition size, 1..12                                               */
     int32_t latent;             /* latent size L, 1..8 (p_in + latent <= 16)                          */
-    int32_t width;              /* hidden width W, must be 16                                          */
+    int32_t width;              /* hidden width W, 8 or 16                                             */
     int32_t p_out;              /* output size P, 1..8                                                 */
     int32_t precision;          /* MS_FP32 (FP32 FMA), or MS_FP16 / MS_BF16: tensor cores, weights rounded
                                    to FP16 / BF16, activations carried as two halves, FP32 accumulation */
@@ -141,7 +141,10 @@ ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const float* z_e
  * ms_decoder.weights).  The optimiser is Adam (AdamW with weight_decay > 0), as in Sec. 3.2.
  * ---------------------------------------------------------------------------------------------------- */
 typedef struct {
-    int32_t p_in, p_out, latent, width;   /* width must be 16; p_in + latent <= 16; p_out + p_in <= 16 */
+    int32_t p_in, p_out, latent, width;   /* a compiled shape: (p_in, p_out) in {(1,1) (2,1) (3,3) (4,1)
+                                             (4,3) (4,6) (7,6)} with latent 4, width 16, or the Table 1
+                                             shapes (2,1) latent 2 width 8, (3,3) and (7,6) latent 5
+                                             width 16; MS_ERR_UNSUPPORTED otherwise                    */
     int32_t precision;                    /* MS_FP32 (BF16 compute with FP32 master weights: MS_BF16)   */
 } ms_cvae_shape;
 
@@ -210,7 +213,9 @@ ms_status ms_training_records(uint64_t n, const int32_t* n_events, const float* 
 /* ------------------------------------------------------------------------------------------------------
  * Rendering a homogeneous translucent SDF object with a point light (Sec. 3, Fig. 2b; Sec. 4.1; Sec. 4.3,
  * Eq. 5).  The object is the displaced unit sphere f(p) = |p| - 1 - A sin(k x) sin(k y) sin(k z) (negative
- * inside); |f| / (1 + A k) is a conservative distance.  The boundary is index matched (no refraction, as in
+ * inside); |f| / (1 + A k) is a conservative distance.  Rays are sphere traced with the larger of that step
+ * and the first root of |p + s w| = R(p) +/- A k s (the radial term followed exactly, the displacement
+ * bounded), which also detects when the surface is out of reach.  The boundary is index matched (no refraction, as in
  * the paper's unrefracted NEE).  Camera paths enter the object; after each free flight to a collision:
  *   MS_SPHERE: if sigma_t * r >= min_optical_radius with r = min(distance bound, max_optical_radius /
  *     sigma_t), one sphere step: LengthGen -> N, PathGen -> exit (Eq. 4), EventGen -> (X, W), NEE at X with
@@ -236,6 +241,10 @@ typedef struct {
     int32_t reserved_;
 } ms_render_params;
 
+/* The renderer's three decoders have the final shapes of Table 1 (the paper's D = 2 hidden layers):
+ * LengthGen latent 2 width 8, PathGen latent 5 width 16, EventGen latent 5 width 16, all MS_FP32.  A sphere
+ * step draws 22 normals n[0..21] (tags 2..7 of its segment, four per tag by Box-Muller): LengthGen z = n[0,1],
+ * eps = n[2]; PathGen z = n[3..7], eps = n[8..10]; EventGen z = n[11..15], eps = n[16..21]. */
 typedef struct {
     ms_decoder length;          /* LengthGen: p_in 2 (ln tau, g), p_out 1 (ln N dequantised)             */
     ms_decoder path;            /* PathGen:   p_in 3 (ln tau, g, ln N), p_out 3 (cos theta, alpha, beta) */

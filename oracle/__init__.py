@@ -207,8 +207,9 @@ def _decoder_struct(wvec, p_in, p_out, latent=4, width=16):
 
 
 def render(params: dict, decoders=None, n_threads=0):
-    """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out)
-    for LengthGen, PathGen, EventGen.  Returns (image_sum[h][w], stats[16], threads)."""
+    """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out) or
+    (weights, p_in, p_out, latent, width) for LengthGen, PathGen, EventGen (latent 4, width 16 when not given).
+    Returns (image_sum[h][w], stats[16], threads)."""
     P = RenderParams()
     for k, v in params.items():
         if isinstance(getattr(P, k), C.Array):
@@ -218,13 +219,15 @@ def render(params: dict, decoders=None, n_threads=0):
     keep = []
     decs = (Decoder * 3)()
     if decoders is not None:
-        for i, (w, p_in, p_out) in enumerate(decoders):
-            d, arr = _decoder_struct(w, p_in, p_out)
+        for i, dd in enumerate(decoders):
+            d, arr = _decoder_struct(*dd)
             decs[i] = d
             keep.append(arr)
     image = np.zeros((P.height, P.width), np.float64)
     stats = np.zeros(16, np.uint64)
     nt = lib().om_render(C.byref(P), C.cast(decs, C.c_void_p), _ptr(image), _ptr(stats), n_threads)
+    if nt < 0:
+        raise ValueError("om_render: the decoders need more than 24 normals per sphere step, or are too wide")
     return image, stats, nt
 
 

@@ -19,7 +19,8 @@
  * Per path (pixel index -> counter id_hi, sample index -> id_lo) and segment step s (counter word 0):
  *   tag 0: u0 free path, u1 HG cosine, u2 HG azimuth, u3 roulette
  *   tag 1: u0 absorption test, u1 rotation angle psi
- *   tags 2..7: Box-Muller normals n[0..23], tag t words (w0,w1) -> n[4(t-2)], n[4(t-2)+1], (w2,w3) -> next two
+ *   tags 2..7: Box-Muller normals n[0..23], tag t words (w0,w1) -> n[4(t-2)], n[4(t-2)+1], (w2,w3) -> next two;
+ *       used in order: LengthGen z then eps, PathGen z then eps, EventGen z then eps
  *   tag 8 at step 0: pixel jitter.
  * Uniforms are (w >> 8) * 2^-24 (24-bit), identical to the single-precision kernels' stream.
  */
@@ -415,15 +416,20 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                 words(&rs, seg, 1u, a4);
                 double n[24];
                 normals(&rs, seg, n);
+                /* the normals are used in order: each model's z (its latent size), then its eps (its output
+                 * size) — LengthGen, PathGen, EventGen */
+                const om_decoder* D = J->dec;
+                int zL = 0, eL = zL + D[0].latent, zP = eL + D[0].p_out, eP = zP + D[1].latent;
+                int zE = eP + D[1].p_out, eE = zE + D[2].latent;
                 double ltau = log(tau);
                 double cL[2] = { ltau, g }, yN;
-                decoder_sample(&J->dec[0], cL, n + 0, n + 4, &yN);
+                decoder_sample(&D[0], cL, n + zL, n + eL, &yN);
                 double N = floor(exp(yN) + 0.5);
                 if (!(N >= 1.0)) N = 1.0;
                 if (N > R_N_MAX) N = R_N_MAX;
                 double lnN = log(N);
                 double cP[3] = { ltau, g, lnN }, xp[3];
-                decoder_sample(&J->dec[1], cP, n + 5, n + 9, xp);
+                decoder_sample(&D[1], cP, n + zP, n + eP, xp);
                 double ct = fmin(1.0, fmax(-1.0, xp[0])), al = xp[1], be = xp[2];
                 double ab2 = al * al + be * be;
                 if (ab2 > 1.0) {
@@ -431,7 +437,7 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                     al = al * s; be = be * s; ab2 = 1.0;
                 }
                 double cE[7] = { ltau, g, phi, ct, al, be, lnN }, xe[6];
-                decoder_sample(&J->dec[2], cE, n + 12, n + 16, xe);
+                decoder_sample(&D[2], cE, n + zE, n + eE, xe);
                 double phiN = pow(phi, N);
                 double lam = (phi < 1.0) ? phi * (1.0 - phiN) / (1.0 - phi) : N;
 
@@ -526,6 +532,14 @@ static void* render_worker(void* arg)
  */
 int om_render(const om_render_params* P, const om_decoder* dec3, double* image, uint64_t* stats, int n_threads)
 {
+    if (P->mode == 1 && dec3) {
+        int used = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (dec3[k].width > 64 || dec3[k].p_in + dec3[k].latent > 64) return -1;
+            used += dec3[k].latent + dec3[k].p_out;
+        }
+        if (used > 24) return -1;   /* a sphere step draws 24 normals */
+    }
     render_job J;
     J.P = P;
     J.dec = dec3;

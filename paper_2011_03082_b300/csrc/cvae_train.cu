@@ -26,12 +26,12 @@
 namespace ms {
 namespace train {
 
-constexpr int kW = 16;
-constexpr int kL = 4;
 constexpr int kSamples = 128;
 
-template <int PI, int PO>
+// Hidden width kW and latent size kL are shape parameters (Table 1 uses W 8 or 16, L 2 or 5).
+template <int PI, int PO, int kW, int kL>
 struct Shape {
+    static constexpr int W = kW, L = kL;
     static constexpr int IE = PO + PI;                // encoder input
     static constexpr int ID = PI + kL;                // decoder input
     // packed parameter offsets: encoder E1 e1 E2 e2 E3 e3, then decoder D1 d1 D2 d2 D3 d3
@@ -78,13 +78,13 @@ __device__ __forceinline__ void bwd_layer(const float* __restrict__ Wm, const fl
         for (int k = 0; k < K; ++k) dx[k] = fmaf(rq<kBF16>(__ldg(Wm + o * K + k)), da[o], dx[k]);
 }
 
-template <int PI, int PO, bool kBF16>
+template <int PI, int PO, int kW, int kL, bool kBF16>
 __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ prm, const float* __restrict__ X,
                                                     const float* __restrict__ Cc, const float* __restrict__ EPS,
                                                     uint64_t B, uint64_t seed, uint64_t step,
                                                     float* __restrict__ partial)
 {
-    using S = Shape<PI, PO>;
+    using S = Shape<PI, PO, kW, kL>;
     extern __shared__ float sm[];
     const int t = threadIdx.x;
     const uint64_t b = (uint64_t)blockIdx.x * kSamples + t;
@@ -108,10 +108,17 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
 #pragma unroll
         for (int l = 0; l < kL; ++l) eps[l] = live ? EPS[b * kL + l] : 0.0f;
     } else {
+        // normals 4j..4j+3 from counter (j, b, step, 0xE0)
         const Stream st(seed, (step << 32) | (b & 0xffffffffull));
-        const Words w = st.at(0u, 0xE0u);
-        const float2 p0 = box_muller(w.w0, w.w1), p1 = box_muller(w.w2, w.w3);
-        eps[0] = p0.x; eps[1] = p0.y; eps[2] = p1.x; eps[3] = p1.y;
+#pragma unroll
+        for (int j = 0; 4 * j < kL; ++j) {
+            const Words w = st.at((uint32_t)j, 0xE0u);
+            const float2 p0 = box_muller(w.w0, w.w1), p1 = box_muller(w.w2, w.w3);
+            const float v[4] = {p0.x, p0.y, p1.x, p1.y};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (4 * j + i < kL) eps[4 * j + i] = v[i];
+        }
     }
     float a1e[kW], h1e[kW], a2e[kW], h2e[kW], oe[2 * kL];
     fwd_layer<S::IE, kW, kBF16>(prm + S::E1, prm + S::e1, xin, a1e);
@@ -293,8 +300,9 @@ __global__ void adam(float* __restrict__ p, float* __restrict__ m, float* __rest
 // Mini-batch b of step t: record index mulhi(w, n) with w word 0 of counter (t, b, 0, 0xB0) (uniform, with
 // replacement), and the latent normals of counter (0, b, t, 0xE0) (the same as the host-step path).
 __global__ void gather_batch(const float* __restrict__ x_all, const float* __restrict__ c_all, uint64_t n, int p_out,
-                             int p_in, uint64_t B, uint64_t seed, const unsigned long long* __restrict__ step,
-                             float* __restrict__ xb, float* __restrict__ cb, float* __restrict__ eps)
+                             int p_in, int latent, uint64_t B, uint64_t seed,
+                             const unsigned long long* __restrict__ step, float* __restrict__ xb,
+                             float* __restrict__ cb, float* __restrict__ eps)
 {
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -305,9 +313,12 @@ __global__ void gather_batch(const float* __restrict__ x_all, const float* __res
     for (int j = 0; j < p_out; ++j) xb[b * p_out + j] = x_all[i * p_out + j];
     for (int j = 0; j < p_in; ++j) cb[b * p_in + j] = c_all[i * p_in + j];
     const Stream st(seed, (t << 32) | (b & 0xffffffffull));
-    const Words e = st.at(0u, 0xE0u);
-    const float2 p0 = box_muller(e.w0, e.w1), p1 = box_muller(e.w2, e.w3);
-    eps[b * kL] = p0.x; eps[b * kL + 1] = p0.y; eps[b * kL + 2] = p1.x; eps[b * kL + 3] = p1.y;
+    for (int j = 0; 4 * j < latent; ++j) {
+        const Words e = st.at((uint32_t)j, 0xE0u);
+        const float2 p0 = box_muller(e.w0, e.w1), p1 = box_muller(e.w2, e.w3);
+        const float v[4] = {p0.x, p0.y, p1.x, p1.y};
+        for (int i = 0; i < 4 && 4 * j + i < latent; ++i) eps[b * latent + 4 * j + i] = v[i];
+    }
 }
 
 // Adam with the step t read from device memory (bias corrections computed here).
@@ -341,29 +352,33 @@ struct Plan {
                           float*, cudaStream_t) = nullptr;
 };
 
-template <int PI, int PO, bool kBF16>
+template <int PI, int PO, int W, int L, bool kBF16>
 cudaError_t launch_fb(const float* prm, const float* X, const float* C, const float* E, uint64_t B, uint64_t seed,
                       uint64_t step, float* partial, cudaStream_t s)
 {
-    using S = Shape<PI, PO>;
+    using S = Shape<PI, PO, W, L>;
     const size_t smem = (size_t)S::NSLOT * kSamples * S::R * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO, kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO, W, L, kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned nblk = (unsigned)((B + kSamples - 1) / kSamples);
-    fwd_bwd<PI, PO, kBF16><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
+    fwd_bwd<PI, PO, W, L, kBF16><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
     return cudaGetLastError();
 }
 
-#define MS_TRAIN_SHAPES(X) X(1, 1) X(2, 1) X(3, 3) X(4, 1) X(4, 3) X(4, 6) X(7, 6)
+// Compiled shapes (p_in, p_out, width, latent): the uniform width-16 / latent-4 set, and the final Table 1
+// shapes of LengthGen, PathGen and EventGen.
+#define MS_TRAIN_SHAPES(X)                                                                                    \
+    X(1, 1, 16, 4) X(2, 1, 16, 4) X(3, 3, 16, 4) X(4, 1, 16, 4) X(4, 3, 16, 4) X(4, 6, 16, 4) X(7, 6, 16, 4)   \
+    X(2, 1, 8, 2) X(3, 3, 16, 5) X(7, 6, 16, 5)
 
 Plan plan_for(const ms_cvae_shape& sh)
 {
     Plan pl;
-    if (sh.latent != kL || sh.width != kW) return pl;
-#define MS_CASE(pi, po)                                                                                        \
-    if (sh.p_in == pi && sh.p_out == po) {                                                                    \
-        pl.np = Shape<pi, po>::NP;                                                                            \
-        pl.launch = sh.precision == MS_BF16 ? launch_fb<pi, po, true> : launch_fb<pi, po, false>;           \
+#define MS_CASE(pi, po, w, l)                                                                                  \
+    if (sh.p_in == pi && sh.p_out == po && sh.width == w && sh.latent == l) {                                 \
+        pl.np = Shape<pi, po, w, l>::NP;                                                                      \
+        pl.launch = sh.precision == MS_BF16 ? launch_fb<pi, po, w, l, true> : launch_fb<pi, po, w, l, false>; \
     }
     MS_TRAIN_SHAPES(MS_CASE)
 #undef MS_CASE
@@ -403,7 +418,8 @@ static ms_status check_shape(const ms_cvae_shape* s, const char* fn, Plan* out)
     if (!out->launch)
         return ms::set_error(MS_ERR_UNSUPPORTED,
                              "%s: shape (p_in %d, p_out %d, latent %d, width %d) is not built; built: latent 4, "
-                             "width 16, (p_in, p_out) in (1,1) (2,1) (3,3) (4,1) (4,3) (4,6) (7,6)",
+                             "width 16, (p_in, p_out) in (1,1) (2,1) (3,3) (4,1) (4,3) (4,6) (7,6); and "
+                             "(2,1) latent 2 width 8, (3,3) and (7,6) latent 5 width 16",
                              fn, s->p_in, s->p_out, s->latent, s->width);
     return MS_OK;
 }
@@ -472,7 +488,7 @@ extern "C" ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, f
 // latent normals.
 static size_t dev_step_extra(const ms_cvae_shape* s, uint64_t B)
 {
-    const size_t f = (size_t)B * (size_t)(s->p_out + s->p_in + kL) * sizeof(float);
+    const size_t f = (size_t)B * (size_t)(s->p_out + s->p_in + s->latent) * sizeof(float);
     return (f + 255) & ~(size_t)255;
 }
 
@@ -501,8 +517,8 @@ extern "C" ms_status ms_cvae_train_step_dev(const ms_cvae_shape* s, float* param
     float* xb = reinterpret_cast<float*>(static_cast<char*>(workspace) + base);
     float* cb = xb + B * s->p_out;
     float* eps = cb + B * s->p_in;
-    gather_batch<<<(unsigned)((B + 255) / 256), 256, 0, cs>>>(x_all, c_all, n_records, s->p_out, s->p_in, B, seed,
-                                                                step, xb, cb, eps);
+    gather_batch<<<(unsigned)((B + 255) / 256), 256, 0, cs>>>(x_all, c_all, n_records, s->p_out, s->p_in, s->latent,
+                                                                B, seed, step, xb, cb, eps);
     MS_CUDA(cudaGetLastError());
     const size_t nblk = (size_t)((B + kSamples - 1) / kSamples);
     const size_t partial_bytes = ((nblk * (pl.np + 2) * sizeof(float)) + 255) & ~(size_t)255;

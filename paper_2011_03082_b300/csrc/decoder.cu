@@ -12,17 +12,17 @@ namespace dec {
 
 constexpr int kInferThreads = 256;
 
-template <int IN4, int P>
+template <int IN4, int P, int W>
 __global__ void __launch_bounds__(kInferThreads, 2) infer_f32(const float* __restrict__ wts, int p_in, int latent,
                                                               const float* __restrict__ cond,
                                                               const float* __restrict__ z_eps, uint64_t seed,
                                                               uint64_t offset, uint64_t n, float* __restrict__ mlv,
                                                               float* __restrict__ smp)
 {
-    __shared__ __align__(16) float s[smem_floats(IN4, P)];
+    __shared__ __align__(16) float s[smem_floats<W>(IN4, P)];
     // per-thread staging row: [c ; z] in the first IN4 entries, then eps (dynamic offsets stay in shared memory)
     __shared__ __align__(16) float row[kInferThreads][IN4 + 8];
-    stage_weights(s, wts, p_in + latent, IN4, P);
+    stage_weights<W>(s, wts, p_in + latent, IN4, P);
     __syncthreads();
     float* my = row[threadIdx.x];
     const int nz = latent + P;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) infer_f32(const float* __res
             x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
         }
         float y[pad4(2 * P)];
-        mlp<IN4, P>(s, x, y);
+        mlp<IN4, P, W>(s, x, y);
         if (mlv) {
 #pragma unroll
             for (int o = 0; o < 2 * P; ++o) mlv[q * (2 * P) + o] = y[o];
@@ -64,34 +64,46 @@ __global__ void __launch_bounds__(kInferThreads, 2) infer_f32(const float* __res
     }
 }
 
-template <int IN4, int P>
+template <int IN4, int P, int W>
 cudaError_t launch_f32(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
                        uint64_t n, float* mlv, float* smp, cudaStream_t stream)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_f32<IN4, P>, kInferThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_f32<IN4, P, W>, kInferThreads, 0);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const uint64_t need = (n + kInferThreads - 1) / kInferThreads;
     if (grid > need) grid = need;
-    infer_f32<IN4, P><<<(unsigned)grid, kInferThreads, 0, stream>>>(d.weights, d.p_in, d.latent, cond, z_eps, seed,
-                                                                    offset, n, mlv, smp);
+    infer_f32<IN4, P, W><<<(unsigned)grid, kInferThreads, 0, stream>>>(d.weights, d.p_in, d.latent, cond, z_eps,
+                                                                       seed, offset, n, mlv, smp);
     return cudaGetLastError();
 }
 
-template <int IN4>
+template <int IN4, int W>
 cudaError_t dispatch_p(const ms_decoder& d, const float* c, const float* z, uint64_t seed, uint64_t off, uint64_t n,
                        float* mlv, float* smp, cudaStream_t s)
 {
     switch (d.p_out) {
-    case 1: return launch_f32<IN4, 1>(d, c, z, seed, off, n, mlv, smp, s);
-    case 2: return launch_f32<IN4, 2>(d, c, z, seed, off, n, mlv, smp, s);
-    case 3: return launch_f32<IN4, 3>(d, c, z, seed, off, n, mlv, smp, s);
-    case 4: return launch_f32<IN4, 4>(d, c, z, seed, off, n, mlv, smp, s);
-    case 5: return launch_f32<IN4, 5>(d, c, z, seed, off, n, mlv, smp, s);
-    case 6: return launch_f32<IN4, 6>(d, c, z, seed, off, n, mlv, smp, s);
-    case 7: return launch_f32<IN4, 7>(d, c, z, seed, off, n, mlv, smp, s);
-    default: return launch_f32<IN4, 8>(d, c, z, seed, off, n, mlv, smp, s);
+    case 1: return launch_f32<IN4, 1, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 2: return launch_f32<IN4, 2, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 3: return launch_f32<IN4, 3, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 4: return launch_f32<IN4, 4, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 5: return launch_f32<IN4, 5, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 6: return launch_f32<IN4, 6, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 7: return launch_f32<IN4, 7, W>(d, c, z, seed, off, n, mlv, smp, s);
+    default: return launch_f32<IN4, 8, W>(d, c, z, seed, off, n, mlv, smp, s);
+    }
+}
+
+template <int W>
+cudaError_t dispatch_in(const ms_decoder& d, const float* c, const float* z, uint64_t seed, uint64_t off, uint64_t n,
+                        float* mlv, float* smp, cudaStream_t s)
+{
+    switch (pad4(d.p_in + d.latent)) {
+    case 4: return dispatch_p<4, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 8: return dispatch_p<8, W>(d, c, z, seed, off, n, mlv, smp, s);
+    case 12: return dispatch_p<12, W>(d, c, z, seed, off, n, mlv, smp, s);
+    default: return dispatch_p<16, W>(d, c, z, seed, off, n, mlv, smp, s);
     }
 }
 
@@ -100,16 +112,16 @@ cudaError_t dispatch_p(const ms_decoder& d, const float* c, const float* z, uint
 // accumulation is FP32, so the result is that of the rounded weights to about 1e-4.
 constexpr int kMmaThreads = 128;
 
-template <int NT3, bool kBF16>
+template <int NT3, int NTH, bool kBF16>
 __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict__ wts, int p_in, int latent, int p_out,
                                                          const float* __restrict__ cond, const float* __restrict__ z_eps,
                                                          uint64_t seed, uint64_t offset, uint64_t n,
                                                          float* __restrict__ mlv, float* __restrict__ smp)
 {
-    __shared__ __align__(16) unsigned char wsm[mmadec::smem_bytes(8)];
+    __shared__ __align__(16) unsigned char wsm[mmadec::smem_bytes(8, NTH)];
     __shared__ float stage[kMmaThreads / 32][mmadec::kStageFloats];
     __shared__ float rows[kMmaThreads][41];   // [0,16) inputs, [16,24) eps, [24,40) outputs
-    mmadec::stage_weights<kBF16>(wsm, wts, p_in + latent, p_out);
+    mmadec::stage_weights<kBF16, NTH>(wsm, wts, p_in + latent, p_out);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* my = rows[threadIdx.x];
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict
 #pragma unroll
         for (int k = 0; k < 16; ++k) x[k] = my[k];
         float y[8 * NT3];
-        mmadec::warp_mlp<NT3, 2, kBF16>(wsm, stage[warp], x, y);
+        mmadec::warp_mlp<NT3, 2, kBF16, NTH>(wsm, stage[warp], x, y);
         if (live) {
 #pragma unroll
             for (int j = 0; j < 8 * NT3; ++j) my[24 + j] = y[j];
@@ -156,10 +168,12 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict
 cudaError_t launch_infer_mma(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
                              uint64_t n, float* mlv, float* smp, cudaStream_t stream)
 {
-    const bool bf16 = d.precision == MS_BF16;
+    const bool bf16 = d.precision == MS_BF16, w8 = d.width == 8;
     const int nt3 = mmadec::n_tiles_out(d.p_out);
-    auto kern = bf16 ? (nt3 == 1 ? infer_mma<1, true> : infer_mma<2, true>)
-                     : (nt3 == 1 ? infer_mma<1, false> : infer_mma<2, false>);
+    auto kern = bf16 ? (nt3 == 1 ? (w8 ? infer_mma<1, 1, true> : infer_mma<1, 2, true>)
+                                 : (w8 ? infer_mma<2, 1, true> : infer_mma<2, 2, true>))
+                     : (nt3 == 1 ? (w8 ? infer_mma<1, 1, false> : infer_mma<1, 2, false>)
+                                 : (w8 ? infer_mma<2, 1, false> : infer_mma<2, 2, false>));
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMmaThreads, 0);
     if (e != cudaSuccess) return e;
@@ -179,7 +193,7 @@ extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const
                                    void* stream)
 {
     MS_CHECK_ARG(d != nullptr && d->weights != nullptr, "ms_cvae_infer: null decoder or weights");
-    MS_CHECK_ARG(d->width == 16, "ms_cvae_infer: width must be 16 (got %d)", d->width);
+    MS_CHECK_ARG(d->width == 8 || d->width == 16, "ms_cvae_infer: width must be 8 or 16 (got %d)", d->width);
     MS_CHECK_ARG(d->p_in >= 1 && d->latent >= 1 && d->latent <= 8 && d->p_in + d->latent <= 16,
                  "ms_cvae_infer: need 1 <= p_in, 1 <= latent <= 8, p_in + latent <= 16");
     MS_CHECK_ARG(d->p_out >= 1 && d->p_out <= 8, "ms_cvae_infer: p_out must be in 1..8");
@@ -192,14 +206,9 @@ extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const
         MS_CUDA(ms::dec::launch_infer_mma(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s));
         return MS_OK;
     }
-    const int in4 = ms::dec::pad4(d->p_in + d->latent);
-    cudaError_t e;
-    switch (in4) {
-    case 4: e = ms::dec::dispatch_p<4>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
-    case 8: e = ms::dec::dispatch_p<8>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
-    case 12: e = ms::dec::dispatch_p<12>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
-    default: e = ms::dec::dispatch_p<16>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s); break;
-    }
+    const cudaError_t e =
+        d->width == 8 ? ms::dec::dispatch_in<8>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s)
+                      : ms::dec::dispatch_in<16>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s);
     MS_CUDA(e);
     return MS_OK;
 }

@@ -1,10 +1,10 @@
 // CVAE decoder MLP (Sec. 3.2, Fig. 3b): three weight layers, Softplus between hidden layers, linear output
 // (mu, log Sigma).  Single-precision, one query per thread, weights in shared memory.
 //
-// Shared-memory layout (floats), transposed so that one input's weights to all outputs are contiguous and
-// every weight load is a 16-byte broadcast (all lanes read the same address):
-//   W1t[IN4][16] b1[16] W2t[16][16] b2[16] W3t[16][O4] b3[O4]      (O4 = 2P rounded up to 4, zero padded)
-// The layer loops run input-outer / output-inner, so only the 16 accumulators and one weight row are live.
+// Shared-memory layout (floats) for hidden width W, transposed so that one input's weights to all outputs are
+// contiguous and every weight load is a 16-byte broadcast (all lanes read the same address):
+//   W1t[IN4][W] b1[W] W2t[W][W] b2[W] W3t[W][O4] b3[O4]      (O4 = 2P rounded up to 4, zero padded)
+// The layer loops run input-outer / output-inner, so only the W accumulators and one weight row are live.
 #pragma once
 
 #include "ms_device.cuh"
@@ -12,16 +12,16 @@
 namespace ms {
 namespace dec {
 
-constexpr int W = 16;
-
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 
+template <int W>
 __host__ __device__ constexpr int smem_floats(int in4, int p)
 {
     return in4 * W + W + W * W + W + W * pad4(2 * p) + pad4(2 * p);
 }
 
-// Copies packed weights (W1[16][in] b1 W2[16][16] b2 W3[2p][16] b3) into the transposed shared layout.
+// Copies packed weights (W1[W][in] b1 W2[W][W] b2 W3[2p][W] b3) into the transposed shared layout.
+template <int W>
 __device__ __forceinline__ void stage_weights(float* s, const float* __restrict__ g, int in, int in4, int p)
 {
     const int o4 = pad4(2 * p);
@@ -79,7 +79,7 @@ __device__ __forceinline__ void dense(const float* __restrict__ Wt, const float*
 }
 
 // y = W3 sp(W2 sp(W1 x + b1) + b2) + b3; x has IN4 entries (zero padded), y has pad4(2P) entries.
-template <int IN4, int P>
+template <int IN4, int P, int W>
 __device__ __forceinline__ void mlp(const float* __restrict__ s, const float (&x)[IN4], float (&y)[pad4(2 * P)])
 {
     constexpr int O4 = pad4(2 * P);

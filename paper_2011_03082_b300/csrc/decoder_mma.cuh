@@ -1,7 +1,9 @@
 // Warp-level CVAE decoder MLP (Sec. 3.2) on the tensor cores with mma.sync.m16n8k16 (FP32 accumulation).
 //
 // A warp evaluates 32 rows at once (two 16-row tiles), one row per lane:
-//   y = W3 sp(W2 sp(W1 x + b1) + b2) + b3,   x in R^16 (zero padded), hidden width 16, y in R^{8 NT3}.
+//   y = W3 sp(W2 sp(W1 x + b1) + b2) + b3,   x in R^16 (zero padded), hidden width 8 NTH (8 or 16),
+//   y in R^{8 NT3}.  A width-8 hidden layer fills the lower half of the next layer's k = 16 operand and zeros
+//   the upper half.
 // The weights are pre-arranged once per block in shared memory in the B-fragment order of the instruction
 // (each lane loads its two 32-bit operand registers per 8-column tile with one 16-byte load), the biases
 // initialise the accumulators, and the accumulator fragment of a hidden layer is, register for register, the
@@ -27,11 +29,12 @@ constexpr int kStageStride = 17;                         // floats per staged ro
 constexpr int kStageFloats = 32 * kStageStride;          // one warp's staging tile
 
 __host__ __device__ constexpr int n_tiles_out(int p_out) { return (2 * p_out + 7) / 8; }
-// shared layout of one decoder: fragments [2 + 2 + NT3][32] uint4, then biases [16 + 16 + 8 NT3] floats
-__host__ __device__ constexpr int frag_tiles(int p_out) { return 4 + n_tiles_out(p_out); }
-__host__ __device__ constexpr int smem_bytes(int p_out)
+// shared layout of one decoder with NTH hidden tiles (width 8 NTH): fragments [NTH + NTH + NT3][32] uint4, then
+// biases [8 NTH + 8 NTH + 8 NT3] floats
+__host__ __device__ constexpr int frag_tiles(int p_out, int nth = 2) { return 2 * nth + n_tiles_out(p_out); }
+__host__ __device__ constexpr int smem_bytes(int p_out, int nth = 2)
 {
-    return frag_tiles(p_out) * 32 * 16 + (32 + 8 * n_tiles_out(p_out)) * 4;
+    return frag_tiles(p_out, nth) * 32 * 16 + (16 * nth + 8 * n_tiles_out(p_out)) * 4;
 }
 
 template <bool kBF16>
@@ -83,24 +86,26 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint3
     }
 }
 
-// Block-wide: packed float weights W1[16][k_in] b1 W2[16][16] b2 W3[2p][16] b3 -> fragment layout at `dst`.
-// For 8-column tile j and lane (g = lane / 4, t = lane % 4) the B operand holds rows k = 2t, 2t+1 (b0) and
-// 2t+8, 2t+9 (b1) of column n = 8j + g, i.e. W[n][k]; stored as {b0 head, b1 head, b0 tail, b1 tail}.
-template <bool kBF16>
+// Block-wide: packed float weights W1[w][k_in] b1 W2[w][w] b2 W3[2p][w] b3 (w = 8 NTH) -> fragment layout at
+// `dst`.  For 8-column tile j and lane (g = lane / 4, t = lane % 4) the B operand holds rows k = 2t, 2t+1 (b0)
+// and 2t+8, 2t+9 (b1) of column n = 8j + g, i.e. W[n][k] (zero for k >= K); stored as
+// {b0 head, b1 head, b0 tail, b1 tail}.
+template <bool kBF16, int NTH = 2>
 __device__ void stage_weights(unsigned char* dst, const float* __restrict__ g, int k_in, int p_out)
 {
+    constexpr int w = 8 * NTH;
     const int nt3 = n_tiles_out(p_out);
     uint4* frag = reinterpret_cast<uint4*>(dst);
-    float* bias = reinterpret_cast<float*>(dst + frag_tiles(p_out) * 32 * 16);
-    const float* W[3] = {g, g + 16 * k_in + 16, g + 16 * k_in + 16 + 256 + 16};
-    const float* Bv[3] = {g + 16 * k_in, g + 16 * k_in + 16 + 256, g + 16 * k_in + 16 + 256 + 16 + 2 * p_out * 16};
-    const int K[3] = {k_in, 16, 16};
-    const int N[3] = {16, 16, 2 * p_out};
-    const int T0[3] = {0, 2, 4};
-    const int total = frag_tiles(p_out) * 32;
+    float* bias = reinterpret_cast<float*>(dst + frag_tiles(p_out, NTH) * 32 * 16);
+    const float* W[3] = {g, g + w * k_in + w, g + w * k_in + w + w * w + w};
+    const float* Bv[3] = {g + w * k_in, g + w * k_in + w + w * w, g + w * k_in + w + w * w + w + 2 * p_out * w};
+    const int K[3] = {k_in, w, w};
+    const int N[3] = {w, w, 2 * p_out};
+    const int T0[3] = {0, NTH, 2 * NTH};
+    const int total = frag_tiles(p_out, NTH) * 32;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int tile = e >> 5, lane = e & 31;
-        const int layer = tile < 2 ? 0 : (tile < 4 ? 1 : 2);
+        const int layer = tile < NTH ? 0 : (tile < 2 * NTH ? 1 : 2);
         const int j = tile - T0[layer];
         const int n = 8 * j + (lane >> 2), t = lane & 3;
         auto w = [&](int k) -> float {
@@ -118,10 +123,10 @@ __device__ void stage_weights(unsigned char* dst, const float* __restrict__ g, i
         }
         frag[e] = make_uint4(h0, h1, l0, l1);
     }
-    for (int e = threadIdx.x; e < 32 + 8 * nt3; e += blockDim.x) {
-        if (e < 16) bias[e] = Bv[0][e];
-        else if (e < 32) bias[e] = Bv[1][e - 16];
-        else bias[e] = (e - 32) < 2 * p_out ? Bv[2][e - 32] : 0.0f;
+    for (int e = threadIdx.x; e < 2 * w + 8 * nt3; e += blockDim.x) {
+        if (e < w) bias[e] = Bv[0][e];
+        else if (e < 2 * w) bias[e] = Bv[1][e - w];
+        else bias[e] = (e - 2 * w) < 2 * p_out ? Bv[2][e - 2 * w] : 0.0f;
     }
 }
 
@@ -145,9 +150,10 @@ __device__ __forceinline__ void layer(const uint32_t (&ah)[2][4], const uint32_t
     }
 }
 
-// Softplus of a 16-wide hidden layer, re-packed as the next layer's A fragments (head and tail).
-template <int kSplit, bool kBF16>
-__device__ __forceinline__ void hidden_to_a(const float (&acc)[2][2][4], uint32_t (&ah)[2][4], uint32_t (&al)[2][4])
+// Softplus of an 8 NTH-wide hidden layer, re-packed as the next layer's A fragments (head and tail); with
+// NTH = 1 the upper k half (columns 8..15) is zero.
+template <int kSplit, bool kBF16, int NTH = 2>
+__device__ __forceinline__ void hidden_to_a(const float (&acc)[2][NTH][4], uint32_t (&ah)[2][4], uint32_t (&al)[2][4])
 {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -155,7 +161,7 @@ __device__ __forceinline__ void hidden_to_a(const float (&acc)[2][2][4], uint32_
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             s[i] = softplus(acc[mt][0][i]);
-            s[4 + i] = softplus(acc[mt][1][i]);
+            s[4 + i] = NTH == 2 ? softplus(acc[mt][NTH - 1][i]) : 0.0f;
         }
         if (kSplit >= 2) {
             split2<kBF16>(s[0], s[1], ah[mt][0], al[mt][0]);
@@ -173,13 +179,13 @@ __device__ __forceinline__ void hidden_to_a(const float (&acc)[2][2][4], uint32_
 
 // The whole MLP for the warp's 32 rows; every lane of the warp must call it (it synchronises the warp).
 // x: this lane's input row (16 values, zero padded); y: this lane's 8*NT3 outputs (mu then log Sigma).
-template <int NT3, int kSplit, bool kBF16>
+template <int NT3, int kSplit, bool kBF16, int NTH = 2>
 __device__ __forceinline__ void warp_mlp(const unsigned char* __restrict__ wsm, float* __restrict__ stage,
                                          const float (&x)[16], float (&y)[8 * NT3])
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint4* frag = reinterpret_cast<const uint4*>(wsm);
-    const float* bias = reinterpret_cast<const float*>(wsm + (4 + NT3) * 32 * 16);
+    const float* bias = reinterpret_cast<const float*>(wsm + (2 * NTH + NT3) * 32 * 16);
 #pragma unroll
     for (int j = 0; j < 16; ++j) stage[lane * kStageStride + j] = x[j];
     __syncwarp();
@@ -194,13 +200,13 @@ __device__ __forceinline__ void warp_mlp(const unsigned char* __restrict__ wsm, 
         split2<kBF16>(r1[2 * t + 8], r1[2 * t + 9], ah[mt][3], al[mt][3]);
     }
     __syncwarp();
-    float h[2][2][4];
-    layer<2, kSplit, kBF16>(ah, al, frag, bias, lane, h);
-    hidden_to_a<kSplit, kBF16>(h, ah, al);
-    layer<2, kSplit, kBF16>(ah, al, frag + 2 * 32, bias + 16, lane, h);
-    hidden_to_a<kSplit, kBF16>(h, ah, al);
+    float h[2][NTH][4];
+    layer<NTH, kSplit, kBF16>(ah, al, frag, bias, lane, h);
+    hidden_to_a<kSplit, kBF16, NTH>(h, ah, al);
+    layer<NTH, kSplit, kBF16>(ah, al, frag + NTH * 32, bias + 8 * NTH, lane, h);
+    hidden_to_a<kSplit, kBF16, NTH>(h, ah, al);
     float o[2][NT3][4];
-    layer<NT3, kSplit, kBF16>(ah, al, frag + 4 * 32, bias + 32, lane, o);
+    layer<NT3, kSplit, kBF16>(ah, al, frag + 2 * NTH * 32, bias + 16 * NTH, lane, o);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll

@@ -68,9 +68,14 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// decoder shapes: LengthGen (2 + 4 -> 1), PathGen (3 + 4 -> 3), EventGen (7 + 4 -> 6); tensor-core fragment
-// layouts in shared memory (decoder_mma.cuh)
-constexpr int kBytesL = mmadec::smem_bytes(1), kBytesP = mmadec::smem_bytes(3), kBytesE = mmadec::smem_bytes(6);
+// decoder shapes, the final settings of Table 1: LengthGen (2 + L 2 -> 1, width 8), PathGen (3 + L 5 -> 3,
+// width 16), EventGen (7 + L 5 -> 6, width 16); tensor-core fragment layouts in shared memory
+// (decoder_mma.cuh).  A sphere step's 22 normals n[] (tags 2..7) are split as z then eps per model.
+constexpr int kLatL = 2, kLatP = 5, kLatE = 5;
+constexpr int kZL = 0, kEL = kZL + kLatL, kZP = kEL + 1, kEP = kZP + kLatP, kZE = kEP + 3, kEE = kZE + kLatE;
+static_assert(kEE + 6 <= 24, "a sphere step draws 24 normals");
+constexpr int kBytesL = mmadec::smem_bytes(1, 1), kBytesP = mmadec::smem_bytes(3, 2),
+              kBytesE = mmadec::smem_bytes(6, 2);
 
 struct V { float x, y, z; };
 __device__ __forceinline__ V v3(float x, float y, float z) { return V{x, y, z}; }
@@ -214,9 +219,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     unsigned char* wev = sw + kBytesL + kBytesP;
     float* stage = s_stage[tid >> 5];
     if constexpr (learned) {
-        mmadec::stage_weights<false>(wl, B.wL, 2 + 4, 1);
-        mmadec::stage_weights<false>(wpth, B.wP, 3 + 4, 3);
-        mmadec::stage_weights<false>(wev, B.wE, 7 + 4, 6);
+        mmadec::stage_weights<false, 1>(wl, B.wL, 2 + kLatL, 1);
+        mmadec::stage_weights<false, 2>(wpth, B.wP, 3 + kLatP, 3);
+        mmadec::stage_weights<false, 2>(wev, B.wE, 7 + kLatE, 6);
     }
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     if (tid == 0) atomicMin(B.t_start, global_ns());
@@ -334,37 +339,38 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 for (int k = 0; k < 24; ++k) n[k] = 0.0f;
             }
             // LengthGen: N (albedo-1 physics, Eq. 3)
-            float xin[16] = {ltau, mine ? qq.g : 0.0f, n[0], n[1], n[2], n[3]};
+            float xin[16] = {ltau, mine ? qq.g : 0.0f, n[kZL], n[kZL + 1]};
             float yL[8];
-            mmadec::warp_mlp<1, 3, false>(wl, stage, xin, yL);
-            const float yN = yL[0] + __expf(0.5f * yL[1]) * n[4];
+            mmadec::warp_mlp<1, 3, false, 1>(wl, stage, xin, yL);
+            const float yN = yL[0] + __expf(0.5f * yL[1]) * n[kEL];
             float N = floorf(__expf(yN) + 0.5f);
             N = fminf(fmaxf(N, 1.0f), kNMax);
             const float lnN = mine ? __logf(N) : 0.0f;
             // PathGen: (cos theta, alpha, beta)
-            float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, n[5], n[6], n[7], n[8]};
+            float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, n[kZP], n[kZP + 1], n[kZP + 2], n[kZP + 3], n[kZP + 4]};
             float yP[8];
-            mmadec::warp_mlp<1, 3, false>(wpth, stage, xp, yP);
-            const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * n[9]));
-            float al = yP[1] + __expf(0.5f * yP[4]) * n[10];
-            float be = yP[2] + __expf(0.5f * yP[5]) * n[11];
+            mmadec::warp_mlp<1, 3, false, 2>(wpth, stage, xp, yP);
+            const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * n[kEP]));
+            float al = yP[1] + __expf(0.5f * yP[4]) * n[kEP + 1];
+            float be = yP[2] + __expf(0.5f * yP[5]) * n[kEP + 2];
             float ab2 = al * al + be * be;
             if (ab2 > 1.0f) {
                 const float s = rsqrtf(ab2);
                 al *= s; be *= s; ab2 = 1.0f;
             }
             // EventGen: representative event (X~, W~)
-            float xe[16] = {ltau, mine ? qq.g : 0.0f, mine ? qq.phi : 0.0f, ct, al, be, lnN, n[12], n[13], n[14], n[15]};
+            float xe[16] = {ltau, mine ? qq.g : 0.0f, mine ? qq.phi : 0.0f, ct, al, be, lnN,
+                            n[kZE], n[kZE + 1], n[kZE + 2], n[kZE + 3], n[kZE + 4]};
             if (!mine) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) xe[k] = 0.0f;
             }
             float yE[16];
-            mmadec::warp_mlp<2, 3, false>(wev, stage, xe, yE);
+            mmadec::warp_mlp<2, 3, false, 2>(wev, stage, xe, yE);
             if (mine) {
                 float e[6];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * n[16 + k];
+                for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * n[kEE + k];
                 const float phiN = __expf(N * qq.log_phi);
                 const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
                 // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
@@ -667,11 +673,12 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     if (any_sphere) {
         MS_CHECK_ARG(models != nullptr, "%s: MS_SPHERE needs the three decoders", fn);
         const ms_decoder* d[3] = {&models->length, &models->path, &models->event};
-        const int pin[3] = {2, 3, 7}, pout[3] = {1, 3, 6};
+        const int pin[3] = {2, 3, 7}, pout[3] = {1, 3, 6}, lat[3] = {kLatL, kLatP, kLatE}, wid[3] = {8, 16, 16};
         for (int k = 0; k < 3; ++k) {
             MS_CHECK_ARG(d[k]->weights != nullptr && d[k]->p_in == pin[k] && d[k]->p_out == pout[k] &&
-                             d[k]->latent == 4 && d[k]->width == 16,
-                         "%s: decoder %d must have p_in %d, latent 4, width 16, p_out %d", fn, k, pin[k], pout[k]);
+                             d[k]->latent == lat[k] && d[k]->width == wid[k],
+                         "%s: decoder %d must have p_in %d, latent %d, width %d, p_out %d (Table 1)", fn, k, pin[k],
+                         lat[k], wid[k], pout[k]);
             MS_CHECK_ARG(d[k]->precision == MS_FP32, "%s: the renderer evaluates FP32 decoders", fn);
         }
         b.wL = models->length.weights;

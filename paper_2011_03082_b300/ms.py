@@ -281,12 +281,14 @@ def render_params(d: dict) -> RenderParams:
 
 
 def cvae_set(models: dict, precision=MS_FP32) -> CvaeSet:
-    """models: {"length": (weights, p_in, p_out), "path": ..., "event": ...} with device float32 weights.
-    The returned struct keeps the weight tensors alive (it holds only their device pointers otherwise)."""
+    """models: {"length": (weights, p_in, p_out, latent, width), "path": ..., "event": ...} with device float32
+    weights (latent 4 and width 16 when a tuple has three entries).  The returned struct keeps the weight
+    tensors alive (it holds only their device pointers otherwise)."""
     s = CvaeSet()
     for k in ("length", "path", "event"):
-        w, p_in, p_out = models[k]
-        setattr(s, k, decoder_struct(w, p_in, p_out, precision=precision))
+        w, p_in, p_out, *lw = models[k]
+        latent, width = lw if lw else (4, 16)
+        setattr(s, k, decoder_struct(w, p_in, p_out, latent, width, precision=precision))
     s._owned = {k: models[k][0] for k in ("length", "path", "event")}
     return s
 

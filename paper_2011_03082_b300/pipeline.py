@@ -8,8 +8,8 @@
 2. ``train``: each CVAE is trained with the library's kernels: one step (mini-batch drawn on the device,
    forward, backward, deterministic reduction, Adam) is captured in a CUDA graph and replayed
    (``ms_cvae_train_step_dev``).
-3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder) and
-   the training log.
+3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder), each
+   model's shape (p_in, p_out, latent, width: the final settings of Table 1) and the training log.
 
 Run as ``python -m paper_2011_03082_b300.pipeline [--walks N] [--steps S] [--out PATH]``.
 """
@@ -25,7 +25,7 @@ import torch
 
 from . import ms, synth
 
-FORMAT = 1
+FORMAT = 2
 DEFAULT_WEIGHTS = Path(__file__).resolve().parent / "weights" / "cvae_set.npz"
 MODELS = ("length", "path", "event")
 RECORD_KEYS = {"length": ("cL", "xL"), "path": ("cP", "xP"), "event": ("cE", "xE")}
@@ -49,10 +49,10 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
               log_every: int = 100):
     """Train one CVAE: one training step (device-side batch sampling, forward, backward, deterministic
     reduction, Adam with its step counter on the device) is captured in a CUDA graph and replayed."""
-    p_in, p_out = synth.MODEL_SHAPES[name]
-    shape = ms.cvae_shape(p_in, p_out)
+    p_in, p_out, latent, width = synth.MODEL_SHAPES[name]
+    shape = ms.cvae_shape(p_in, p_out, latent, width)
     dev = c.device
-    params = torch.from_numpy(synth.xavier_cvae(seed, p_in, p_out)).to(dev)
+    params = torch.from_numpy(synth.xavier_cvae(seed, p_in, p_out, latent, width)).to(dev)
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
     step = torch.ones(1, dtype=torch.int64, device=dev)
@@ -75,7 +75,7 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
     return params, log
 
 
-def train(records: dict, *, steps=2000, batch=65536, lr=1e-3, seed=1, log_every=100) -> dict:
+def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every=100) -> dict:
     models = {}
     for i, name in enumerate(MODELS):
         ck, xk = RECORD_KEYS[name]
@@ -87,8 +87,7 @@ def train(records: dict, *, steps=2000, batch=65536, lr=1e-3, seed=1, log_every=
 
 def decoder_part(name: str, params: np.ndarray) -> np.ndarray:
     """The decoder block of a packed CVAE parameter vector (what the renderer evaluates)."""
-    p_in, p_out = synth.MODEL_SHAPES[name]
-    W, L = synth.WIDTH, synth.LATENT
+    p_in, p_out, L, W = synth.MODEL_SHAPES[name]
     n_enc = W * (p_out + p_in) + W + W * W + W + 2 * L * W + 2 * L
     return np.ascontiguousarray(params[n_enc:], dtype=np.float32)
 
@@ -98,6 +97,7 @@ def save(path, models: dict, meta: dict):
     path.parent.mkdir(parents=True, exist_ok=True)
     arrays = {f"{k}_params": v["params"].astype(np.float32) for k, v in models.items()}
     arrays.update({f"{k}_log": np.asarray(v["log"], np.float64) for k, v in models.items()})
+    arrays.update({f"{k}_shape": np.asarray(synth.MODEL_SHAPES[k], np.int64) for k in models})
     np.savez(path, format=np.int64(FORMAT), meta=json.dumps(meta), **arrays)
 
 
@@ -105,23 +105,33 @@ def load(path=DEFAULT_WEIGHTS) -> dict:
     z = np.load(path, allow_pickle=False)
     if int(z["format"]) != FORMAT:
         raise ValueError(f"{path}: unsupported weights format {int(z['format'])}")
+    for k in MODELS:
+        shape = tuple(int(v) for v in z[f"{k}_shape"])
+        if shape != tuple(synth.MODEL_SHAPES[k]) or z[f"{k}_params"].size != _n_params(k):
+            raise ValueError(f"{path}: {k} has shape {shape}, expected {synth.MODEL_SHAPES[k]}")
     return {k: dict(params=z[f"{k}_params"], log=z[f"{k}_log"]) for k in MODELS} | {
         "meta": json.loads(str(z["meta"]))}
 
 
+def _n_params(name: str) -> int:
+    p_in, p_out, L, W = synth.MODEL_SHAPES[name]
+    enc = W * (p_out + p_in) + W + W * W + W + 2 * L * W + 2 * L
+    dec = W * (p_in + L) + W + W * W + W + 2 * p_out * W + 2 * p_out
+    return enc + dec
+
+
 def device_decoders(models: dict, device="cuda") -> dict:
-    """{name: (decoder weights on the device, p_in, p_out)} as ms.cvae_set expects."""
+    """{name: (decoder weights on the device, p_in, p_out, latent, width)} as ms.cvae_set expects."""
     out = {}
     for name in MODELS:
-        p_in, p_out = synth.MODEL_SHAPES[name]
-        out[name] = (torch.from_numpy(decoder_part(name, models[name]["params"])).to(device), p_in, p_out)
+        out[name] = (torch.from_numpy(decoder_part(name, models[name]["params"])).to(device), *synth.MODEL_SHAPES[name])
     return out
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--walks", type=int, default=1 << 24)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)

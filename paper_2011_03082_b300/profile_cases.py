@@ -47,9 +47,9 @@ def case_decoder(n=1 << 22, p_out=6, precision=ms.MS_FP32):
 
 
 def case_train(B=65536):
-    p_in, p_out = synth.MODEL_SHAPES["event"]
-    shape = ms.cvae_shape(p_in, p_out)
-    p = torch.from_numpy(synth.xavier_cvae(1, p_in, p_out)).cuda()
+    p_in, p_out, latent, width = synth.MODEL_SHAPES["event"]
+    shape = ms.cvae_shape(p_in, p_out, latent, width)
+    p = torch.from_numpy(synth.xavier_cvae(1, p_in, p_out, latent, width)).cuda()
     m, v = torch.zeros_like(p), torch.zeros_like(p)
     g = torch.Generator().manual_seed(0)
     x = torch.randn(B, p_out, generator=g).cuda()

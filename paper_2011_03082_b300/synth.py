@@ -17,7 +17,9 @@ from __future__ import annotations
 import numpy as np
 
 # Model shapes (P_in, P_out) of the three learned samplers (Eq. 3): LengthGen, PathGen, EventGen.
-MODEL_SHAPES = {"length": (2, 1), "path": (3, 3), "event": (7, 6)}
+# (p_in, p_out, latent, width) of the three CVAEs: the final settings of Table 1 (D = 2 hidden layers)
+MODEL_SHAPES = {"length": (2, 1, 2, 8), "path": (3, 3, 5, 16), "event": (7, 6, 5, 16)}
+# defaults of the generic helpers (and of the decoder benchmark's condition-4 decoders)
 LATENT = 4
 WIDTH = 16
 

@@ -12,35 +12,37 @@ from paper_2011_03082_b300 import ms, synth
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(4, 1), (4, 6), (2, 1), (3, 3), (7, 6), (1, 8), (12, 2)]
+# (p_in, p_out, latent, width): latent-4 / width-16 shapes, the final Table 1 shapes, and width 8 with P_out 6
+SHAPES = [(4, 1, 4, 16), (4, 6, 4, 16), (2, 1, 4, 16), (3, 3, 4, 16), (7, 6, 4, 16), (1, 8, 4, 16),
+          (12, 2, 4, 16), (2, 1, 2, 8), (3, 3, 5, 16), (7, 6, 5, 16), (4, 6, 4, 8)]
 
 
-def _run(w, p_in, p_out, cond, n, z_eps=None, seed=7, offset=0, latent=4):
+def _run(w, p_in, p_out, cond, n, z_eps=None, seed=7, offset=0, latent=4, width=16):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     wt, ct = dev(w), dev(cond)
     ze = dev(z_eps) if z_eps is not None else None
     mlv = torch.zeros(n, 2 * p_out, device="cuda")
     smp = torch.zeros(n, p_out, device="cuda")
-    d = ms.decoder_struct(wt, p_in, p_out, latent=latent)
+    d = ms.decoder_struct(wt, p_in, p_out, latent=latent, width=width)
     ms.ms_cvae_infer(d, ct, n, z_eps=ze, seed=seed, offset=offset, out_mean_logvar=mlv, out_sample=smp)
     torch.cuda.synchronize()
     return mlv.cpu().numpy(), smp.cpu().numpy()
 
 
-@pytest.mark.parametrize("p_in,p_out", SHAPES)
+@pytest.mark.parametrize("p_in,p_out,latent,width", SHAPES)
 @pytest.mark.parametrize("n", [1, 1000, 65539])
-def test_decoder_given_normals(p_in, p_out, n):
-    shape = cvae.Shape(p_in, p_out)
-    w = synth.xavier_decoder(7, p_in, p_out)
+def test_decoder_given_normals(p_in, p_out, latent, width, n):
+    shape = cvae.Shape(p_in, p_out, latent, width)
+    w = synth.xavier_decoder(7, p_in, p_out, latent, width)
     w = w + np.float32(0.05) * synth.standard_normals(8, w.shape)   # nonzero biases too
     rng = np.random.default_rng(1)
     cond = rng.uniform(-1, 2, (n, p_in)).astype(np.float32)
-    ze = synth.standard_normals(2, (n, 4 + p_out))
-    mlv, smp = _run(w, p_in, p_out, cond, n, ze)
-    mu, lv = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :4])
+    ze = synth.standard_normals(2, (n, latent + p_out))
+    mlv, smp = _run(w, p_in, p_out, cond, n, ze, latent=latent, width=width)
+    mu, lv = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :latent])
     assert np.abs(mlv[:, :p_out] - mu).max() <= 1e-5
     assert np.abs(mlv[:, p_out:] - lv).max() <= 1e-5
-    ref = mu + np.exp(0.5 * lv) * ze[:, 4:]
+    ref = mu + np.exp(0.5 * lv) * ze[:, latent:]
     assert np.abs(smp - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
 
@@ -77,7 +79,7 @@ def test_decoder_rejects_bad_shapes():
     w = torch.zeros(1000, device="cuda")
     c = torch.zeros(4, 4, device="cuda")
     out = torch.zeros(4, 2, device="cuda")
-    for kw in (dict(p_in=4, p_out=9), dict(p_in=13, p_out=1), dict(p_in=4, p_out=1, width=8)):
+    for kw in (dict(p_in=4, p_out=9), dict(p_in=13, p_out=1), dict(p_in=4, p_out=1, width=12)):
         d = ms.decoder_struct(w, kw["p_in"], kw["p_out"], width=kw.get("width", 16))
         with pytest.raises(ms.MsError):
             ms.ms_cvae_infer(d, c, 4, out_mean_logvar=out)
@@ -91,28 +93,29 @@ def _round_bf16(a):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-@pytest.mark.parametrize("p_in,p_out", [(4, 1), (4, 6), (7, 6), (3, 3)])
-def test_half_precision_decoder(p_in, p_out, prec):
+@pytest.mark.parametrize("p_in,p_out,latent,width", [(4, 1, 4, 16), (4, 6, 4, 16), (7, 6, 4, 16), (3, 3, 4, 16),
+                                                     (2, 1, 2, 8), (3, 3, 5, 16), (7, 6, 5, 16), (4, 6, 4, 8)])
+def test_half_precision_decoder(p_in, p_out, latent, width, prec):
     """Tensor-core decoder (FP16 or BF16 weights and activations, FP32 accumulation): max |error| <= 3e-3
     against the FP64 oracle given the same rounded weights; the error against the FP32 weights is bounded
     too (rounding of the weights themselves)."""
     n = 40000
-    w = synth.xavier_decoder(7, p_in, p_out)
+    w = synth.xavier_decoder(7, p_in, p_out, latent, width)
     cond = synth.decoder_queries(7, n)[:, :p_in] if p_in <= 4 else \
         np.random.default_rng(2).uniform(-1, 2, (n, p_in)).astype(np.float32)
-    ze = synth.standard_normals(3, (n, 4 + p_out))
+    ze = synth.standard_normals(3, (n, latent + p_out))
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     mlv = torch.zeros(n, 2 * p_out, device="cuda")
     smp = torch.zeros(n, p_out, device="cuda")
-    d = ms.decoder_struct(dev(w), p_in, p_out, precision=ms.MS_FP16 if prec == "fp16" else ms.MS_BF16)
+    d = ms.decoder_struct(dev(w), p_in, p_out, latent, width, precision=ms.MS_FP16 if prec == "fp16" else ms.MS_BF16)
     ms.ms_cvae_infer(d, dev(cond), n, z_eps=dev(ze), out_mean_logvar=mlv, out_sample=smp)
     torch.cuda.synchronize()
     wq = w.astype(np.float16).astype(np.float64) if prec == "fp16" else _round_bf16(w)
-    shape = cvae.Shape(p_in, p_out)
-    mu, lv = cvae.decoder_forward(wq, shape, cond, ze[:, :4])
+    shape = cvae.Shape(p_in, p_out, latent, width)
+    mu, lv = cvae.decoder_forward(wq, shape, cond, ze[:, :latent])
     got = mlv.cpu().numpy()
     assert np.abs(got[:, :p_out] - mu).max() <= 3e-3
     assert np.abs(got[:, p_out:] - lv).max() <= 3e-3
-    mu32, _ = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :4])
+    mu32, _ = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :latent])
     assert np.abs(got[:, :p_out] - mu32).max() <= (2e-2 if prec == "bf16" else 3e-3)
-    assert np.allclose(smp.cpu().numpy(), mu + np.exp(0.5 * lv) * ze[:, 4:], atol=1e-2)
+    assert np.allclose(smp.cpu().numpy(), mu + np.exp(0.5 * lv) * ze[:, latent:], atol=1e-2)

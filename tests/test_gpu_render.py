@@ -23,8 +23,8 @@ pytestmark = pytest.mark.gpu
 
 def _models():
     out = {}
-    for i, (name, (p_in, p_out)) in enumerate(synth.MODEL_SHAPES.items()):
-        out[name] = (synth.xavier_decoder(100 + i, p_in, p_out), p_in, p_out)
+    for i, (name, shape) in enumerate(synth.MODEL_SHAPES.items()):
+        out[name] = (synth.xavier_decoder(100 + i, *shape), *shape)
     return out
 
 
@@ -35,10 +35,10 @@ def gpu_render(params, models=None):
     keep = []
     if models is not None:
         dm = {}
-        for k, (w, pi, po) in models.items():
+        for k, (w, *shape) in models.items():
             t = torch.from_numpy(w).cuda()
             keep.append(t)
-            dm[k] = (t, pi, po)
+            dm[k] = (t, *shape)
         cs = ms.cvae_set(dm)
     ms.ms_render(ms.render_params(params), cs, img, st)
     torch.cuda.synchronize()
@@ -48,7 +48,7 @@ def gpu_render(params, models=None):
 def oracle_render(orc, params, models=None):
     decs = None
     if models is not None:
-        decs = [(models[k][0].astype(np.float64), models[k][1], models[k][2]) for k in ("length", "path", "event")]
+        decs = [(models[k][0].astype(np.float64), *models[k][1:]) for k in ("length", "path", "event")]
     img, st, _ = orc.render(params, decs)
     return img, st
 
@@ -100,7 +100,7 @@ def test_sample_offsets_and_batches_compose():
     npx = sum(r["width"] * r["height"] for r in reqs)
     imgs = torch.zeros(npx, dtype=torch.float64, device="cuda")
     st = torch.zeros(len(reqs), 16, dtype=torch.int64, device="cuda")
-    dm = {k: (torch.from_numpy(w).cuda(), pi, po) for k, (w, pi, po) in models.items()}
+    dm = {k: (torch.from_numpy(w).cuda(), *shape) for k, (w, *shape) in models.items()}
     ms.ms_render_batch([ms.render_params(r) for r in reqs], ms.cvae_set(dm), imgs, st)
     torch.cuda.synchronize()
     off = 0
@@ -143,7 +143,7 @@ def test_kernel_variants_agree_and_autotune():
             ref_img, ref_st = img, st
         assert np.array_equal(st[:10], ref_st[:10]), v
         assert np.allclose(img, ref_img, rtol=1e-6, atol=1e-12), v
-    dm = {k: (torch.from_numpy(w).cuda(), pi, po) for k, (w, pi, po) in models.items()}
+    dm = {k: (torch.from_numpy(w).cuda(), *shape) for k, (w, *shape) in models.items()}
     imgs = torch.zeros(32 * 32, dtype=torch.float64, device="cuda")
     st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
     best, times = ms.ms_render_autotune([ms.render_params(p)], ms.cvae_set(dm), imgs, st)
@@ -158,7 +158,7 @@ def test_batch_in_a_cuda_graph_matches_direct_launch():
     models = _models()
     reqs = [ms.render_params(r) for r in synth.batch_requests(5, 6, scale=1 / 32)]
     npx = sum(r.width * r.height for r in reqs)
-    dm = {k: (torch.from_numpy(w).cuda(), pi, po) for k, (w, pi, po) in models.items()}
+    dm = {k: (torch.from_numpy(w).cuda(), *shape) for k, (w, *shape) in models.items()}
     cset = ms.cvae_set(dm)
     ws = ms.workspace(ms.ms_render_workspace_size(reqs))
     direct = torch.zeros(npx, dtype=torch.float64, device="cuda")

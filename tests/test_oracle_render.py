@@ -160,7 +160,7 @@ def test_single_scattering_limit_matches_quadrature(orc):
 
 def test_sphere_mode_runs_with_models(orc):
     decs = []
-    for i, (name, (p_in, p_out)) in enumerate(synth.MODEL_SHAPES.items()):
-        decs.append((synth.xavier_decoder(100 + i, p_in, p_out).astype(np.float64), p_in, p_out))
+    for i, (name, shape) in enumerate(synth.MODEL_SHAPES.items()):
+        decs.append((synth.xavier_decoder(100 + i, *shape).astype(np.float64), *shape))
     img, st, _ = _render(orc, mode=1, sigma_t=64.0, decoders=decs)
     assert st[3] > 0 and np.all(np.isfinite(img)) and np.all(img >= 0)
