@@ -2,7 +2,7 @@
 
 1. ``generate_records``: brute-force HG walks from the centre of the unit sphere in the paper's convention
    (first event at the centre, incoming direction (0,0,1)) with per-walk media drawn like the training set
-   (optical radius log-uniform in [1,256], g U[0,0.95], albedo U[0.9,1]); the path follows the albedo-1
+   (optical radius log-uniform in [1,256], g U[-1,1), albedo U[0.9,1]); the path follows the albedo-1
    physics and the representative event is chosen with weights albedo^k (``reservoir=2``); the records are
    turned into the conditions and targets of LengthGen, PathGen and EventGen by ``ms_training_records``.
 2. ``train``: each CVAE is trained with the library's kernels: one step (mini-batch drawn on the device,

@@ -8,7 +8,7 @@ stream that each side implements on its own.
 Workloads (the shapes of the paper's experiments, Sec. 5, with synthetic stand-ins for its meshes):
 * ``walk_cfg``        65,536 photons, optical radius 8, g 0.8, albedo 0.999, isotropic start, seed 1
 * ``decoder_queries`` condition (log optical radius U[0,6], g U[0,0.95], albedo U[0.9,1], cosine U[-1,1])
-* ``training_media``  optical radius log-uniform in [1,256], g U[0,0.95], albedo U[0.9,1]
+* ``training_media``  optical radius log-uniform in [1,256], g U[-1,1), albedo U[0.9,1]
 * ``render_scene``    displaced unit sphere 0.1 sin(6x) sin(6y) sin(6z), point light, g 0.8, albedo 0.999
 * ``batch_requests``  heterogeneous render requests (resolution, spp, density, g, albedo, frequency)
 """
@@ -67,10 +67,11 @@ def walk_cfg() -> dict:
 
 
 def training_media(seed: int, n: int):
-    """Per-walk media: optical radius log-uniform in [1,256], g U[0,0.95], albedo U[0.9,1]."""
+    """Per-walk media: optical radius log-uniform in [1,256], g U[-1,1) (the anisotropy range of the paper's
+    training set, Sec. 5), albedo U[0.9,1]."""
     rng = np.random.default_rng(seed)
     tau = np.exp(rng.uniform(0.0, np.log(256.0), n))
-    g = rng.uniform(0.0, 0.95, n)
+    g = rng.uniform(-1.0, 1.0, n)
     phi = rng.uniform(0.9, 1.0, n)
     return tau, g, phi
 
