@@ -29,13 +29,14 @@ SIGMAS = (16.0, 32.0, 64.0, 128.0)
 WORKLOAD = ("render of the displaced sphere 0.1 sin(6x)sin(6y)sin(6z), point light, 512x512 px, 256 spp, "
             "sigma_t {16,32,64,128}, g 0.8, albedo 0.999, CVAE sphere tracing + NEE (trained decoders)")
 
-# Algorithmic work per counted unit (roofline of the renderer): special-function (MUFU)
-# operations per SDF distance evaluation (sqrt + 3 sin), per gradient evaluation (3 sin/cos pairs + rsqrt),
-# per sphere step (3 decoders: 32 Softplus x (exp + log) each, 10 posterior exps, 11 Box-Muller pairs x 4,
+# Algorithmic work per counted unit of the renderer's roofline: special-function (MUFU) operations per SDF
+# distance evaluation (sqrt + 3 sin), per gradient evaluation (3 sin/cos pairs + rsqrt), per sphere step
+# (the three decoders' 2 x width Softplus each, as exp + log; 10 posterior exps; 11 Box-Muller pairs x 4;
 # 3 logs) and per brute-force event (log, sin/cos, rsqrt, divide).
 MUFU_PER_SDF = 4
 MUFU_PER_GRAD = 7
-MUFU_PER_SPHERE = 3 * 32 * 2 + 10 + 11 * 4 + 3
+MUFU_PER_SPHERE = sum(2 * shape[3] * 2 for shape in (
+    (2, 1, 2, 8), (3, 3, 5, 16), (7, 6, 5, 16))) + 10 + 11 * 4 + 3      # Table 1 decoder shapes: 217
 MUFU_PER_EVENT = 5
 MUFU_PER_NEE = 4
 
