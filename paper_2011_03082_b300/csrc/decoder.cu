@@ -185,6 +185,184 @@ cudaError_t launch_infer_mma(const ms_decoder& d, const float* cond, const float
     return cudaGetLastError();
 }
 
+// ---- shape-specialised kernels (the shapes in use: the decoder benchmark's and Table 1's) ----
+// The query's row [c; z] and its eps are built in registers with compile-time indices, and rows are read and
+// written with the widest aligned vector accesses; the runtime-shaped kernels above stage them through shared
+// memory instead.
+
+template <int N>
+__device__ __forceinline__ void load_row(const float* __restrict__ src, float* v)
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k += 4) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src) + k / 4);
+            v[k] = a.x; v[k + 1] = a.y; v[k + 2] = a.z; v[k + 3] = a.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) {
+            const float2 a = __ldg(reinterpret_cast<const float2*>(src) + k / 2);
+            v[k] = a.x; v[k + 1] = a.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = __ldg(src + k);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_row(float* __restrict__ dst, const float* v)
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k += 4) reinterpret_cast<float4*>(dst)[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) reinterpret_cast<float2*>(dst)[k / 2] = make_float2(v[k], v[k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) dst[k] = v[k];
+    }
+}
+
+// x[PI .. PI+L) = z and eps[0 .. P) of query q: from z_eps [n][L+P], or normals 4j..4j+3 from counter
+// (j, id_lo, id_hi, 0xD0) with id = offset + q.
+template <int PI, int L, int P, int XN>
+__device__ __forceinline__ void query_normals(const float* __restrict__ z_eps, uint64_t seed, uint64_t id, uint64_t q,
+                                              float (&x)[XN], float (&eps)[P])
+{
+    constexpr int NZ = L + P;
+    float nz[(NZ + 3) / 4 * 4];
+    if (z_eps) {
+        load_row<NZ>(z_eps + q * NZ, nz);
+    } else {
+        const Stream st(seed, id);
+#pragma unroll
+        for (int j = 0; 4 * j < NZ; ++j) {
+            const float4 v = normals4(st, (uint32_t)j, 0xD0u);
+            nz[4 * j] = v.x; nz[4 * j + 1] = v.y; nz[4 * j + 2] = v.z; nz[4 * j + 3] = v.w;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < L; ++m) x[PI + m] = nz[m];
+#pragma unroll
+    for (int m = 0; m < P; ++m) eps[m] = nz[L + m];
+}
+
+template <int PI, int L, int P, int W>
+__global__ void __launch_bounds__(kInferThreads, 2) infer_f32_fixed(const float* __restrict__ wts,
+                                                                    const float* __restrict__ cond,
+                                                                    const float* __restrict__ z_eps, uint64_t seed,
+                                                                    uint64_t offset, uint64_t n,
+                                                                    float* __restrict__ mlv, float* __restrict__ smp)
+{
+    constexpr int IN4 = pad4(PI + L), O4 = pad4(2 * P);
+    __shared__ __align__(16) float s[smem_floats<W>(IN4, P)];
+    stage_weights<W>(s, wts, PI + L, IN4, P);
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        float x[IN4], eps[P];
+#pragma unroll
+        for (int k = 0; k < IN4; ++k) x[k] = 0.0f;
+        load_row<PI>(cond + q * PI, x);
+        query_normals<PI, L, P>(z_eps, seed, offset + q, q, x, eps);
+        float y[O4];
+        mlp<IN4, P, W>(s, x, y);
+        if (mlv) store_row<2 * P>(mlv + q * (2 * P), y);
+        if (smp) {
+            float o[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) o[k] = y[k] + __expf(0.5f * y[P + k]) * eps[k];
+            store_row<P>(smp + q * P, o);
+        }
+    }
+}
+
+template <int PI, int L, int P, int NTH, bool kBF16>
+__global__ void __launch_bounds__(kMmaThreads) infer_mma_fixed(const float* __restrict__ wts,
+                                                               const float* __restrict__ cond,
+                                                               const float* __restrict__ z_eps, uint64_t seed,
+                                                               uint64_t offset, uint64_t n, float* __restrict__ mlv,
+                                                               float* __restrict__ smp)
+{
+    constexpr int NT3 = mmadec::n_tiles_out(P);
+    __shared__ __align__(16) unsigned char wsm[mmadec::smem_bytes(P, NTH)];
+    __shared__ float stage[kMmaThreads / 32][mmadec::kStageFloats];
+    mmadec::stage_weights<kBF16, NTH>(wsm, wts, PI + L, P);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t n_chunks = (n + 31) / 32;
+    const uint64_t warps = (uint64_t)gridDim.x * (kMmaThreads / 32);
+    for (uint64_t ch = (uint64_t)blockIdx.x * (kMmaThreads / 32) + warp; ch < n_chunks; ch += warps) {
+        const uint64_t q = ch * 32 + lane;
+        const bool live = q < n;
+        float x[16], eps[P];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) eps[k] = 0.0f;
+        if (live) {
+            load_row<PI>(cond + q * PI, x);
+            query_normals<PI, L, P>(z_eps, seed, offset + q, q, x, eps);
+        }
+        float y[8 * NT3];
+        mmadec::warp_mlp<NT3, 2, kBF16, NTH>(wsm, stage[warp], x, y);
+        if (live) {
+            if (mlv) store_row<2 * P>(mlv + q * (2 * P), y);
+            if (smp) {
+                float o[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) o[k] = y[k] + __expf(0.5f * y[P + k]) * eps[k];
+                store_row<P>(smp + q * P, o);
+            }
+        }
+    }
+}
+
+template <typename K>
+cudaError_t launch_grid(K kern, int threads, uint64_t rows_per_block, uint64_t n, cudaStream_t stream,
+                        const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
+                        float* mlv, float* smp)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (n + rows_per_block - 1) / rows_per_block;
+    if (grid > need) grid = need;
+    kern<<<(unsigned)grid, threads, 0, stream>>>(d.weights, cond, z_eps, seed, offset, n, mlv, smp);
+    return cudaGetLastError();
+}
+
+// The specialised shapes: (p_in, latent, p_out, width).
+#define MS_INFER_SHAPES(X) X(4, 4, 1, 16) X(4, 4, 6, 16) X(2, 2, 1, 8) X(3, 5, 3, 16) X(7, 5, 6, 16)
+
+// Launches the specialised kernel for d's shape and precision; returns false when the shape has none, or when
+// a row pointer is not 16-byte aligned (the vector accesses need it; those calls take the runtime-shaped path).
+bool launch_fixed(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
+                  uint64_t n, float* mlv, float* smp, cudaStream_t s, cudaError_t* err)
+{
+    if (((uintptr_t)cond | (uintptr_t)z_eps | (uintptr_t)mlv | (uintptr_t)smp) & 15u) return false;
+#define MS_FIXED_CASE(pi, l, p, w)                                                                            \
+    if (d.p_in == pi && d.latent == l && d.p_out == p && d.width == w) {                                      \
+        if (d.precision == MS_FP32)                                                                            \
+            *err = launch_grid(infer_f32_fixed<pi, l, p, w>, kInferThreads, kInferThreads, n, s, d, cond, z_eps, \
+                               seed, offset, mlv, smp);                                                        \
+        else if (d.precision == MS_BF16)                                                                       \
+            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, true>, kMmaThreads, kMmaThreads, n, s, d, cond, \
+                               z_eps, seed, offset, mlv, smp);                                                 \
+        else                                                                                                   \
+            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, false>, kMmaThreads, kMmaThreads, n, s, d,      \
+                               cond, z_eps, seed, offset, mlv, smp);                                           \
+        return true;                                                                                           \
+    }
+    MS_INFER_SHAPES(MS_FIXED_CASE)
+#undef MS_FIXED_CASE
+    return false;
+}
+
 }  // namespace dec
 }  // namespace ms
 
@@ -202,6 +380,11 @@ extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const
     MS_CHECK_ARG(n == 0 || cond != nullptr, "ms_cvae_infer: cond is null");
     if (n == 0 || (out_mean_logvar == nullptr && out_sample == nullptr)) return MS_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t fe = cudaSuccess;
+    if (ms::dec::launch_fixed(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s, &fe)) {
+        MS_CUDA(fe);
+        return MS_OK;
+    }
     if (d->precision != MS_FP32) {
         MS_CUDA(ms::dec::launch_infer_mma(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s));
         return MS_OK;

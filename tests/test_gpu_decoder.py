@@ -46,18 +46,43 @@ def test_decoder_given_normals(p_in, p_out, latent, width, n):
     assert np.abs(smp - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("p_in,p_out", [(4, 1), (4, 6)])
-def test_decoder_philox_normals(orc, p_in, p_out):
+@pytest.mark.parametrize("p_in,p_out,latent,width", [(4, 1, 4, 16), (4, 6, 4, 16), (2, 1, 2, 8), (7, 6, 5, 16),
+                                                     (3, 3, 5, 16), (5, 2, 3, 16)])
+def test_decoder_philox_normals(orc, p_in, p_out, latent, width):
     n, offset = 5000, 123456
-    w = synth.xavier_decoder(7, p_in, p_out)
-    cond = synth.decoder_queries(7, n)[:, :p_in]
-    mlv, smp = _run(w, p_in, p_out, cond, n, None, seed=7, offset=offset)
-    nz = orc.decoder_normals(7, offset, n, 4 + p_out)
-    shape = cvae.Shape(p_in, p_out)
-    mu, lv = cvae.decoder_forward(w.astype(np.float64), shape, cond, nz[:, :4])
+    w = synth.xavier_decoder(7, p_in, p_out, latent, width)
+    cond = np.random.default_rng(4).uniform(-1, 2, (n, p_in)).astype(np.float32)
+    mlv, smp = _run(w, p_in, p_out, cond, n, None, seed=7, offset=offset, latent=latent, width=width)
+    nz = orc.decoder_normals(7, offset, n, latent + p_out)
+    shape = cvae.Shape(p_in, p_out, latent, width)
+    mu, lv = cvae.decoder_forward(w.astype(np.float64), shape, cond, nz[:, :latent])
     assert np.abs(mlv[:, :p_out] - mu).max() <= 1e-4
-    ref = mu + np.exp(0.5 * lv) * nz[:, 4:]
+    ref = mu + np.exp(0.5 * lv) * nz[:, latent:]
     assert np.abs(smp - ref).max() <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [ms.MS_FP32, ms.MS_FP16])
+@pytest.mark.parametrize("p_in,p_out,latent,width", [(4, 6, 4, 16), (7, 6, 5, 16), (2, 1, 2, 8)])
+def test_unaligned_rows_take_the_general_path_with_equal_results(p_in, p_out, latent, width, prec):
+    """Row pointers that are not 16-byte aligned go to the runtime-shaped kernels; they compute the same
+    arithmetic as the shape-specialised ones, so the outputs are bit-identical."""
+    n = 3000
+    w = torch.from_numpy(synth.xavier_decoder(7, p_in, p_out, latent, width)).cuda()
+    cond = np.random.default_rng(5).uniform(-1, 2, (n, p_in)).astype(np.float32)
+    d = ms.decoder_struct(w, p_in, p_out, latent, width, precision=prec)
+    outs = []
+    for shift in (0, 1):                       # shift 1: every pointer 4 bytes past a 16-byte boundary
+        cbuf = torch.zeros(n * p_in + 4, device="cuda")
+        cbuf[shift:shift + n * p_in] = torch.from_numpy(cond.ravel()).cuda()
+        mbuf = torch.zeros(n * 2 * p_out + 4, device="cuda")
+        sbuf = torch.zeros(n * p_out + 4, device="cuda")
+        c = cbuf[shift:shift + n * p_in].view(n, p_in)
+        mlv = mbuf[shift:shift + n * 2 * p_out].view(n, 2 * p_out)
+        smp = sbuf[shift:shift + n * p_out].view(n, p_out)
+        ms.ms_cvae_infer(d, c, n, seed=3, offset=9, out_mean_logvar=mlv, out_sample=smp)
+        torch.cuda.synchronize()
+        outs.append((mlv.cpu().numpy().copy(), smp.cpu().numpy().copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
 def test_decoder_full_size_sampled(orc):
