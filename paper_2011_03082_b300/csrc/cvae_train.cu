@@ -20,6 +20,7 @@
 #include <cmath>
 
 #include <cuda_bf16.h>
+#include <type_traits>
 
 #include "ms_device.cuh"
 
@@ -38,9 +39,15 @@ struct Shape {
     static constexpr int E1 = 0, e1 = E1 + kW * IE, E2 = e1 + kW, e2 = E2 + kW * kW, E3 = e2 + kW,
                          e3 = E3 + 2 * kL * kW, D1 = e3 + 2 * kL, d1 = D1 + kW * ID, D2 = d1 + kW,
                          d2 = D2 + kW * kW, D3 = d2 + kW, d3 = D3 + 2 * PO * kW, NP = d3 + 2 * PO;
-    // shared staging: per sample, the inputs and deltas of the six layers; rows of stride 17 (odd)
+    // shared staging: per sample, the inputs and deltas of the six layers; rows of stride 17 (odd), and slots
+    // SLOT floats apart (not a multiple of 32, so equal columns of different slots fall in different banks)
     static constexpr int R = 17;
+    static constexpr int SLOT = kSamples * R + 5;
     enum Slot { IN1E, H1E, H2E, IN1D, H1D, H2D, DA1E, DA2E, DOE, DA1D, DA2D, DY, NSLOT };
+    // the six weight matrices in shared memory after the slots, rows padded to a multiple of 4 (float4 loads)
+    static constexpr int P4(int k) { return (k + 3) & ~3; }
+    static constexpr int sE1 = 0, sE2 = sE1 + kW * P4(IE), sE3 = sE2 + kW * P4(kW), sD1 = sE3 + 2 * kL * P4(kW),
+                         sD2 = sD1 + kW * P4(ID), sD3 = sD2 + kW * P4(kW), SW = sD3 + 2 * PO * P4(kW);
 };
 
 __device__ __forceinline__ float sigmoidf_fast(float a) { return __fdividef(1.0f, 1.0f + __expf(-a)); }
@@ -53,29 +60,56 @@ __device__ __forceinline__ float rq(float x)
     else return x;
 }
 
+// Weights Ws: shared memory, row-major [O][K4] with K4 = K rounded up to 4 (zero padded); every lane of a warp
+// reads the same row, so each float4 load is a broadcast serving four FMAs.  Sums run over k in order.
 template <int K, int O, bool kBF16>
-__device__ __forceinline__ void fwd_layer(const float* __restrict__ Wm, const float* __restrict__ b,
+__device__ __forceinline__ void fwd_layer(const float* __restrict__ Ws, const float* __restrict__ b,
                                           const float (&x)[K], float (&a)[O])
 {
+    constexpr int K4 = (K + 3) & ~3;
 #pragma unroll
     for (int o = 0; o < O; ++o) {
         float acc = __ldg(b + o);
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc = fmaf(rq<kBF16>(__ldg(Wm + o * K + k)), x[k], acc);
+        for (int k = 0; k < K4; k += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(Ws + o * K4 + k);
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (k + j < K) acc = fmaf(rq<kBF16>(wv[j]), x[k + j], acc);
+        }
         a[o] = acc;
     }
 }
 
 // dx = W^T da
 template <int K, int O, bool kBF16>
-__device__ __forceinline__ void bwd_layer(const float* __restrict__ Wm, const float (&da)[O], float (&dx)[K])
+__device__ __forceinline__ void bwd_layer(const float* __restrict__ Ws, const float (&da)[O], float (&dx)[K])
 {
+    constexpr int K4 = (K + 3) & ~3;
 #pragma unroll
     for (int k = 0; k < K; ++k) dx[k] = 0.0f;
 #pragma unroll
     for (int o = 0; o < O; ++o)
 #pragma unroll
-        for (int k = 0; k < K; ++k) dx[k] = fmaf(rq<kBF16>(__ldg(Wm + o * K + k)), da[o], dx[k]);
+        for (int k = 0; k < K4; k += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(Ws + o * K4 + k);
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (k + j < K) dx[k + j] = fmaf(rq<kBF16>(wv[j]), da[o], dx[k + j]);
+        }
+}
+
+// Copies one [O][K] weight matrix into the padded shared layout.
+template <int O, int K>
+__device__ __forceinline__ void stage_matrix(float* __restrict__ dst, const float* __restrict__ src)
+{
+    constexpr int K4 = (K + 3) & ~3;
+    for (int i = threadIdx.x; i < O * K4; i += blockDim.x) {
+        const int o = i / K4, k = i - o * K4;
+        dst[i] = k < K ? src[o * K + k] : 0.0f;
+    }
 }
 
 template <int PI, int PO, int kW, int kL, bool kBF16>
@@ -89,9 +123,17 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     const int t = threadIdx.x;
     const uint64_t b = (uint64_t)blockIdx.x * kSamples + t;
     const bool live = b < B;
-    float* row_base = sm;   // [NSLOT][kSamples][R]
-    auto row = [&](int slot, int s) -> float* { return row_base + ((size_t)slot * kSamples + s) * S::R; };
+    float* row_base = sm;   // [NSLOT][SLOT]: sample s of a slot at s * R
+    auto row = [&](int slot, int s) -> float* { return row_base + (size_t)slot * S::SLOT + (size_t)s * S::R; };
     __shared__ float s_rec[kSamples / 32], s_kl[kSamples / 32];
+    float* ws = sm + S::NSLOT * S::SLOT;    // padded weight matrices
+    stage_matrix<kW, S::IE>(ws + S::sE1, prm + S::E1);
+    stage_matrix<kW, kW>(ws + S::sE2, prm + S::E2);
+    stage_matrix<2 * kL, kW>(ws + S::sE3, prm + S::E3);
+    stage_matrix<kW, S::ID>(ws + S::sD1, prm + S::D1);
+    stage_matrix<kW, kW>(ws + S::sD2, prm + S::D2);
+    stage_matrix<2 * PO, kW>(ws + S::sD3, prm + S::D3);
+    __syncthreads();
 
     // ---------------- forward ----------------
     float xin[S::IE], c[PI], x[PO];
@@ -121,13 +163,13 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
         }
     }
     float a1e[kW], h1e[kW], a2e[kW], h2e[kW], oe[2 * kL];
-    fwd_layer<S::IE, kW, kBF16>(prm + S::E1, prm + S::e1, xin, a1e);
+    fwd_layer<S::IE, kW, kBF16>(ws + S::sE1, prm + S::e1, xin, a1e);
 #pragma unroll
     for (int o = 0; o < kW; ++o) h1e[o] = rq<kBF16>(softplus(a1e[o]));
-    fwd_layer<kW, kW, kBF16>(prm + S::E2, prm + S::e2, h1e, a2e);
+    fwd_layer<kW, kW, kBF16>(ws + S::sE2, prm + S::e2, h1e, a2e);
 #pragma unroll
     for (int o = 0; o < kW; ++o) h2e[o] = rq<kBF16>(softplus(a2e[o]));
-    fwd_layer<kW, 2 * kL, kBF16>(prm + S::E3, prm + S::e3, h2e, oe);
+    fwd_layer<kW, 2 * kL, kBF16>(ws + S::sE3, prm + S::e3, h2e, oe);
     float sd_e[kL], z[kL];
 #pragma unroll
     for (int l = 0; l < kL; ++l) {
@@ -140,13 +182,13 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
 #pragma unroll
     for (int l = 0; l < kL; ++l) din[PI + l] = rq<kBF16>(z[l]);
     float a1d[kW], h1d[kW], a2d[kW], h2d[kW], y[2 * PO];
-    fwd_layer<S::ID, kW, kBF16>(prm + S::D1, prm + S::d1, din, a1d);
+    fwd_layer<S::ID, kW, kBF16>(ws + S::sD1, prm + S::d1, din, a1d);
 #pragma unroll
     for (int o = 0; o < kW; ++o) h1d[o] = rq<kBF16>(softplus(a1d[o]));
-    fwd_layer<kW, kW, kBF16>(prm + S::D2, prm + S::d2, h1d, a2d);
+    fwd_layer<kW, kW, kBF16>(ws + S::sD2, prm + S::d2, h1d, a2d);
 #pragma unroll
     for (int o = 0; o < kW; ++o) h2d[o] = rq<kBF16>(softplus(a2d[o]));
-    fwd_layer<kW, 2 * PO, kBF16>(prm + S::D3, prm + S::d3, h2d, y);
+    fwd_layer<kW, 2 * PO, kBF16>(ws + S::sD3, prm + S::d3, h2d, y);
 
     const float invB = 1.0f / (float)B;
     float rec = 0.0f, kl = 0.0f;
@@ -164,13 +206,13 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
 
     // ---------------- backward ----------------
     float dh[kW], da2d[kW], da1d[kW], ddin[S::ID];
-    bwd_layer<kW, 2 * PO, kBF16>(prm + S::D3, dy, dh);
+    bwd_layer<kW, 2 * PO, kBF16>(ws + S::sD3, dy, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da2d[o] = dh[o] * sigmoidf_fast(a2d[o]);
-    bwd_layer<kW, kW, kBF16>(prm + S::D2, da2d, dh);
+    bwd_layer<kW, kW, kBF16>(ws + S::sD2, da2d, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da1d[o] = dh[o] * sigmoidf_fast(a1d[o]);
-    bwd_layer<S::ID, kW, kBF16>(prm + S::D1, da1d, ddin);
+    bwd_layer<S::ID, kW, kBF16>(ws + S::sD1, da1d, ddin);
     float doe[2 * kL];
 #pragma unroll
     for (int l = 0; l < kL; ++l) {
@@ -179,10 +221,10 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
         doe[kL + l] = live ? dz * eps[l] * 0.5f * sd_e[l] + 0.5f * (sd_e[l] * sd_e[l] - 1.0f) * invB : 0.0f;
     }
     float da2e[kW], da1e[kW];
-    bwd_layer<kW, 2 * kL, kBF16>(prm + S::E3, doe, dh);
+    bwd_layer<kW, 2 * kL, kBF16>(ws + S::sE3, doe, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da2e[o] = dh[o] * sigmoidf_fast(a2e[o]);
-    bwd_layer<kW, kW, kBF16>(prm + S::E2, da2e, dh);
+    bwd_layer<kW, kW, kBF16>(ws + S::sE2, da2e, dh);
 #pragma unroll
     for (int o = 0; o < kW; ++o) da1e[o] = dh[o] * sigmoidf_fast(a1e[o]);
 
@@ -218,37 +260,75 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     if ((t & 31) == 0) { s_rec[t >> 5] = rec; s_kl[t >> 5] = kl; }
     __syncthreads();
 
-    // ---------------- block gradient: one thread per parameter, samples in order ----------------
+    // ---------------- block gradient: 4 x 4 register tiles, samples in order ----------------
+    // Work items: per layer, the ceil(O/4) x ceil(K/4) tiles of dW = sum_s delta_s x_s^T and the ceil(O/4) 4-wide
+    // tiles of db = sum_s delta_s.  Each parameter is summed over the block's samples in sample order (one FMA or
+    // add per sample), exactly as a one-thread-per-parameter loop would.  Tile entries past O or K read row
+    // padding and are not stored.
     float* out = partial + (size_t)blockIdx.x * (S::NP + 2);
-    for (int p = t; p < S::NP; p += kSamples) {
-        int dslot, islot, K, base, O;
-        if (p < S::e1) { dslot = S::DA1E; islot = S::IN1E; K = S::IE; base = S::E1; O = kW; }
-        else if (p < S::E2) { dslot = S::DA1E; islot = -1; K = 1; base = S::e1; O = kW; }
-        else if (p < S::e2) { dslot = S::DA2E; islot = S::H1E; K = kW; base = S::E2; O = kW; }
-        else if (p < S::E3) { dslot = S::DA2E; islot = -1; K = 1; base = S::e2; O = kW; }
-        else if (p < S::e3) { dslot = S::DOE; islot = S::H2E; K = kW; base = S::E3; O = 2 * kL; }
-        else if (p < S::D1) { dslot = S::DOE; islot = -1; K = 1; base = S::e3; O = 2 * kL; }
-        else if (p < S::d1) { dslot = S::DA1D; islot = S::IN1D; K = S::ID; base = S::D1; O = kW; }
-        else if (p < S::D2) { dslot = S::DA1D; islot = -1; K = 1; base = S::d1; O = kW; }
-        else if (p < S::d2) { dslot = S::DA2D; islot = S::H1D; K = kW; base = S::D2; O = kW; }
-        else if (p < S::D3) { dslot = S::DA2D; islot = -1; K = 1; base = S::d2; O = kW; }
-        else if (p < S::d3) { dslot = S::DY; islot = S::H2D; K = kW; base = S::D3; O = 2 * PO; }
-        else { dslot = S::DY; islot = -1; K = 1; base = S::d3; O = 2 * PO; }
-        (void)O;
-        const int q = p - base;
-        const int o = islot >= 0 ? q / K : q;
-        const int k = islot >= 0 ? q - o * K : 0;
-        const float* dcol = row(dslot, 0) + o;
-        float acc = 0.0f;
-        if (islot >= 0) {
-            const float* icol = row(islot, 0) + k;
-#pragma unroll 8
-            for (int s = 0; s < kSamples; ++s) acc = fmaf(dcol[s * S::R], icol[s * S::R], acc);
+    auto tiles = [&](auto O_, auto K_, int dslot, int islot, int bW, int bb, int item) {
+        constexpr int O = decltype(O_)::value, K = decltype(K_)::value;
+        constexpr int TO = (O + 3) / 4, TK = (K + 3) / 4;
+        const float* dr = row(dslot, 0);
+        if (item < TO * TK) {
+            const int o0 = 4 * (item / TK), k0 = 4 * (item % TK);
+            const float* xr = row(islot, 0) + k0;
+            dr += o0;
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+            for (int smp = 0; smp < kSamples; ++smp) {
+                const float* d = dr + smp * S::R;
+                const float* x = xr + smp * S::R;
+                const float d4[4] = {d[0], d[1], d[2], d[3]}, x4[4] = {x[0], x[1], x[2], x[3]};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(d4[i], x4[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (o0 + i < O && k0 + j < K) out[bW + (o0 + i) * K + k0 + j] = acc[i][j];
         } else {
-#pragma unroll 8
-            for (int s = 0; s < kSamples; ++s) acc += dcol[s * S::R];
+            const int o0 = 4 * (item - TO * TK);
+            dr += o0;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+            for (int smp = 0; smp < kSamples; ++smp) {
+                const float* d = dr + smp * S::R;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += d[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (o0 + i < O) out[bb + o0 + i] = acc[i];
         }
-        out[p] = acc;
+    };
+    using IE = std::integral_constant<int, S::IE>;
+    using ID = std::integral_constant<int, S::ID>;
+    using W_ = std::integral_constant<int, kW>;
+    using L2 = std::integral_constant<int, 2 * kL>;
+    using P2 = std::integral_constant<int, 2 * PO>;
+    auto n_items = [](int O, int K) { return ((O + 3) / 4) * ((K + 3) / 4) + (O + 3) / 4; };
+    constexpr int T1 = ((kW + 3) / 4) * ((S::IE + 3) / 4) + (kW + 3) / 4;
+    constexpr int T2 = ((kW + 3) / 4) * ((kW + 3) / 4) + (kW + 3) / 4;
+    constexpr int T3 = ((2 * kL + 3) / 4) * ((kW + 3) / 4) + (2 * kL + 3) / 4;
+    constexpr int T4 = ((kW + 3) / 4) * ((S::ID + 3) / 4) + (kW + 3) / 4;
+    constexpr int T6 = ((2 * PO + 3) / 4) * ((kW + 3) / 4) + (2 * PO + 3) / 4;
+    constexpr int B1 = T1, B2 = B1 + T2, B3 = B2 + T3, B4 = B3 + T4, B5 = B4 + T2, B6 = B5 + T6;
+    (void)n_items;
+    for (int it = t; it < B6; it += kSamples) {
+        if (it < B1) tiles(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1, it);
+        else if (it < B2) tiles(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2, it - B1);
+        else if (it < B3) tiles(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3, it - B2);
+        else if (it < B4) tiles(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1, it - B3);
+        else if (it < B5) tiles(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2, it - B4);
+        else tiles(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3, it - B5);
     }
     if (t == 0) {
         float r = 0.0f, k = 0.0f;
@@ -258,18 +338,33 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     }
 }
 
-// grad[p] = sum over blocks of partial[blk][p] in block order; loss3 = (rec + kl, rec, kl) / B.
-__global__ void reduce_partials(const float* __restrict__ partial, int nblk, int np, uint64_t B,
-                                float* __restrict__ grad, float* __restrict__ loss3)
+// grad[p] = sum over blocks of partial[blk][p]; loss3 = (rec + kl, rec, kl) / B.  A block handles 32 consecutive
+// entries (one per lane); its warp w adds rows w, w + 8, w + 16, ... in that order, and the eight warp sums are
+// then added in warp order, so the result does not depend on scheduling (bit-reproducible).
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials(const float* __restrict__ partial, int nblk,
+                                                                     int np, uint64_t B, float* __restrict__ grad,
+                                                                     float* __restrict__ loss3)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np + 2) return;
+    __shared__ float s_sum[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
     float acc = 0.0f;
-    for (int blk = 0; blk < nblk; ++blk) acc += partial[(size_t)blk * (np + 2) + p];
+    if (p < np + 2) {
+#pragma unroll 8
+        for (int blk = w; blk < nblk; blk += kReduceWarps) acc += __ldg(partial + (size_t)blk * (np + 2) + p);
+    }
+    s_sum[w][lane] = acc;
+    __syncthreads();
+    if (w != 0 || p >= np + 2) return;
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kReduceWarps; ++k) t += s_sum[k][lane];
     if (p < np) {
-        if (grad) grad[p] = acc;
+        if (grad) grad[p] = t;
     } else if (loss3) {
-        const float v = acc / (float)B;
+        const float v = t / (float)B;
         if (p == np) { loss3[1] = v; } else { loss3[2] = v; }
     }
 }
@@ -357,7 +452,7 @@ cudaError_t launch_fb(const float* prm, const float* X, const float* C, const fl
                       uint64_t step, float* partial, cudaStream_t s)
 {
     using S = Shape<PI, PO, W, L>;
-    const size_t smem = (size_t)S::NSLOT * kSamples * S::R * sizeof(float);
+    const size_t smem = ((size_t)S::NSLOT * S::SLOT + S::SW) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO, W, L, kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -442,7 +537,7 @@ extern "C" ms_status ms_cvae_forward_backward(const ms_cvae_shape* s, const floa
     const int nblk = (int)((B + kSamples - 1) / kSamples);
     MS_CUDA(pl.launch(params, x, c, eps_z, B, seed, step, partial, cs));
     const int n = pl.np + 2;
-    reduce_partials<<<(n + 127) / 128, 128, 0, cs>>>(partial, nblk, pl.np, B, grad, loss3);
+    reduce_partials<<<(n + 31) / 32, 32 * kReduceWarps, 0, cs>>>(partial, nblk, pl.np, B, grad, loss3);
     MS_CUDA(cudaGetLastError());
     finish_loss<<<1, 32, 0, cs>>>(loss3);
     MS_CUDA(cudaGetLastError());
