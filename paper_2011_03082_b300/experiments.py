@@ -13,6 +13,14 @@ error of the smallest ladder run, the speed-up is bounded above by that run, and
 
 ``python -m paper_2011_03082_b300.experiments [--res 128] [--ref-spp 8192] [--st-spp 256]``, and
 ``python -m paper_2011_03082_b300.experiments --batched [--scale 0.25]`` for the 64-request batch.
+
+Two further studies:
+
+* ``--absorption``: the absorption experiment of Sec. 5 (Fig. 8).  RGB media with absorption 1 - phi of
+  (2e-3, 2e-4, 2e-3), doubled between settings; each colour channel is one request of a three-request batch with
+  a shared seed, rendered by sphere tracing and by brute force, timed with CUDA events.
+* ``--fallback``: the sphere / brute-force threshold (the minimum optical radius sigma_t r of a sphere step, the
+  thin-region fallback of Sec. 6): render time and RMSE against a brute-force reference for several thresholds.
 """
 from __future__ import annotations
 
@@ -124,6 +132,61 @@ def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None):
                 sequential_seconds=a.elapsed_time(b) / 1e3)
 
 
+def _render_batch(reqs: list, cset, variant=0):
+    reqs = [ms.render_params(dict(r, variant=variant)) for r in reqs]
+    npx = sum(r.width * r.height for r in reqs)
+    img = torch.zeros(npx, dtype=torch.float64, device="cuda")
+    st = torch.zeros(len(reqs), ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    ws = ms.workspace(ms.ms_render_workspace_size(reqs))
+    learned = any(r.mode == ms.MS_SPHERE for r in reqs)
+    ms.ms_render_batch(reqs, cset if learned else None, img, st, ws=ws)       # warm-up
+    img.zero_()
+    st.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ms.ms_render_batch(reqs, cset if learned else None, img, st, ws=ws)
+    b.record()
+    b.synchronize()
+    return img.cpu().numpy(), st.cpu().numpy(), a.elapsed_time(b) / 1e3
+
+
+def absorption_sweep(sigma=64.0, res=256, spp=64, settings=6, cset=None, variant=0):
+    """Render time of both methods against absorption: RGB absorption (2e-3, 2e-4, 2e-3) x 2^i, i < settings."""
+    if cset is None:
+        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    out = []
+    for i in range(settings):
+        absorb = [a * 2.0 ** i for a in (2e-3, 2e-4, 2e-3)]
+        row = dict(absorption_rgb=absorb)
+        for mode, name in ((ms.MS_SPHERE, "sphere"), (ms.MS_BRUTE, "brute")):
+            reqs = [synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode, seed=7, albedo=1.0 - a)
+                    for a in absorb]
+            img, st, t = _render_batch(reqs, cset, variant)
+            paths = 3 * res * res * spp
+            row[name] = dict(seconds=t, paths_per_s=paths / t, mean_rgb=[float(img[k * res * res:(k + 1) * res * res].mean()
+                                                                            / spp) for k in range(3)],
+                             steps_per_path=float(st[:, 4].sum() + st[:, 3].sum()) / paths)
+        row["speedup"] = row["brute"]["seconds"] / row["sphere"]["seconds"]
+        out.append(row)
+    return out
+
+
+def fallback_sweep(sigma=64.0, res=128, spp=256, ref_spp=8192, tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None,
+                   variant=0):
+    """Render time and RMSE against a brute-force reference for several minimum optical radii of a sphere step."""
+    if cset is None:
+        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    base = synth.render_scene(sigma, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101)
+    ref, _ = _render(base, cset, variant)
+    out = []
+    for tm in tau_mins:
+        img, t = _render(dict(base, mode=ms.MS_SPHERE, spp=spp, seed=202, min_optical_radius=tm), cset, variant)
+        out.append(dict(tau_min=tm, seconds=t, rmse=float(np.sqrt(np.mean((img - ref) ** 2)))))
+    bf, t_bf = _render(dict(base, spp=spp, seed=303), cset, variant)
+    out.append(dict(tau_min=None, mode="brute force", seconds=t_bf, rmse=float(np.sqrt(np.mean((bf - ref) ** 2)))))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--res", type=int, default=128)
@@ -131,9 +194,19 @@ def main(argv=None):
     ap.add_argument("--st-spp", type=int, default=256)
     ap.add_argument("--batched", action="store_true", help="run the 64-request batch instead")
     ap.add_argument("--scale", type=float, default=0.25)
+    ap.add_argument("--absorption", action="store_true", help="run the absorption sweep instead")
+    ap.add_argument("--fallback", action="store_true", help="run the fallback-threshold sweep instead")
     a = ap.parse_args(argv)
     if a.batched:
         print(json.dumps(batched(scale=a.scale)))
+        return
+    if a.absorption:
+        for r in absorption_sweep():
+            print(json.dumps(r))
+        return
+    if a.fallback:
+        for r in fallback_sweep():
+            print(json.dumps(r))
         return
     for r in equal_rmse(res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp):
         print(json.dumps(r))
