@@ -238,8 +238,24 @@ typedef struct {
     uint64_t seed, sample_offset;
     int32_t variant;            /* kernel variant (scheduling constants), 0..ms_render_variants()-1, 0 by
                                    default; in a batch the first request's variant is used           */
-    int32_t reserved_;
+    int32_t sdf_grid_n;         /* 0, or the n of sdf_grid                                              */
+    const float* sdf_grid;      /* NULL, or device [n][n][n] from ms_sdf_grid_build(disp_amp, disp_freq, n):
+                                   a sphere step's radius is then the larger of the distance bound and
+                                   the value of the grid voxel holding the collision point             */
 } ms_render_params;
+
+/* The voxel grid of conservative distances that sizes sphere steps (Sec. 3: the bounding volume is voxelised
+ * in a pre-process, each voxel holding a conservative shortest Chebyshev distance to the surface).  grid:
+ * device [n][n][n] floats, index (iz * n + iy) * n + ix; with h = 2 (1 + disp_amp) / (n - 2) and
+ * b = 1 + disp_amp + h, voxel (ix, iy, iz) is the cube [-b + ix h, -b + (ix + 1) h] x ... (one voxel of
+ * margin around the bounding sphere).  A voxel may hold surface if |f(c)| <= (1 + A k) h sqrt(3) / 2 at its
+ * centre c; every voxel's value is (m - 1) h, clamped at 0, with m its Chebyshev (L-infinity) index distance
+ * to the nearest such voxel — a lower bound of the distance from each of its points to the surface.
+ * workspace: device, 16-byte aligned, ms_sdf_grid_workspace_size(n) bytes (two integer grids).
+ * n in 4..1024, 0 <= disp_amp < 1.  Asynchronous on `stream` (n + 2 kernel launches). */
+size_t ms_sdf_grid_workspace_size(int32_t n);
+ms_status ms_sdf_grid_build(float disp_amp, float disp_freq, int32_t n, float* grid, void* workspace,
+                            size_t workspace_bytes, void* stream);
 
 /* The renderer's three decoders have the final shapes of Table 1 (the paper's D = 2 hidden layers):
  * LengthGen latent 2 width 8, PathGen latent 5 width 16, EventGen latent 5 width 16, all MS_FP32.  A sphere

@@ -63,9 +63,9 @@ class RenderParams(C.Structure):
                 ("light_pos", C.c_double * 3), ("light_I", C.c_double),
                 ("sigma_t", C.c_double), ("g", C.c_double), ("albedo", C.c_double),
                 ("disp_amp", C.c_double), ("disp_freq", C.c_double),
-                ("mode", C.c_int32), ("pad_", C.c_int32),
+                ("mode", C.c_int32), ("sdf_grid_n", C.c_int32),
                 ("min_optical_radius", C.c_double), ("max_optical_radius", C.c_double),
-                ("seed", C.c_uint64), ("sample_offset", C.c_uint64)]
+                ("seed", C.c_uint64), ("sample_offset", C.c_uint64), ("sdf_grid", C.c_void_p)]
 
 
 def lib():
@@ -212,11 +212,18 @@ def render(params: dict, decoders=None, n_threads=0):
     Returns (image_sum[h][w], stats[16], threads)."""
     P = RenderParams()
     for k, v in params.items():
+        if k == "sdf_grid":
+            continue            # the oracle builds its own grid (sdf_grid_n); never take a device pointer
         if isinstance(getattr(P, k), C.Array):
             setattr(P, k, type(getattr(P, k))(*[float(t) for t in v]))
         else:
             setattr(P, k, v)
     keep = []
+    if params.get("sdf_grid_n", 0) and params.get("mode", 0) == 1:
+        g, _, _ = sdf_grid(P.disp_amp, P.disp_freq, int(params["sdf_grid_n"]))
+        g = np.ascontiguousarray(g)
+        keep.append(g)
+        P.sdf_grid = g.ctypes.data
     decs = (Decoder * 3)()
     if decoders is not None:
         for i, dd in enumerate(decoders):
@@ -245,6 +252,28 @@ def inside_length(A, k, X, xl):
     X = np.ascontiguousarray(X, np.float64)
     xl = np.ascontiguousarray(xl, np.float64)
     return lib().om_inside_length(A, k, _ptr(X), _ptr(xl))
+
+
+def sdf_grid(A, k, n):
+    """Voxel grid of conservative distances to the displaced sphere (Sec. 3: the bounding volume voxelised in a
+    pre-process, each voxel holding a conservative shortest distance to the surface).  The cube [-b, b]^3,
+    h = 2 (1 + A) / (n - 2), b = 1 + A + h, in n^3 voxels (index [iz][iy][ix]):
+      1. a voxel may hold surface if |f(c)| <= (1 + A k) h sqrt(3) / 2 at its centre c (f's Lipschitz constant
+         is 1 + A k, and no point of the voxel is farther than h sqrt(3) / 2 from c);
+      2. e = the Euclidean distance, in voxels, from each voxel's centre to the nearest such voxel's centre
+         (scipy's exact Euclidean distance transform);
+      3. value = (e - sqrt(3)) h, at least 0 (points of two voxels are at most one diagonal nearer than their
+         centres).
+    Returns (grid, b, h)."""
+    from scipy import ndimage
+    h = 2.0 * (1.0 + A) / (n - 2)
+    b = 1.0 + A + h
+    c = -b + (np.arange(n) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    f = np.sqrt(x * x + y * y + z * z) - 1.0 - A * np.sin(k * x) * np.sin(k * y) * np.sin(k * z)
+    may_hold = np.abs(f) <= (1.0 + A * k) * (np.sqrt(3.0) / 2.0) * h
+    e = ndimage.distance_transform_edt(~may_hold)
+    return np.maximum(0.0, (e - np.sqrt(3.0)) * h), b, h
 
 
 def ray_crossing(A, k, p, w):

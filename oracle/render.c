@@ -47,14 +47,18 @@ typedef struct {
     double sigma_t, g, albedo;
     double disp_amp, disp_freq;
     int32_t mode;              /* 0 brute force, 1 sphere tracing */
-    int32_t pad_;
+    int32_t sdf_grid_n;        /* 0, or n: sphere radii also from an n^3 voxel grid of conservative distances */
     double min_optical_radius, max_optical_radius;
     uint64_t seed, sample_offset;
+    const double* sdf_grid;    /* sdf_grid_n^3 voxel values (index (iz n + iy) n + ix) over [-b, b]^3, voxel side
+                                  h = 2 (1 + A) / (n - 2), b = 1 + A + h; each a lower bound of the distance from
+                                  the voxel's points to the surface (built by the Python side of the oracle) */
 } om_render_params;
 
 typedef struct {
     const om_render_params* P;
     const om_decoder* dec;     /* [3]: LengthGen, PathGen, EventGen (NULL in brute force) */
+    const double* grid;        /* the voxel grid (sdf_grid_n > 0), else NULL */
     double* image;
     uint64_t* stats;
     int next_row;
@@ -70,7 +74,12 @@ static ov3 cross(ov3 a, ov3 b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.
 static ov3 normalize(ov3 a) { return mul(a, 1.0 / sqrt(dot(a, a))); }
 
 /* ---- scene: displaced unit sphere f(p) = |p| - 1 - A sin(kx) sin(ky) sin(kz), negative inside ---- */
-typedef struct { double A, k, lip, rb2; } scene;
+typedef struct {
+    double A, k, lip, rb2;
+    const double* grid;        /* voxel grid of conservative distances (NULL: none), n^3, index (iz n + iy) n + ix */
+    int gn;
+    double gb, gh;             /* the grid covers [-gb, gb]^3 in voxels of side gh */
+} scene;
 
 static _Thread_local uint64_t t_sdf_evals, t_grad_evals;
 
@@ -331,6 +340,18 @@ static ov3 scatter_dir(ov3 w, double mu, double u)
 }
 
 /* Next-event estimate toward the point light from X, arriving with direction W (Eq. 5 term). */
+/* The grid value of the voxel holding p (the voxel index clamped to the grid). */
+static double grid_value(const scene* S, ov3 p)
+{
+    int i[3];
+    double c[3] = { p.x, p.y, p.z };
+    for (int a = 0; a < 3; ++a) {
+        int v = (int)floor((c[a] + S->gb) / S->gh);
+        i[a] = v < 0 ? 0 : (v > S->gn - 1 ? S->gn - 1 : v);
+    }
+    return S->grid[((size_t)i[2] * S->gn + i[1]) * S->gn + i[0]];
+}
+
 static double nee(const scene* S, const om_render_params* P, ov3 X, ov3 W, double weight, uint64_t* st)
 {
     ov3 xl = v3(P->light_pos[0], P->light_pos[1], P->light_pos[2]);
@@ -407,6 +428,8 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
         }
         if (P->mode == 1) {
             double d = -sdf(S, c) / S->lip;
+            if (S->grid)
+                d = fmax(d, grid_value(S, c));
             double r = fmin(d, P->max_optical_radius / sig);
             double tau = sig * r;
             if (tau >= P->min_optical_radius) {
@@ -500,6 +523,10 @@ static void* render_worker(void* arg)
     S.lip = 1.0 + P->disp_amp * P->disp_freq;
     double rb = 1.0 + P->disp_amp + 1e-3;
     S.rb2 = rb * rb;
+    S.grid = J->grid;
+    S.gn = P->sdf_grid_n;
+    S.gh = S.grid ? 2.0 * (1.0 + S.A) / (double)(S.gn - 2) : 0.0;
+    S.gb = 1.0 + S.A + S.gh;
     uint64_t st[16] = { 0 };
     t_sdf_evals = 0;
     t_grad_evals = 0;
@@ -540,9 +567,15 @@ int om_render(const om_render_params* P, const om_decoder* dec3, double* image, 
         }
         if (used > 24) return -1;   /* a sphere step draws 24 normals */
     }
+    const double* grid = NULL;
+    if (P->mode == 1 && P->sdf_grid_n > 0) {
+        if (P->sdf_grid_n < 4 || P->disp_amp >= 1.0 || !P->sdf_grid) return -1;
+        grid = P->sdf_grid;
+    }
     render_job J;
     J.P = P;
     J.dec = dec3;
+    J.grid = grid;
     J.image = image;
     J.stats = stats;
     J.next_row = 0;

@@ -42,6 +42,9 @@ struct Req {
     float light[3], I;
     float sigma, g, phi, log_phi, A, k, lip, inv_lip, rb2;
     float tau_min, tau_max;
+    const float* grid;               // voxel grid of conservative distances, or null
+    int32_t grid_n;
+    float grid_b, grid_inv_h;
     int32_t W, H, mode;
     uint32_t spp, max_segments;
     uint64_t seed, sample_offset, image_offset, samples_begin;
@@ -428,7 +431,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                     const V c = mo + md * ml;
                     bool sphere = false;
                     if (q.mode == MS_SPHERE && learned) {
-                        const float dc = -sdf(geo, c) * geo.inv_lip;
+                        float dc = -sdf(geo, c) * geo.inv_lip;
+                        if (q.grid) {
+                            // the voxel holding c: its value bounds the distance from every point of the voxel
+                            const int n1 = q.grid_n - 1;
+                            const int ix = min(max((int)((c.x + q.grid_b) * q.grid_inv_h), 0), n1);
+                            const int iy = min(max((int)((c.y + q.grid_b) * q.grid_inv_h), 0), n1);
+                            const int iz = min(max((int)((c.z + q.grid_b) * q.grid_inv_h), 0), n1);
+                            dc = fmaxf(dc, __ldg(q.grid + ((size_t)iz * q.grid_n + iy) * q.grid_n + ix));
+                        }
                         cnt[8] += 1u;
                         rad = fminf(dc, q.tau_max / q.sigma);
                         tau = q.sigma * rad;
@@ -633,6 +644,19 @@ static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const
         q.rb2 = rb * rb;
         q.tau_min = p.min_optical_radius;
         q.tau_max = p.max_optical_radius;
+        if (p.sdf_grid != nullptr) {
+            if (p.sdf_grid_n < 4 || p.sdf_grid_n > 1024 || !(p.disp_amp < 1.0f))
+                return ms::set_error(MS_ERR_INVALID_ARG, "%s: request %d: sdf_grid_n must be in 4..1024", fn, i);
+            const float h = 2.0f * (1.0f + p.disp_amp) / (float)(p.sdf_grid_n - 2);
+            q.grid = p.sdf_grid;
+            q.grid_n = p.sdf_grid_n;
+            q.grid_b = 1.0f + p.disp_amp + h;
+            q.grid_inv_h = 1.0f / h;
+        } else {
+            q.grid = nullptr;
+            q.grid_n = 0;
+            q.grid_b = q.grid_inv_h = 0.0f;
+        }
         q.W = p.width;
         q.H = p.height;
         q.mode = p.mode;

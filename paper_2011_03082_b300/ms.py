@@ -26,7 +26,8 @@ EXPORTS = ("ms_last_error", "ms_version", "ms_walk_workspace_size", "ms_simulate
            "ms_cvae_num_params", "ms_cvae_workspace_size", "ms_cvae_forward_backward", "ms_adam_step",
            "ms_cvae_train_step", "ms_cvae_train_step_dev_workspace_size", "ms_cvae_train_step_dev",
            "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records", "ms_render_workspace_size", "ms_render",
-           "ms_render_batch", "ms_render_variants", "ms_render_variant_info", "ms_render_autotune")
+           "ms_render_batch", "ms_render_variants", "ms_render_variant_info", "ms_render_autotune",
+           "ms_sdf_grid_workspace_size", "ms_sdf_grid_build")
 
 
 class MsError(RuntimeError):
@@ -72,7 +73,7 @@ class RenderParams(C.Structure):
                 ("disp_amp", C.c_float), ("disp_freq", C.c_float), ("mode", C.c_int32),
                 ("min_optical_radius", C.c_float), ("max_optical_radius", C.c_float),
                 ("seed", C.c_uint64), ("sample_offset", C.c_uint64), ("variant", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("sdf_grid_n", C.c_int32), ("sdf_grid", C.c_void_p)]
 
 
 class CvaeSet(C.Structure):
@@ -108,6 +109,8 @@ def lib():
         "ms_cvae_train_step_static": ([P, P, P, P, P, P, P, U64, U64, U64, F, F, P, P], C.c_int),
         "ms_training_records": ([U64, P, P, P, P, P, P, I32, U64, P, P, P, P, P, P, P], C.c_int),
         "ms_render_workspace_size": ([P, C.c_int], C.c_size_t),
+        "ms_sdf_grid_workspace_size": ([I32], C.c_size_t),
+        "ms_sdf_grid_build": ([C.c_float, C.c_float, I32, P, P, C.c_size_t, P], C.c_int),
         "ms_render": ([P, P, P, P, P, C.c_size_t, P], C.c_int),
         "ms_render_batch": ([P, C.c_int, P, P, P, P, C.c_size_t, P], C.c_int),
         "ms_render_variants": ([], C.c_int),
@@ -256,6 +259,19 @@ def ms_cvae_train_step_static(shape, params, m, v, x, c, B, *, eps_z=None, seed=
     return _check(lib().ms_cvae_train_step_static(C.byref(shape), _ptr(params), _ptr(m), _ptr(v), _ptr(x), _ptr(c),
                                                   _ptr(eps_z), B, seed, step, lr, weight_decay, _ptr(loss3),
                                                   _stream(stream)), "ms_cvae_train_step_static")
+
+
+def ms_sdf_grid_build(disp_amp, disp_freq, n, device="cuda", stream=None) -> torch.Tensor:
+    """The n^3 voxel grid of conservative distances for a request's displaced sphere (device float32 [n][n][n]);
+    pass it as ``sdf_grid=grid.data_ptr(), sdf_grid_n=n`` in the render parameters (and keep it alive)."""
+    g = torch.empty(n, n, n, dtype=torch.float32, device=device)
+    nb = int(lib().ms_sdf_grid_workspace_size(n))
+    ws = torch.empty(nb // 4 + 4, dtype=torch.int32, device=device)
+    _check(lib().ms_sdf_grid_build(disp_amp, disp_freq, n, _ptr(g), _ptr(ws), nb, _stream(stream)),
+           "ms_sdf_grid_build")
+    if stream is not None:
+        ws.record_stream(stream)     # the scratch stays reserved until that stream's work is done
+    return g
 
 
 def ms_training_records(n, n_events, exit_pos, exit_dir, rep_pos, rep_dir, media, seed, outs: dict, stream=None):

@@ -8,6 +8,7 @@
   render    one 128x128 px x 16 spp render at sigma_t 64, sphere tracing with the trained decoders
   brute     the same render in brute-force mode
   render512 / brute512   512x512 px x 64 spp at sigma_t 128 (sphere tracing / brute force)
+  render512g             render512 with sphere radii also from a 128^3 voxel grid of conservative distances
 Each case runs ``--repeat`` times (default 2) and prints the CUDA-event time of the last run.
 """
 from __future__ import annotations
@@ -59,11 +60,16 @@ def case_train(B=65536):
     return lambda: ms.ms_cvae_train_step(shape, p, m, v, x, c, B, step=1, loss3=loss3, ws=ws)
 
 
-def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0):
+def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0, grid_n=0):
     """One render; the returned callable exposes the per-request counters as ``.stats``."""
     models = pipeline.load()
     cset = ms.cvae_set(pipeline.device_decoders(models))
-    p = ms.render_params(synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode))
+    scene = synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode)
+    grid = None
+    if grid_n:
+        grid = ms.ms_sdf_grid_build(scene["disp_amp"], scene["disp_freq"], grid_n)
+        scene.update(sdf_grid_n=grid_n, sdf_grid=grid.data_ptr())
+    p = ms.render_params(scene)
     img = torch.zeros(res * res, dtype=torch.float64, device="cuda")
     st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
     ws = ms.workspace(ms.ms_render_workspace_size([p]))
@@ -72,6 +78,7 @@ def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0):
         st.zero_()
         ms.ms_render(p, cset if mode == ms.MS_SPHERE else None, img, st, ws=ws)
     run.stats = st
+    run.grid = grid          # keeps the grid alive with the case
     return run
 
 
@@ -79,6 +86,7 @@ CASES = {"walk": case_walk, "walk24": case_walk24, "decoder": case_decoder, "tra
          "decoder16": lambda: case_decoder(precision=ms.MS_FP16),
          "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE),
          "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
+         "render512g": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0, grid_n=128),
          "brute512": lambda: case_render(ms.MS_BRUTE, 512, 64, 128.0)}
 
 

@@ -181,3 +181,37 @@ def test_batch_in_a_cuda_graph_matches_direct_launch():
     assert np.allclose(imgs.cpu().numpy(), direct.cpu().numpy(), rtol=1e-6, atol=1e-12)
     assert np.array_equal(st.cpu().numpy()[:, :10], dst.cpu().numpy()[:, :10])
     assert np.all(st.cpu().numpy()[:, 10] > 0)
+
+
+@pytest.mark.parametrize("A,k,n", [(0.1, 6.0, 64), (0.15, 10.0, 48)])
+def test_sdf_grid_matches_oracle(orc, A, k, n):
+    """The voxel grid of conservative distances: the GPU's (single-precision marking, integer distance
+    transform) equals the oracle's, except in the rare voxels whose marking test is decided by rounding."""
+    g = ms.ms_sdf_grid_build(A, k, n).cpu().numpy().astype(np.float64)
+    ref, _, h = orc.sdf_grid(A, k, n)
+    same = np.abs(g - ref) <= 1e-5 * (1.0 + ref)
+    assert same.mean() >= 0.999, same.mean()
+    assert np.abs(g - ref).max() <= 2.0 * h
+
+
+def test_render_with_sdf_grid_matches_oracle(orc):
+    """Sphere radii from the larger of the distance bound and the voxel grid: the image and counters agree with
+    the oracle's (same acceptance as without the grid), and the larger spheres take fewer sphere steps."""
+    models = _models()
+    n = 64
+    grid = ms.ms_sdf_grid_build(0.1, 6.0, n)
+    p1 = synth.render_scene(64.0, width=32, height=32, spp=16, mode=1, seed=1)
+    p2 = dict(p1, seed=2)
+    og = dict(sdf_grid_n=n)
+    o1, _ = oracle_render(orc, dict(p1, **og), models)
+    o2, s2 = oracle_render(orc, dict(p2, **og), models)
+    g2, gs = gpu_render(dict(p2, sdf_grid_n=n, sdf_grid=grid.data_ptr()), models)
+    _, gs_plain = gpu_render(p2, models)
+    tol = 2.0 * 64.0 * (1.0 + 0.6) * 1e-4
+    same = np.abs(g2 - o2) <= tol * np.abs(o2) + 1e-9
+    assert same.mean() >= 0.99, same.mean()
+    noise = rmse(o2[same], o1[same])
+    assert abs(rmse(g2[same], o1[same]) / noise - 1.0) <= 0.01
+    for kk in (2, 3, 4, 7):
+        assert abs(int(gs[kk]) - int(s2[kk])) <= 0.01 * max(s2[kk], 100), (kk, gs[kk], s2[kk])
+    assert gs[3] + gs[4] < gs_plain[3] + gs_plain[4]     # fewer sphere steps plus events per path

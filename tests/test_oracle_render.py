@@ -164,3 +164,54 @@ def test_sphere_mode_runs_with_models(orc):
         decs.append((synth.xavier_decoder(100 + i, *shape).astype(np.float64), *shape))
     img, st, _ = _render(orc, mode=1, sigma_t=64.0, decoders=decs)
     assert st[3] > 0 and np.all(np.isfinite(img)) and np.all(img >= 0)
+
+
+def _surface_points(A, k, n_dir, seed):
+    """Points of the displaced sphere: along each unit direction u the surface is the root of
+    t - 1 - A sin(k t u_x) sin(k t u_y) sin(k t u_z) (unique: its t-derivative is at least 1 - A k > 0)."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n_dir, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    lo, hi = np.full(n_dir, 1.0 - A), np.full(n_dir, 1.0 + A)
+    g = lambda t: t - 1 - A * np.prod(np.sin(k * t[:, None] * u), axis=1)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        pos = g(mid) > 0
+        hi = np.where(pos, mid, hi)
+        lo = np.where(pos, lo, mid)
+    return 0.5 * (lo + hi)[:, None] * u
+
+
+def test_sdf_grid_distance_transform_against_brute_force(orc):
+    """On a 14^3 grid the values are (e - sqrt(3)) h with e the Euclidean distance between the voxel's centre and
+    the nearest centre of a voxel that may hold surface, found here by brute force over all pairs."""
+    A, k, n = 0.12, 7.0, 14
+    grid, b, h = orc.sdf_grid(A, k, n)
+    c = -b + (np.arange(n) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    f = np.sqrt(x * x + y * y + z * z) - 1 - A * np.sin(k * x) * np.sin(k * y) * np.sin(k * z)
+    marked = np.argwhere(np.abs(f) <= (1 + A * k) * np.sqrt(3) / 2 * h)
+    assert 0 < len(marked) < n ** 3
+    idx = np.argwhere(np.ones((n, n, n), bool))
+    e = np.sqrt(((idx[:, None, :] - marked[None, :, :]) ** 2).sum(axis=2).min(axis=1)).reshape(n, n, n)
+    assert np.allclose(grid, np.maximum(e - np.sqrt(3), 0) * h, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("A,k,n", [(0.1, 6.0, 32), (0.15, 10.0, 48), (0.1, 6.0, 96)])
+def test_sdf_grid_is_conservative_and_useful(orc, A, k, n):
+    """Every voxel value is at most the distance from any point of the voxel to the surface (checked at random
+    points against the nearest of 100,000 surface points, an upper bound of the true distance), and deep inside
+    it is above the global Lipschitz bound (the grid's reason to exist)."""
+    grid, b, h = orc.sdf_grid(A, k, n)
+    assert grid.shape == (n, n, n) and np.all(grid >= 0)
+    surf = _surface_points(A, k, 100_000, 3)
+    rng = np.random.default_rng(int(1000 * A + k))
+    pts = rng.uniform(-1.0 - A, 1.0 + A, (1500, 3))
+    idx = np.clip(np.floor((pts + b) / h).astype(int), 0, n - 1)
+    gv = grid[idx[:, 2], idx[:, 1], idx[:, 0]]
+    for i in range(0, len(pts), 250):
+        p = pts[i:i + 250]
+        d = np.sqrt(((p[:, None, :] - surf[None, :, :]) ** 2).sum(-1)).min(axis=1)
+        assert np.all(gv[i:i + 250] <= d + 1e-12), (gv[i:i + 250] - d).max()
+    c = np.clip(np.floor((np.zeros(3) + b) / h).astype(int), 0, n - 1)
+    assert grid[c[2], c[1], c[0]] > (1.0 - A) / (1.0 + A * k)
