@@ -130,14 +130,16 @@ def oracle_paths_per_second(models_np, budget_s: float, sigmas=SIGMAS, mode=1):
     import oracle
     from paper_2011_03082_b300 import synth
     decs = [(models_np[k].astype(np.float64), *synth.MODEL_SHAPES[k]) for k in ("length", "path", "event")]
-    # calibrate on a tiny sample, then size the real one
-    t0 = time.perf_counter()
-    for s in sigmas:
-        oracle.render(synth.render_scene(s, width=16, height=16, spp=2, mode=mode), decs)
-    t_cal = time.perf_counter() - t0
-    per_path = t_cal / (len(sigmas) * 16 * 16 * 2)
-    n_target = max(4096, int(budget_s / max(per_path, 1e-9) / len(sigmas)))
     side = 64
+    # calibrate on one sample per pixel of the same image (large enough that thread start-up is negligible),
+    # then size the real sample
+    t0 = time.perf_counter()
+    cal_paths = 0
+    for s in sigmas:
+        _, st, _ = oracle.render(synth.render_scene(s, width=side, height=side, spp=1, mode=mode), decs)
+        cal_paths += int(st[0])
+    per_path = (time.perf_counter() - t0) / max(1, cal_paths)
+    n_target = max(4096, int(budget_s / max(per_path, 1e-9) / len(sigmas)))
     spp = max(1, n_target // (side * side))
     paths = 0
     threads = 0
