@@ -130,10 +130,11 @@ __device__ void stage_weights(unsigned char* dst, const float* __restrict__ g, i
     }
 }
 
-template <int NT, int kSplit, bool kBF16>
-__device__ __forceinline__ void layer(const uint32_t (&ah)[2][4], const uint32_t (&al)[2][4],
+// One layer for MT 16-row tiles: acc = bias + A W^T, A given as half-precision head (and tail) fragments.
+template <int NT, int kSplit, bool kBF16, int MT = 2>
+__device__ __forceinline__ void layer(const uint32_t (&ah)[MT][4], const uint32_t (&al)[MT][4],
                                       const uint4* __restrict__ frag, const float* __restrict__ bias, int lane,
-                                      float (&acc)[2][NT][4])
+                                      float (&acc)[MT][NT][4])
 {
     const int t = lane & 3;
 #pragma unroll
@@ -141,7 +142,7 @@ __device__ __forceinline__ void layer(const uint32_t (&ah)[2][4], const uint32_t
         const uint4 w = frag[nt * 32 + lane];
         const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
+        for (int mt = 0; mt < MT; ++mt) {
             acc[mt][nt][0] = b0; acc[mt][nt][1] = b1; acc[mt][nt][2] = b0; acc[mt][nt][3] = b1;
             if (kSplit >= 2) mma<kBF16>(acc[mt][nt], al[mt], w.x, w.y);
             if (kSplit == 3) mma<kBF16>(acc[mt][nt], ah[mt], w.z, w.w);
@@ -152,11 +153,12 @@ __device__ __forceinline__ void layer(const uint32_t (&ah)[2][4], const uint32_t
 
 // Softplus of an 8 NTH-wide hidden layer, re-packed as the next layer's A fragments (head and tail); with
 // NTH = 1 the upper k half (columns 8..15) is zero.
-template <int kSplit, bool kBF16, int NTH = 2>
-__device__ __forceinline__ void hidden_to_a(const float (&acc)[2][NTH][4], uint32_t (&ah)[2][4], uint32_t (&al)[2][4])
+template <int kSplit, bool kBF16, int NTH = 2, int MT = 2>
+__device__ __forceinline__ void hidden_to_a(const float (&acc)[MT][NTH][4], uint32_t (&ah)[MT][4],
+                                            uint32_t (&al)[MT][4])
 {
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+    for (int mt = 0; mt < MT; ++mt) {
         float s[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -220,6 +222,54 @@ __device__ __forceinline__ void warp_mlp(const unsigned char* __restrict__ wsm, 
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 8 * NT3; ++j) y[j] = stage[lane * kStageStride + j];
+    __syncwarp();
+}
+
+// The MLP for the 16 rows of one tile, staged by row index instead of by lane: a lane with `active` set
+// supplies input row `row` (0..15) and receives that row's outputs; other lanes supply nothing and get zeros.
+// Rows no active lane supplied carry whatever the staging tile held: every output row depends on its own input
+// row only, so those rows are computed and ignored.  Every lane of the warp must call it.  Used where fewer
+// than half a warp's lanes have a query: the work is that of one tile instead of two.
+template <int NT3, int kSplit, bool kBF16, int NTH = 2>
+__device__ __forceinline__ void warp_mlp_rows16(const unsigned char* __restrict__ wsm, float* __restrict__ stage,
+                                                const float (&x)[16], float (&y)[8 * NT3], int row, bool active)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint4* frag = reinterpret_cast<const uint4*>(wsm);
+    const float* bias = reinterpret_cast<const float*>(wsm + (2 * NTH + NT3) * 32 * 16);
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stage[row * kStageStride + j] = x[j];
+    }
+    __syncwarp();
+    uint32_t ah[1][4], al[1][4];
+    {
+        const float* r0 = stage + g * kStageStride;
+        const float* r1 = r0 + 8 * kStageStride;
+        split2<kBF16>(r0[2 * t], r0[2 * t + 1], ah[0][0], al[0][0]);
+        split2<kBF16>(r1[2 * t], r1[2 * t + 1], ah[0][1], al[0][1]);
+        split2<kBF16>(r0[2 * t + 8], r0[2 * t + 9], ah[0][2], al[0][2]);
+        split2<kBF16>(r1[2 * t + 8], r1[2 * t + 9], ah[0][3], al[0][3]);
+    }
+    __syncwarp();
+    float h[1][NTH][4];
+    layer<NTH, kSplit, kBF16, 1>(ah, al, frag, bias, lane, h);
+    hidden_to_a<kSplit, kBF16, NTH, 1>(h, ah, al);
+    layer<NTH, kSplit, kBF16, 1>(ah, al, frag + NTH * 32, bias + 8 * NTH, lane, h);
+    hidden_to_a<kSplit, kBF16, NTH, 1>(h, ah, al);
+    float o[1][NT3][4];
+    layer<NT3, kSplit, kBF16, 1>(ah, al, frag + 2 * NTH * 32, bias + 16 * NTH, lane, o);
+#pragma unroll
+    for (int nt = 0; nt < NT3; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = g + (i >= 2 ? 8 : 0);
+            const int c = 8 * nt + 2 * t + (i & 1);
+            stage[r * kStageStride + c] = o[0][nt][i];
+        }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8 * NT3; ++j) y[j] = active ? stage[row * kStageStride + j] : 0.0f;
     __syncwarp();
 }
 

@@ -198,6 +198,8 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
 }
 
 constexpr int kUsedStats = 10;
+constexpr int kDrawKeys = 26 * 16;   // staging-tile offset of the draw keys (5 words per row) in a decoder round
+static_assert(kDrawKeys + 5 * 16 <= mmadec::kStageFloats, "decoder-round draws exceed the staging tile");
 
 // Scheduling constants of a kernel variant (see ms_render_autotune): kDecodeBatch parked lanes trigger a
 // decoder round, kTransBatch pending (or idle) lanes a transition (or refill) round, and between two
@@ -320,31 +322,61 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
 
         if (learned && parked && (__popc(parked) >= kDecodeBatch || n_active + __popc(pending) < kDecodeBatch)) {
             // ================= decoder round: the three learned samplers for the parked lanes =================
-            // The MLPs run on the tensor cores for all 32 rows of the warp (a lane that is not parked feeds
-            // zeros and ignores its outputs); everything per path stays in the lane's registers.
-            const bool mine = st == kDecode;
+            // The first 16 parked lanes (by lane index) are compacted into the 16 rows of one tensor-core tile;
+            // the MLPs run on that tile, and lanes parked beyond it wait for the next round.  Everything else
+            // per path stays in the lane's registers.
+            const int rank = __popc(parked & ((1u << lane) - 1u));
+            const bool mine = st == kDecode && rank < 16;
             const Req& qq = B.r[req];
-            const Stream rs(qq.seed, ((uint64_t)id_hi << 32) | id_lo);
+            // The step's draws (tag 1: absorption and azimuth uniforms; tags 2..7: 24 normals) are the same
+            // Philox blocks as drawn lane by lane, but the 7 blocks of each of the nsel selected paths are
+            // spread over all 32 lanes and handed over through the staging tile: value v of row r at
+            // [v * 16 + r], the rows' counter keys after them.
+            const int nsel = min(16, __popc(parked));
+            uint32_t* keys = reinterpret_cast<uint32_t*>(stage) + kDrawKeys;
+            if (mine) {
+                keys[5 * rank] = id_lo;
+                keys[5 * rank + 1] = id_hi;
+                keys[5 * rank + 2] = seg;
+                keys[5 * rank + 3] = (uint32_t)qq.seed;
+                keys[5 * rank + 4] = (uint32_t)(qq.seed >> 32);
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int i = lane; i < 7 * nsel; i += 32) {
+                const int c = (int)__fdividef((float)i + 0.5f, (float)nsel);   // block c of row r
+                const int r = i - c * nsel;
+                const uint32_t* kr = keys + 5 * r;
+                const Words wd = philox(kr[2], kr[0], kr[1], 1u + (uint32_t)c, kr[3], kr[4]);
+                if (c == 0) {
+                    stage[24 * 16 + r] = u24(wd.w0);
+                    stage[25 * 16 + r] = u24(wd.w1);
+                } else {
+                    const float2 a = box_muller(wd.w0, wd.w1), b = box_muller(wd.w2, wd.w3);
+                    float* o = stage + 4 * (c - 1) * 16 + r;
+                    o[0] = a.x; o[16] = a.y; o[32] = b.x; o[48] = b.y;
+                }
+            }
+            __syncwarp();
             float n[24];
-            Words a4{0u, 0u, 0u, 0u};
+            float u_abs = 0.0f, u_psi = 0.0f;
             float ltau = 0.0f;
             if (mine) {
                 cnt[3] += 1u;
-                a4 = rs.at(seg, 1u);
 #pragma unroll
-                for (int t = 0; t < 6; ++t) {
-                    const float4 v = dec::normals4(rs, seg, 2u + t);
-                    n[4 * t] = v.x; n[4 * t + 1] = v.y; n[4 * t + 2] = v.z; n[4 * t + 3] = v.w;
-                }
+                for (int v = 0; v < 24; ++v) n[v] = stage[v * 16 + rank];
+                u_abs = stage[24 * 16 + rank];
+                u_psi = stage[25 * 16 + rank];
                 ltau = __logf(tau);
             } else {
 #pragma unroll
                 for (int k = 0; k < 24; ++k) n[k] = 0.0f;
             }
+            __syncwarp();
             // LengthGen: N (albedo-1 physics, Eq. 3)
             float xin[16] = {ltau, mine ? qq.g : 0.0f, n[kZL], n[kZL + 1]};
             float yL[8];
-            mmadec::warp_mlp<1, 3, false, 1>(wl, stage, xin, yL);
+            mmadec::warp_mlp_rows16<1, 3, false, 1>(wl, stage, xin, yL, rank, mine);
             const float yN = yL[0] + __expf(0.5f * yL[1]) * n[kEL];
             float N = floorf(__expf(yN) + 0.5f);
             N = fminf(fmaxf(N, 1.0f), kNMax);
@@ -352,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             // PathGen: (cos theta, alpha, beta)
             float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, n[kZP], n[kZP + 1], n[kZP + 2], n[kZP + 3], n[kZP + 4]};
             float yP[8];
-            mmadec::warp_mlp<1, 3, false, 2>(wpth, stage, xp, yP);
+            mmadec::warp_mlp_rows16<1, 3, false, 2>(wpth, stage, xp, yP, rank, mine);
             const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * n[kEP]));
             float al = yP[1] + __expf(0.5f * yP[4]) * n[kEP + 1];
             float be = yP[2] + __expf(0.5f * yP[5]) * n[kEP + 2];
@@ -364,12 +396,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             // EventGen: representative event (X~, W~)
             float xe[16] = {ltau, mine ? qq.g : 0.0f, mine ? qq.phi : 0.0f, ct, al, be, lnN,
                             n[kZE], n[kZE + 1], n[kZE + 2], n[kZE + 3], n[kZE + 4]};
-            if (!mine) {
-#pragma unroll
-                for (int k = 0; k < 16; ++k) xe[k] = 0.0f;
-            }
             float yE[16];
-            mmadec::warp_mlp<2, 3, false, 2>(wev, stage, xe, yE);
+            mmadec::warp_mlp_rows16<2, 3, false, 2>(wev, stage, xe, yE, rank, mine);
             if (mine) {
                 float e[6];
 #pragma unroll
@@ -380,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 V t1, t2;
                 onb(w, &t1, &t2);
                 float sn, cs;
-                sincos_turns_fast(u24(a4.w1), &sn, &cs);
+                sincos_turns_fast(u_psi, &sn, &cs);
                 const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
                 const float nn = sqrtf(fmaxf(0.0f, 1.0f - ab2));
                 V vs[4] = {v3(stt, 0.0f, ct), v3(be * ct + nn * stt, al, -be * stt + nn * ct), v3(e[0], e[1], e[2]),
@@ -398,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 nX = p + vw[2] * rad;                   // p holds the collision point c
                 nW = unit(vw[3]);
                 nwt = lam;
-                if (u24(a4.w0) >= phiN) {
+                if (u_abs >= phiN) {
                     cnt[5] += 1u;
                     end_after = true;
                 } else {
@@ -595,10 +623,11 @@ Variant make_variant()
 {
     return Variant{(const void*)render_kernel<D, T, S, M, true>, (const void*)render_kernel<D, T, S, M, false>, D, T, S, M};
 }
+// A decoder round takes at most 16 parked lanes (one tensor-core tile), so the decode thresholds stay <= 16.
 static const Variant kVariants[] = {
-    make_variant<20, 12, 8, 3>(), make_variant<16, 8, 1, 2>(), make_variant<16, 8, 4, 2>(),
-    make_variant<16, 8, 8, 3>(), make_variant<20, 12, 16, 3>(), make_variant<24, 16, 8, 3>(),
-    make_variant<16, 12, 16, 3>(), make_variant<20, 12, 8, 4>(), make_variant<24, 16, 16, 3>(),
+    make_variant<16, 12, 16, 3>(), make_variant<12, 12, 16, 3>(), make_variant<16, 12, 8, 3>(),
+    make_variant<16, 8, 16, 3>(), make_variant<12, 8, 8, 3>(), make_variant<16, 16, 16, 3>(),
+    make_variant<8, 8, 16, 3>(), make_variant<16, 12, 16, 4>(), make_variant<16, 12, 32, 3>(),
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
