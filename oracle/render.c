@@ -134,6 +134,29 @@ static double safe_step(const scene* S, ov3 p, ov3 w, double f)
     return B < 0.0 ? c / (sq - B) : (B + sq) / -a;
 }
 
+/*
+ * The step from a point r of the boundary band (|f| / lip < R_EPS) when the ray leaves the boundary on the
+ * side being marched.  Let h be that side's distance function along the ray (h = -f inside, f outside),
+ * h0 = max(h(r), 0) and h1 = dh/ds >= 0 its rate (from the gradient).  The second directional derivative of
+ * A sin(kx) sin(ky) sin(kz) is at most 3 A k^2 in magnitude (its Hessian has entries of magnitude at most
+ * A k^2, and |w1 w2| + |w1 w3| + |w2 w3| <= 1 for a unit w); that of |p + s w| lies in [0, 1 / |p + s w|].
+ * So outside h'' >= -H with H = 3 A k^2, and inside, for s <= |r| / 2 (where |p + s w| >= |r| / 2),
+ * h'' >= -H with H = 3 A k^2 + 2 / |r|.  Hence h(s) >= h0 + h1 s - H s^2 / 2, which stays positive for
+ * 0 < s < (h1 + sqrt(h1^2 + 2 H h0)) / H: the ray cannot meet the surface before that.  The step is that
+ * bound, capped at |r| / 2 inside and at 4 outside (past the bounding sphere), and at least R_EPS.  A
+ * sphere tracer that moves off the surface by R_EPS per step would need about lip / h1 steps to leave the
+ * band; this takes one.
+ */
+static double band_step(const scene* S, ov3 r, double f, double h1, int inside)
+{
+    double rp = sqrt(dot(r, r));
+    double H = 3.0 * S->A * S->k * S->k + (inside ? 2.0 / rp : 0.0);
+    double cap = inside ? 0.5 * rp : 4.0;
+    double h0 = fmax(inside ? -f : f, 0.0);
+    double s = H > 0.0 ? (h1 + sqrt(h1 * h1 + 2.0 * H * h0)) / H : cap;
+    return fmax(R_EPS, fmin(s, cap));
+}
+
 /* March inside the medium from p along w for at most l.  Returns 1 on a collision (*q = p + l w), 0 when
  * the boundary is crossed outward at *q, 2 when the step cap runs out. */
 static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
@@ -144,11 +167,12 @@ static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
         double f = sdf(S, r);
         double d = -f / S->lip;
         if (d < R_EPS) {
-            if (dot(sdf_grad(S, r), w) > 0.0) {
+            double gd = dot(sdf_grad(S, r), w);
+            if (gd > 0.0) {
                 *q = r;
                 return 0;
             }
-            d = R_EPS;
+            d = band_step(S, r, f, -gd, 1);
         } else {
             d = fmax(d, safe_step(S, r, w, f));
         }
@@ -173,11 +197,12 @@ static int march_outside(const scene* S, ov3 p, ov3 w, ov3* q)
         double f = sdf(S, r);
         double d = f / S->lip;
         if (d < R_EPS) {
-            if (dot(sdf_grad(S, r), w) < 0.0) {
+            double gd = dot(sdf_grad(S, r), w);
+            if (gd < 0.0) {
                 *q = r;
                 return 1;
             }
-            d = R_EPS;
+            d = band_step(S, r, f, gd, 0);
         } else {
             double h = safe_step(S, r, w, f);
             if (h == INFINITY)
@@ -206,11 +231,12 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
             double f = sdf(S, r);
             double d = -f / S->lip;
             if (d < R_EPS) {
-                if (dot(sdf_grad(S, r), w) > 0.0) {
+                double gd = dot(sdf_grad(S, r), w);
+                if (gd > 0.0) {
                     inside = 0;
                     continue;
                 }
-                d = R_EPS;
+                d = band_step(S, r, f, -gd, 1);
             } else {
                 d = fmax(d, safe_step(S, r, w, f));
             }
@@ -223,11 +249,12 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
             double f = sdf(S, r);
             double d = f / S->lip;
             if (d < R_EPS) {
-                if (dot(sdf_grad(S, r), w) < 0.0) {
+                double gd = dot(sdf_grad(S, r), w);
+                if (gd < 0.0) {
                     inside = 1;
                     continue;
                 }
-                d = R_EPS;
+                d = band_step(S, r, f, gd, 0);
             } else {
                 double h = safe_step(S, r, w, f);
                 if (h == INFINITY)
