@@ -94,6 +94,8 @@ def lib():
         L.om_inside_length.restype = C.c_double
         L.om_ray_crossing.argtypes = [C.c_double, C.c_double, P, P, P]
         L.om_ray_crossing.restype = C.c_int
+        L.om_band_step.argtypes = [C.c_double, C.c_double, P, P]
+        L.om_band_step.restype = C.c_double
         _lib = L
     return _lib
 
@@ -274,6 +276,14 @@ def sdf_grid(A, k, n):
     may_hold = np.abs(f) <= (1.0 + A * k) * (np.sqrt(3.0) / 2.0) * h
     e = ndimage.distance_transform_edt(~may_hold)
     return np.maximum(0.0, (e - np.sqrt(3.0)) * h), b, h
+
+
+def band_step(A, k, p, w):
+    """The march's step from a point p of the boundary band along w, on the side of f(p); -1 when the ray
+    moves toward the surface (a crossing)."""
+    p = np.ascontiguousarray(p, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    return float(lib().om_band_step(A, k, _ptr(p), _ptr(w)))
 
 
 def ray_crossing(A, k, p, w):

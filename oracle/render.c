@@ -137,11 +137,12 @@ static double safe_step(const scene* S, ov3 p, ov3 w, double f)
 /*
  * The step from a point r of the boundary band (|f| / lip < R_EPS) when the ray leaves the boundary on the
  * side being marched.  Let h be that side's distance function along the ray (h = -f inside, f outside),
- * h0 = max(h(r), 0) and h1 = dh/ds >= 0 its rate (from the gradient).  The second directional derivative of
- * A sin(kx) sin(ky) sin(kz) is at most 3 A k^2 in magnitude (its Hessian has entries of magnitude at most
- * A k^2, and |w1 w2| + |w1 w3| + |w2 w3| <= 1 for a unit w); that of |p + s w| lies in [0, 1 / |p + s w|].
- * So outside h'' >= -H with H = 3 A k^2, and inside, for s <= |r| / 2 (where |p + s w| >= |r| / 2),
- * h'' >= -H with H = 3 A k^2 + 2 / |r|.  Hence h(s) >= h0 + h1 s - H s^2 / 2, which stays positive for
+ * h0 = max(h(r), 0) and h1 = dh/ds >= 0 its rate (from the gradient).  Along p + s w, the product
+ * sin(kx) sin(ky) sin(kz) is, by sin a sin b sin c = [sin(a+b-c) + sin(a-b+c) + sin(-a+b+c) - sin(a+b+c)] / 4,
+ * a sum of four sinusoids of angular frequencies k (+-w1 +-w2 +-w3), so its second derivative in s is at most
+ * k^2 / 4 times the sum of the four squared frequencies, i.e. k^2 |w|^2 = k^2; that of |p + s w| lies in
+ * [0, 1 / |p + s w|].  So outside h'' >= -H with H = A k^2, and inside, for s <= |r| / 2 (where
+ * |p + s w| >= |r| / 2), h'' >= -H with H = A k^2 + 2 / |r|.  Hence h(s) >= h0 + h1 s - H s^2 / 2, which stays positive for
  * 0 < s < (h1 + sqrt(h1^2 + 2 H h0)) / H: the ray cannot meet the surface before that.  The step is that
  * bound, capped at |r| / 2 inside and at 4 outside (past the bounding sphere), and at least R_EPS.  A
  * sphere tracer that moves off the surface by R_EPS per step would need about lip / h1 steps to leave the
@@ -150,7 +151,7 @@ static double safe_step(const scene* S, ov3 p, ov3 w, double f)
 static double band_step(const scene* S, ov3 r, double f, double h1, int inside)
 {
     double rp = sqrt(dot(r, r));
-    double H = 3.0 * S->A * S->k * S->k + (inside ? 2.0 / rp : 0.0);
+    double H = S->A * S->k * S->k + (inside ? 2.0 / rp : 0.0);
     double cap = inside ? 0.5 * rp : 4.0;
     double h0 = fmax(inside ? -f : f, 0.0);
     double s = H > 0.0 ? (h1 + sqrt(h1 * h1 + 2.0 * H * h0)) / H : cap;
@@ -641,6 +642,19 @@ int om_ray_crossing(double A, double k, const double* p, const double* w, double
     }
     *t = sqrt(dot(sub(q, o), sub(q, o)));
     return r;
+}
+
+/* The band step from p along w (the side is that of f(p)); -1 when the ray meets the surface there (it
+ * moves toward it), exposed for the tests. */
+double om_band_step(double A, double k, const double* p, const double* w)
+{
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    ov3 r = v3(p[0], p[1], p[2]), d = v3(w[0], w[1], w[2]);
+    double f = sdf(&S, r);
+    int inside = f < 0.0;
+    double gd = dot(sdf_grad(&S, r), d);
+    double h1 = inside ? -gd : gd;
+    return h1 < 0.0 ? -1.0 : band_step(&S, r, f, h1, inside);
 }
 
 /* Inside length of one segment, exposed for the tests. */

@@ -134,12 +134,13 @@ __device__ __forceinline__ float safe_step(const Geo& q, V p, V w, float rp, flo
 
 // Step off the surface from a point of the boundary band when the ray leaves it on the marched side: with hs
 // that side's distance function (-f inside, f outside) and h1 >= 0 its rate along the ray, the second
-// directional derivative bound H = 3 A k^2 (displacement) + 2 / |p| (inside only, the curvature of |p| while
+// directional derivative bound H = A k^2 (sin sin sin along a line is a sum of four sinusoids of angular
+// frequencies k (+-w1 +-w2 +-w3), whose squares sum to 4 k^2) + 2 / |p| (inside only, the curvature of |p| while
 // the step stays below |p| / 2) gives hs(s) >= hs + h1 s - H s^2 / 2 > 0 up to (h1 + sqrt(h1^2 + 2 H hs)) / H.
 // Capped at |p| / 2 inside and 4 outside (beyond the bounding sphere), and at least the band width.
 __device__ __forceinline__ float band_step(const Geo& q, float rp, float hs, float h1, bool in_medium)
 {
-    const float H = 3.0f * q.A * q.k * q.k + (in_medium ? __fdividef(2.0f, rp) : 0.0f);
+    const float H = q.A * q.k * q.k + (in_medium ? __fdividef(2.0f, rp) : 0.0f);
     const float cap = in_medium ? 0.5f * rp : 4.0f;
     const float h0 = fmaxf(hs, 0.0f);
     const float s = H > 0.0f ? __fdividef(h1 + sqrtf(fmaf(h1, h1, 2.0f * H * h0)), H) : cap;

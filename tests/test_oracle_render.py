@@ -215,3 +215,76 @@ def test_sdf_grid_is_conservative_and_useful(orc, A, k, n):
         assert np.all(gv[i:i + 250] <= d + 1e-12), (gv[i:i + 250] - d).max()
     c = np.clip(np.floor((np.zeros(3) + b) / h).astype(int), 0, n - 1)
     assert grid[c[2], c[1], c[0]] > (1.0 - A) / (1.0 + A * k)
+
+
+def _surface_points(f, n, rng):
+    """n points on the displaced sphere: radial bisection of f along random directions."""
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    lo, hi = np.full(n, 0.5), np.full(n, 1.6)
+    for _ in range(60):
+        m = 0.5 * (lo + hi)
+        neg = f(m[:, None] * u) < 0
+        lo = np.where(neg, m, lo)
+        hi = np.where(neg, hi, m)
+    return lo[:, None] * u
+
+
+def _disp_grad(A, k, p):
+    s, c = np.sin(k * p), np.cos(k * p)
+    return p / np.linalg.norm(p) - A * k * np.array([c[0] * s[1] * s[2], s[0] * c[1] * s[2], s[0] * s[1] * c[2]])
+
+
+@pytest.mark.parametrize("A,k", [(0.1, 6.0), (0.2, 4.0), (0.05, 10.0)])
+def test_band_step_never_crosses_and_is_tight(orc, A, k):
+    """The march's step off the boundary band (a second-order bound on f along the ray) against dense sampling
+    of f: from surface points, along directions that leave the surface at shallow angles on either side, the
+    surface is never met within the step, and for the worst-curved of them the step reaches most of the way
+    to where the ray does meet it again (at least 60 %).  A curvature bound too small by a third lets some rays
+    cross; one three times too large keeps every step below 30 % of that distance."""
+    rng = np.random.default_rng(int(10 * k))
+    f = _disp_sdf(A, k)
+    pts = _surface_points(f, 1500, rng)
+    best, checked = 0.0, 0
+    for p in pts:
+        n = _disp_grad(A, k, p)
+        n /= np.linalg.norm(n)
+        t = rng.standard_normal(3)
+        t -= (t @ n) * n
+        t /= np.linalg.norm(t)
+        side = rng.choice([-1.0, 1.0])
+        c = rng.uniform(0.01, 0.3)
+        w = t * math.sqrt(1 - c * c) + side * c * n
+        p0 = p + side * 1e-9 * n                     # on the chosen side of the surface, inside the band
+        s = orc.band_step(A, k, p0, w)
+        assert s >= 1e-4, (p0, w, s)
+        tt = np.linspace(0.0, 3.0 * s, 6001)[1:]
+        h = side * f(p0 + tt[:, None] * w)
+        neg = np.nonzero(h < -1e-12)[0]
+        if neg.size:
+            assert tt[neg[0]] > s, (p0, w, s, tt[neg[0]])
+            best = max(best, s / tt[neg[0]])
+        checked += 1
+    assert checked == len(pts)
+    assert best > 0.6, best
+
+
+def test_band_step_on_the_sphere(orc):
+    """A = 0 (the unit sphere): outside, a ray leaving the sphere never returns, and the step is the cap (4);
+    inside, a ray leaving the surface at cos theta to the inward normal meets it again after the chord
+    2 cos theta, and the step stays within it and reaches at least a quarter of it (below the cap |p| / 2);
+    a ray moving toward the surface reports a crossing (-1)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        t = rng.standard_normal(3)
+        t -= (t @ u) * u
+        t /= np.linalg.norm(t)
+        c = rng.uniform(0.02, 1.0)
+        w_out = c * u + math.sqrt(1 - c * c) * t
+        assert orc.band_step(0.0, 6.0, (1 + 1e-9) * u, w_out) == 4.0
+        w_in = -c * u + math.sqrt(1 - c * c) * t
+        s = orc.band_step(0.0, 6.0, (1 - 1e-9) * u, w_in)
+        assert s <= 2 * c and s >= min(0.5 * c, 0.5) - 1e-12, (c, s)
+        assert orc.band_step(0.0, 6.0, (1 - 1e-9) * u, w_out) == -1.0
