@@ -217,7 +217,7 @@ def test_sdf_grid_is_conservative_and_useful(orc, A, k, n):
     assert grid[c[2], c[1], c[0]] > (1.0 - A) / (1.0 + A * k)
 
 
-def _surface_points(f, n, rng):
+def _radial_surface_points(f, n, rng):
     """n points on the displaced sphere: radial bisection of f along random directions."""
     u = rng.standard_normal((n, 3))
     u /= np.linalg.norm(u, axis=1, keepdims=True)
@@ -244,7 +244,7 @@ def test_band_step_never_crosses_and_is_tight(orc, A, k):
     cross; one three times too large keeps every step below 30 % of that distance."""
     rng = np.random.default_rng(int(10 * k))
     f = _disp_sdf(A, k)
-    pts = _surface_points(f, 1500, rng)
+    pts = _radial_surface_points(f, 1500, rng)
     best, checked = 0.0, 0
     for p in pts:
         n = _disp_grad(A, k, p)
