@@ -29,12 +29,13 @@ SIGMAS = (16.0, 32.0, 64.0, 128.0)
 WORKLOAD = ("render of the displaced sphere 0.1 sin(6x)sin(6y)sin(6z), point light, 512x512 px, 256 spp, "
             "sigma_t {16,32,64,128}, g 0.8, albedo 0.999, CVAE sphere tracing + NEE (trained decoders)")
 
-# Algorithmic work per counted unit of the renderer's roofline: special-function (MUFU) operations per SDF
-# distance evaluation (sqrt + 3 sin), per gradient evaluation (3 sin/cos pairs + rsqrt), per sphere step
-# (the three decoders' 2 x width Softplus each, as exp + log; 10 posterior exps; 11 Box-Muller pairs x 4;
-# 3 logs) and per brute-force event (log, sin/cos, rsqrt, divide).
-MUFU_PER_SDF = 4
-MUFU_PER_GRAD = 7
+# Algorithmic work per counted unit of the renderer's roofline: special-function (MUFU) operations per march
+# step (f and its derivative along the ray: sqrt + 3 sin/cos pairs), per sphere-radius evaluation at a
+# collision (f alone: sqrt + 3 sin), per sphere step (the three decoders' 2 x width Softplus each, as exp +
+# log; 10 posterior exps; 11 Box-Muller pairs x 4; 3 logs) and per brute-force event (log, sin/cos, rsqrt,
+# divide).
+MUFU_PER_MARCH = 7
+MUFU_PER_RADIUS = 4
 MUFU_PER_SPHERE = sum(2 * shape[3] * 2 for shape in (
     (2, 1, 2, 8), (3, 3, 5, 16), (7, 6, 5, 16))) + 10 + 11 * 4 + 3      # Table 1 decoder shapes: 217
 MUFU_PER_EVENT = 5
@@ -292,8 +293,10 @@ def main(argv=None):
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2032.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     mufu_peak = n_sm * 16 * sm_mhz_max * 1e6 / 1e12              # Tops/s at the maximum SM clock
-    mufu_ops = (st[8] * MUFU_PER_SDF + st[9] * MUFU_PER_GRAD + st[3] * MUFU_PER_SPHERE + st[4] * MUFU_PER_EVENT
-                + st[7] * MUFU_PER_NEE + st[2] * 2)
+    # every collision of a sphere-tracing request evaluates f once for the sphere's radius (counted in st[8])
+    radius_evals = st[3] + st[4]
+    mufu_ops = ((st[8] - radius_evals) * MUFU_PER_MARCH + radius_evals * MUFU_PER_RADIUS + st[3] * MUFU_PER_SPHERE
+                + st[4] * MUFU_PER_EVENT + st[7] * MUFU_PER_NEE + st[2] * 2)
     achieved = mufu_ops / (t_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
                 "frac": achieved / mufu_peak, "traffic": recorded_traffic(ms.ms_render_variant_info(variant)),

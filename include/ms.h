@@ -213,9 +213,11 @@ ms_status ms_training_records(uint64_t n, const int32_t* n_events, const float* 
 /* ------------------------------------------------------------------------------------------------------
  * Rendering a homogeneous translucent SDF object with a point light (Sec. 3, Fig. 2b; Sec. 4.1; Sec. 4.3,
  * Eq. 5).  The object is the displaced unit sphere f(p) = |p| - 1 - A sin(k x) sin(k y) sin(k z) (negative
- * inside); |f| / (1 + A k) is a conservative distance.  Rays are sphere traced with the larger of that step
- * and the first root of |p + s w| = R(p) +/- A k s (the radial term followed exactly, the displacement
- * bounded), which also detects when the surface is out of reach.  The boundary is index matched (no refraction, as in
+ * inside); |f| / (1 + A k) is a conservative distance.  Rays are sphere traced with the largest of that step,
+ * the first root of |p + s w| = R(p) +/- A k s (the radial term followed exactly, the displacement bounded;
+ * it also detects when the surface is out of reach) and the first root of the curvature bound
+ * h + h' s - H s^2 / 2 on the side's distance h (H = A k^2, plus 2 / |p| inside), which closes in on the
+ * surface quadratically and steps off it in one step.  The boundary is index matched (no refraction, as in
  * the paper's unrefracted NEE).  Camera paths enter the object; after each free flight to a collision:
  *   MS_SPHERE: if sigma_t * r >= min_optical_radius with r = min(distance bound, max_optical_radius /
  *     sigma_t), one sphere step: LengthGen -> N, PathGen -> exit (Eq. 4), EventGen -> (X, W), NEE at X with
@@ -273,7 +275,8 @@ size_t ms_render_workspace_size(const ms_render_params* reqs, int n_requests);
 /* image: device [height][width] doubles, accumulated: the sum over the pixel's samples (divide by spp).
  * stats: device [MS_RENDER_STATS] accumulated: [0] camera paths, [1] paths entering the object, [2] flights,
  * [3] sphere steps, [4] brute-force events, [5] absorbed, [6] truncated paths or dropped estimates,
- * [7] next-event estimates, [8] SDF distance evaluations, [9] SDF gradient evaluations, [10] completion time
+ * [7] next-event estimates, [8] SDF evaluations (march steps, each with f's derivative along the ray, and
+ * sphere radii at collisions), [9] march steps in the boundary band, [10] completion time
  * of the request in ns after the launch's first block started (written, not accumulated), [11..15] zero.
  * models: host struct with device weight pointers (ignored in MS_BRUTE).  workspace:
  * ms_render_workspace_size() bytes (sample ticket, start time, finished-path counters).  One persistent

@@ -96,6 +96,8 @@ def lib():
         L.om_ray_crossing.restype = C.c_int
         L.om_band_step.argtypes = [C.c_double, C.c_double, P, P]
         L.om_band_step.restype = C.c_double
+        L.om_march_step.argtypes = [C.c_double, C.c_double, P, P]
+        L.om_march_step.restype = C.c_double
         _lib = L
     return _lib
 
@@ -284,6 +286,14 @@ def band_step(A, k, p, w):
     p = np.ascontiguousarray(p, np.float64)
     w = np.ascontiguousarray(w, np.float64)
     return float(lib().om_band_step(A, k, _ptr(p), _ptr(w)))
+
+
+def march_step(A, k, p, w):
+    """One step of the march from p along w on the side of f(p): -1 for a crossing of the boundary band,
+    inf when the surface cannot be reached (outside)."""
+    p = np.ascontiguousarray(p, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    return float(lib().om_march_step(A, k, _ptr(p), _ptr(w)))
 
 
 def ray_crossing(A, k, p, w):

@@ -91,7 +91,6 @@ static double sdf(const scene* S, ov3 p)
 
 static ov3 sdf_grad(const scene* S, ov3 p)
 {
-    t_grad_evals += 1;
     double sx = sin(S->k * p.x), sy = sin(S->k * p.y), sz = sin(S->k * p.z);
     double cx = cos(S->k * p.x), cy = cos(S->k * p.y), cz = cos(S->k * p.z);
     double n = sqrt(dot(p, p));
@@ -135,27 +134,58 @@ static double safe_step(const scene* S, ov3 p, ov3 w, double f)
 }
 
 /*
- * The step from a point r of the boundary band (|f| / lip < R_EPS) when the ray leaves the boundary on the
- * side being marched.  Let h be that side's distance function along the ray (h = -f inside, f outside),
- * h0 = max(h(r), 0) and h1 = dh/ds >= 0 its rate (from the gradient).  Along p + s w, the product
- * sin(kx) sin(ky) sin(kz) is, by sin a sin b sin c = [sin(a+b-c) + sin(a-b+c) + sin(-a+b+c) - sin(a+b+c)] / 4,
- * a sum of four sinusoids of angular frequencies k (+-w1 +-w2 +-w3), so its second derivative in s is at most
- * k^2 / 4 times the sum of the four squared frequencies, i.e. k^2 |w|^2 = k^2; that of |p + s w| lies in
- * [0, 1 / |p + s w|].  So outside h'' >= -H with H = A k^2, and inside, for s <= |r| / 2 (where
- * |p + s w| >= |r| / 2), h'' >= -H with H = A k^2 + 2 / |r|.  Hence h(s) >= h0 + h1 s - H s^2 / 2, which stays positive for
- * 0 < s < (h1 + sqrt(h1^2 + 2 H h0)) / H: the ray cannot meet the surface before that.  The step is that
- * bound, capped at |r| / 2 inside and at 4 outside (past the bounding sphere), and at least R_EPS.  A
- * sphere tracer that moves off the surface by R_EPS per step would need about lip / h1 steps to leave the
- * band; this takes one.
+ * A second conservative step, from the curvature of f along the ray.  Let h be the marched side's distance
+ * function along the ray (h = -f inside the medium, f outside), h0 = h(r) >= 0 and h1 = dh/ds its rate (from
+ * the gradient).  Along p + s w, the product sin(kx) sin(ky) sin(kz) is, by
+ * sin a sin b sin c = [sin(a+b-c) + sin(a-b+c) + sin(-a+b+c) - sin(a+b+c)] / 4, a sum of four sinusoids of
+ * angular frequencies k (+-w1 +-w2 +-w3), so its second derivative in s is at most k^2 / 4 times the sum of the
+ * four squared frequencies, i.e. k^2 |w|^2 = k^2; that of |p + s w| lies in [0, 1 / |p + s w|].  So outside
+ * h'' >= -H with H = A k^2, and inside, for s <= |r| / 2 (where |p + s w| >= |r| / 2), h'' >= -H with
+ * H = A k^2 + 2 / |r|.  Hence h(s) >= h0 + h1 s - H s^2 / 2, which stays positive up to its first positive
+ * root (h1 + sqrt(h1^2 + 2 H h0)) / H, written 2 h0 / (sqrt(h1^2 + 2 H h0) - h1) when h1 < 0 (no
+ * cancellation): the ray cannot meet the surface before it.  The step is that root, capped at |r| / 2 inside
+ * and at 4 outside (past the bounding sphere).  Toward the surface it approaches the crossing quadratically
+ * (where the Lipschitz step only closes a fixed fraction of the gap per step); away from it, it leaves the
+ * boundary band in one step where steps of the band width would need about lip / h1 of them.
  */
-static double band_step(const scene* S, ov3 r, double f, double h1, int inside)
+static double curve_step(const scene* S, double rp, double h0, double h1, int inside)
 {
-    double rp = sqrt(dot(r, r));
     double H = S->A * S->k * S->k + (inside ? 2.0 / rp : 0.0);
     double cap = inside ? 0.5 * rp : 4.0;
-    double h0 = fmax(inside ? -f : f, 0.0);
-    double s = H > 0.0 ? (h1 + sqrt(h1 * h1 + 2.0 * H * h0)) / H : cap;
-    return fmax(R_EPS, fmin(s, cap));
+    double q = sqrt(h1 * h1 + 2.0 * H * h0);
+    double s = h1 < 0.0 ? 2.0 * h0 / (q - h1) : (H > 0.0 ? (h1 + q) / H : cap);
+    return fmin(s, cap);
+}
+
+/*
+ * One march step at r along w on the marched side (inside: the medium).  In the boundary band
+ * (|f| / lip < R_EPS) the point counts as on the surface: the ray crosses there when it moves to the other
+ * side (*crossing = 1, no step), and otherwise steps off with the curvature step from h0 = max(h, 0), at
+ * least R_EPS.  Elsewhere the step is the largest of the three conservative steps (Lipschitz, radial plus
+ * Lipschitz, curvature); *escape = 1 when, outside, the surface cannot be reached along the ray.
+ */
+static double march_step(const scene* S, ov3 r, ov3 w, int inside, int* crossing, int* escape)
+{
+    double f = sdf(S, r);
+    double gd = dot(sdf_grad(S, r), w);
+    double h = inside ? -f : f, h1 = inside ? -gd : gd;
+    double rp = sqrt(dot(r, r));
+    *crossing = 0;
+    *escape = 0;
+    if (h / S->lip < R_EPS) {
+        t_grad_evals += 1;
+        if (h1 < 0.0) {
+            *crossing = 1;
+            return 0.0;
+        }
+        return fmax(R_EPS, curve_step(S, rp, fmax(h, 0.0), h1, inside));
+    }
+    double q = safe_step(S, r, w, f);
+    if (q == INFINITY) {
+        *escape = 1;
+        return INFINITY;
+    }
+    return fmax(fmax(h / S->lip, q), curve_step(S, rp, h, h1, inside));
 }
 
 /* March inside the medium from p along w for at most l.  Returns 1 on a collision (*q = p + l w), 0 when
@@ -165,17 +195,11 @@ static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
     double t = 0.0;
     for (int it = 0; it < R_MAX_MARCH; ++it) {
         ov3 r = add(p, mul(w, t));
-        double f = sdf(S, r);
-        double d = -f / S->lip;
-        if (d < R_EPS) {
-            double gd = dot(sdf_grad(S, r), w);
-            if (gd > 0.0) {
-                *q = r;
-                return 0;
-            }
-            d = band_step(S, r, f, -gd, 1);
-        } else {
-            d = fmax(d, safe_step(S, r, w, f));
+        int crossing, escape;
+        double d = march_step(S, r, w, 1, &crossing, &escape);
+        if (crossing) {
+            *q = r;
+            return 0;
         }
         if (t + d >= l) {
             *q = add(p, mul(w, l));
@@ -195,28 +219,21 @@ static int march_outside(const scene* S, ov3 p, ov3 w, ov3* q)
         ov3 r = add(p, mul(w, t));
         if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
             return 0;
-        double f = sdf(S, r);
-        double d = f / S->lip;
-        if (d < R_EPS) {
-            double gd = dot(sdf_grad(S, r), w);
-            if (gd < 0.0) {
-                *q = r;
-                return 1;
-            }
-            d = band_step(S, r, f, gd, 0);
-        } else {
-            double h = safe_step(S, r, w, f);
-            if (h == INFINITY)
-                return 0;
-            d = fmax(d, h);
+        int crossing, escape;
+        double d = march_step(S, r, w, 0, &crossing, &escape);
+        if (crossing) {
+            *q = r;
+            return 1;
         }
+        if (escape)
+            return 0;
         t = t + d;
     }
     return 2;
 }
 
 /* Length of the straight segment X -> x_L that lies inside the medium (Sec. 4.3, d_t); -1 when the step
- * cap runs out (the estimate is then dropped). */
+ * cap runs out (the estimate is then dropped).  A boundary crossing switches the side at the same point. */
 static double inside_length(const scene* S, ov3 X, ov3 xl)
 {
     ov3 dl = sub(xl, X);
@@ -228,42 +245,20 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
         if (t >= D)
             return din;
         ov3 r = add(X, mul(w, t));
-        if (inside) {
-            double f = sdf(S, r);
-            double d = -f / S->lip;
-            if (d < R_EPS) {
-                double gd = dot(sdf_grad(S, r), w);
-                if (gd > 0.0) {
-                    inside = 0;
-                    continue;
-                }
-                d = band_step(S, r, f, -gd, 1);
-            } else {
-                d = fmax(d, safe_step(S, r, w, f));
-            }
-            double step = fmin(d, D - t);
-            din = din + step;
-            t = t + step;
-        } else {
-            if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
-                return din;
-            double f = sdf(S, r);
-            double d = f / S->lip;
-            if (d < R_EPS) {
-                double gd = dot(sdf_grad(S, r), w);
-                if (gd < 0.0) {
-                    inside = 1;
-                    continue;
-                }
-                d = band_step(S, r, f, gd, 0);
-            } else {
-                double h = safe_step(S, r, w, f);
-                if (h == INFINITY)
-                    return din;
-                d = fmax(d, h);
-            }
-            t = t + fmin(d, D - t);
+        if (!inside && dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
+            return din;
+        int crossing, escape;
+        double d = march_step(S, r, w, inside, &crossing, &escape);
+        if (crossing) {
+            inside = !inside;
+            continue;
         }
+        if (escape)
+            return din;
+        double step = fmin(d, D - t);
+        if (inside)
+            din = din + step;
+        t = t + step;
     }
     return -1.0;
 }
@@ -583,7 +578,7 @@ static void* render_worker(void* arg)
  * Render: image[h][w] accumulates the sum over the spp samples of each pixel (divide by spp for the mean).
  * stats[16]: camera paths, paths entering the object, flight segments, sphere steps, brute events,
  * absorbed paths, truncated paths or dropped estimates (segment cap or march step cap), next-event
- * estimates, SDF distance evaluations, SDF gradient evaluations, zeros.  Returns the number of threads used.
+ * estimates, SDF evaluations (distance and gradient), boundary-band steps, zeros.  Returns the number of threads used.
  */
 int om_render(const om_render_params* P, const om_decoder* dec3, double* image, uint64_t* stats, int n_threads)
 {
@@ -653,8 +648,19 @@ double om_band_step(double A, double k, const double* p, const double* w)
     double f = sdf(&S, r);
     int inside = f < 0.0;
     double gd = dot(sdf_grad(&S, r), d);
-    double h1 = inside ? -gd : gd;
-    return h1 < 0.0 ? -1.0 : band_step(&S, r, f, h1, inside);
+    double h = inside ? -f : f, h1 = inside ? -gd : gd;
+    return h1 < 0.0 ? -1.0 : fmax(R_EPS, curve_step(&S, sqrt(dot(r, r)), fmax(h, 0.0), h1, inside));
+}
+
+/* One march step from p along w on the side of f(p): -1 for a crossing, INFINITY for an escape, exposed
+ * for the tests. */
+double om_march_step(double A, double k, const double* p, const double* w)
+{
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    ov3 r = v3(p[0], p[1], p[2]), d = v3(w[0], w[1], w[2]);
+    int crossing, escape;
+    double s = march_step(&S, r, d, sdf(&S, r) < 0.0, &crossing, &escape);
+    return crossing ? -1.0 : s;
 }
 
 /* Inside length of one segment, exposed for the tests. */

@@ -132,30 +132,37 @@ __device__ __forceinline__ float safe_step(const Geo& q, V p, V w, float rp, flo
     return __fdividef(num, den);
 }
 
-// Step off the surface from a point of the boundary band when the ray leaves it on the marched side: with hs
-// that side's distance function (-f inside, f outside) and h1 >= 0 its rate along the ray, the second
-// directional derivative bound H = A k^2 (sin sin sin along a line is a sum of four sinusoids of angular
-// frequencies k (+-w1 +-w2 +-w3), whose squares sum to 4 k^2) + 2 / |p| (inside only, the curvature of |p| while
-// the step stays below |p| / 2) gives hs(s) >= hs + h1 s - H s^2 / 2 > 0 up to (h1 + sqrt(h1^2 + 2 H hs)) / H.
-// Capped at |p| / 2 inside and 4 outside (beyond the bounding sphere), and at least the band width.
-__device__ __forceinline__ float band_step(const Geo& q, float rp, float hs, float h1, bool in_medium)
+// The curvature step: with hs >= 0 the marched side's distance function (-f inside, f outside) and h1 its rate
+// along the ray, the second directional derivative bound H = A k^2 (sin sin sin along a line is a sum of four
+// sinusoids of angular frequencies k (+-w1 +-w2 +-w3), whose squares sum to 4 k^2) + 2 / |p| (inside only, the
+// curvature of |p| while the step stays below |p| / 2) gives hs(s) >= hs + h1 s - H s^2 / 2 > 0 up to its
+// first positive root, written without cancellation for the sign of h1.  Capped at |p| / 2 inside and 4
+// outside (beyond the bounding sphere).  Toward the surface it closes in quadratically; away from it, it
+// leaves the boundary band in one step.
+__device__ __forceinline__ float curve_step(const Geo& q, float rp, float h0, float h1, bool in_medium)
 {
     const float H = q.A * q.k * q.k + (in_medium ? __fdividef(2.0f, rp) : 0.0f);
     const float cap = in_medium ? 0.5f * rp : 4.0f;
-    const float h0 = fmaxf(hs, 0.0f);
-    const float s = H > 0.0f ? __fdividef(h1 + sqrtf(fmaf(h1, h1, 2.0f * H * h0)), H) : cap;
-    return fmaxf(kEps, fminf(s, cap));
+    const float x = fmaf(h1, h1, 2.0f * H * h0);
+    const float sq = x > 0.0f ? x * rsqrtf(x) : 0.0f;
+    const float s = h1 < 0.0f ? __fdividef(2.0f * h0, sq - h1) : (H > 0.0f ? __fdividef(h1 + sq, H) : cap);
+    return fminf(s, cap);
 }
 
-__device__ __forceinline__ V sdf_grad(const Geo& q, V p)
+// f at p with its parts (|p| and R(p)) and its derivative along the unit direction w.
+__device__ __forceinline__ float sdf_parts_grad(const Geo& q, V p, V w, float* rp, float* R0, float* gd)
 {
+    const float d2 = dot(p, p);
+    const float ir = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
     float sx, cx, sy, cy, sz, cz;
     __sincosf(q.k * p.x, &sx, &cx);
     __sincosf(q.k * p.y, &sy, &cy);
     __sincosf(q.k * p.z, &sz, &cz);
-    const float inv = rsqrtf(dot(p, p));
-    const float ak = q.A * q.k;
-    return v3(p.x * inv - ak * cx * sy * sz, p.y * inv - ak * sx * cy * sz, p.z * inv - ak * sx * sy * cz);
+    *rp = d2 * ir;
+    *R0 = fmaf(q.A, sx * sy * sz, 1.0f);
+    const float ds = fmaf(cx * sy * sz, w.x, fmaf(sx * cy * sz, w.y, sx * sy * cz * w.z));
+    *gd = fmaf(-q.A * q.k, ds, dot(p, w) * ir);
+    return *rp - *R0;
 }
 
 __device__ __forceinline__ float hg_pdf(float cosang, float g)
@@ -559,19 +566,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 st = kPending;
                 continue;
             }
-            float rp, R0;
-            const float f = sdf_parts(geo, r, &rp, &R0);
+            float rp, R0, gd;
+            const float f = sdf_parts_grad(geo, r, md, &rp, &R0, &gd);
             cnt[8] += 1u;
-            float d = (in_medium ? -f : f) * geo.inv_lip;
+            const float hs = in_medium ? -f : f, h1 = in_medium ? -gd : gd;   // the marched side's distance
+            float d = hs * geo.inv_lip;
             bool crossing = false, escape = false;
             if (d < kEps) {
+                // boundary band: on the surface; the ray crosses if it moves to the other side
                 cnt[9] += 1u;
-                const float gd = dot(sdf_grad(geo, r), md);
-                const float h1 = in_medium ? -gd : gd;       // rate of the marched side's distance
                 crossing = h1 < 0.0f;
-                d = band_step(geo, rp, in_medium ? -f : f, h1, in_medium);
+                d = fmaxf(kEps, curve_step(geo, rp, fmaxf(hs, 0.0f), h1, in_medium));
             } else {
-                d = fmaxf(d, safe_step(geo, r, md, rp, R0, f, in_medium, &escape));
+                d = fmaxf(fmaxf(d, safe_step(geo, r, md, rp, R0, f, in_medium, &escape)),
+                          curve_step(geo, rp, hs, h1, in_medium));
             }
             if (escape) {                                    // the surface is out of reach along the ray
                 ev = shadow ? kEvShadowDone : kEvEscape;

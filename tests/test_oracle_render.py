@@ -288,3 +288,50 @@ def test_band_step_on_the_sphere(orc):
         s = orc.band_step(0.0, 6.0, (1 - 1e-9) * u, w_in)
         assert s <= 2 * c and s >= min(0.5 * c, 0.5) - 1e-12, (c, s)
         assert orc.band_step(0.0, 6.0, (1 - 1e-9) * u, w_out) == -1.0
+
+
+@pytest.mark.parametrize("A,k", [(0.1, 6.0), (0.2, 4.0), (0.05, 10.0)])
+def test_march_step_never_crosses_and_closes_in(orc, A, k):
+    """One march step (the largest of the Lipschitz, radial-plus-Lipschitz and curvature steps) against dense
+    sampling of f, from points inside and outside at distances 1e-3 .. 0.3 from the surface in random
+    directions: the surface is never met within the step.  Aimed at the surface along its normal from close
+    by, the step covers nearly all of the gap (at least 90 % from 1e-3 .. 1e-2 away): the curvature step
+    converges quadratically where the Lipschitz step alone would cover 1 / (1 + A k) of it."""
+    rng = np.random.default_rng(int(7 * k))
+    f = _disp_sdf(A, k)
+    surf = _radial_surface_points(f, 600, rng)
+    checked = 0
+    for p in surf:
+        n = _disp_grad(A, k, p)
+        n /= np.linalg.norm(n)
+        side = rng.choice([-1.0, 1.0])
+        gap = 10 ** rng.uniform(-3, math.log10(0.3))
+        x = p + side * gap * n
+        if side * f(x) < 2e-4:
+            continue                                    # not on the chosen side at that distance
+        w = rng.standard_normal(3)
+        w /= np.linalg.norm(w)
+        s = orc.march_step(A, k, x, w)
+        if s == math.inf:
+            assert side > 0                             # escape: outside only, and never meets the surface
+            tt = np.linspace(0.0, 6.0, 60001)[1:]
+            assert np.all(f(x + tt[:, None] * w) > -1e-12), (x, w)
+            continue
+        assert s > 0, (x, w, s)
+        tt = np.linspace(0.0, s, 4001)[1:]
+        assert np.all(side * f(x + tt[:, None] * w) > -1e-12), (x, w, s)
+        checked += 1
+    assert checked > 300
+    ratios = []
+    for p in surf[:200]:
+        n = _disp_grad(A, k, p)
+        n /= np.linalg.norm(n)
+        for side in (-1.0, 1.0):
+            x = p + side * rng.uniform(1e-3, 1e-2) * n
+            w = -side * n
+            tt = np.linspace(0.0, 0.05, 50001)
+            h = side * f(x + tt[:, None] * w)
+            cross = tt[np.nonzero(h < 0)[0][0]]
+            ratios.append(orc.march_step(A, k, x, w) / cross)
+    ratios = np.array(ratios)
+    assert ratios.max() < 1.0 and np.median(ratios) > 0.9, (ratios.max(), np.median(ratios))
