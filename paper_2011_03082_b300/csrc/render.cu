@@ -139,21 +139,24 @@ __device__ __forceinline__ float safe_step(const Geo& q, V p, V w, float rp, flo
 // first positive root, written without cancellation for the sign of h1.  Capped at |p| / 2 inside and 4
 // outside (beyond the bounding sphere).  Toward the surface it closes in quadratically; away from it, it
 // leaves the boundary band in one step.
-__device__ __forceinline__ float curve_step(const Geo& q, float rp, float h0, float h1, bool in_medium)
+__device__ __forceinline__ float curve_step(const Geo& q, float ir, float rp, float h0, float h1, bool in_medium)
 {
-    const float H = q.A * q.k * q.k + (in_medium ? __fdividef(2.0f, rp) : 0.0f);
+    const float H = q.A * q.k * q.k + (in_medium ? 2.0f * ir : 0.0f);     // ir = 1 / |p|
     const float cap = in_medium ? 0.5f * rp : 4.0f;
     const float x = fmaf(h1, h1, 2.0f * H * h0);
     const float sq = x > 0.0f ? x * rsqrtf(x) : 0.0f;
-    const float s = h1 < 0.0f ? __fdividef(2.0f * h0, sq - h1) : (H > 0.0f ? __fdividef(h1 + sq, H) : cap);
-    return fminf(s, cap);
+    const bool toward = h1 < 0.0f;
+    const float num = toward ? 2.0f * h0 : h1 + sq;
+    const float den = toward ? sq - h1 : H;
+    return (toward || H > 0.0f) ? fminf(__fdividef(num, den), cap) : cap;
 }
 
-// f at p with its parts (|p| and R(p)) and its derivative along the unit direction w.
-__device__ __forceinline__ float sdf_parts_grad(const Geo& q, V p, V w, float* rp, float* R0, float* gd)
+// f at p with its parts (|p|, 1 / |p| and R(p)) and its derivative along the unit direction w.
+__device__ __forceinline__ float sdf_parts_grad(const Geo& q, V p, V w, float* rp, float* irp, float* R0, float* gd)
 {
     const float d2 = dot(p, p);
     const float ir = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+    *irp = ir;
     float sx, cx, sy, cy, sz, cz;
     __sincosf(q.k * p.x, &sx, &cx);
     __sincosf(q.k * p.y, &sy, &cy);
@@ -566,21 +569,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 st = kPending;
                 continue;
             }
-            float rp, R0, gd;
-            const float f = sdf_parts_grad(geo, r, md, &rp, &R0, &gd);
+            float rp, irp, R0, gd;
+            const float f = sdf_parts_grad(geo, r, md, &rp, &irp, &R0, &gd);
             cnt[8] += 1u;
             const float hs = in_medium ? -f : f, h1 = in_medium ? -gd : gd;   // the marched side's distance
-            float d = hs * geo.inv_lip;
-            bool crossing = false, escape = false;
-            if (d < kEps) {
-                // boundary band: on the surface; the ray crosses if it moves to the other side
-                cnt[9] += 1u;
-                crossing = h1 < 0.0f;
-                d = fmaxf(kEps, curve_step(geo, rp, fmaxf(hs, 0.0f), h1, in_medium));
-            } else {
-                d = fmaxf(fmaxf(d, safe_step(geo, r, md, rp, R0, f, in_medium, &escape)),
-                          curve_step(geo, rp, hs, h1, in_medium));
-            }
+            const float dl = hs * geo.inv_lip;
+            // boundary band: the point is on the surface; the ray crosses there if it moves to the other side,
+            // else steps off with the curvature step.  Elsewhere: the largest of the three steps.  (Selects,
+            // not branches: most iterations hold lanes of both kinds.)
+            const bool band = dl < kEps;
+            cnt[9] += band ? 1u : 0u;
+            const float cs = curve_step(geo, irp, rp, band ? fmaxf(hs, 0.0f) : hs, h1, in_medium);
+            bool escape;
+            const float ss = safe_step(geo, r, md, rp, R0, f, in_medium, &escape);
+            const bool crossing = band && h1 < 0.0f;
+            escape = escape && !band;
+            float d = band ? fmaxf(kEps, cs) : fmaxf(fmaxf(dl, ss), cs);
             if (escape) {                                    // the surface is out of reach along the ray
                 ev = shadow ? kEvShadowDone : kEvEscape;
                 st = kPending;
