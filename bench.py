@@ -132,23 +132,23 @@ def oracle_paths_per_second(models_np, budget_s: float, sigmas=SIGMAS, mode=1):
     from paper_2011_03082_b300 import synth
     decs = [(models_np[k].astype(np.float64), *synth.MODEL_SHAPES[k]) for k in ("length", "path", "event")]
     side = 64
-    # calibrate on one sample per pixel of the same image (large enough that thread start-up is negligible),
-    # then size the real sample
-    t0 = time.perf_counter()
-    cal_paths = 0
-    for s in sigmas:
-        _, st, _ = oracle.render(synth.render_scene(s, width=side, height=side, spp=1, mode=mode), decs)
-        cal_paths += int(st[0])
-    per_path = (time.perf_counter() - t0) / max(1, cal_paths)
-    n_target = max(4096, int(budget_s / max(per_path, 1e-9) / len(sigmas)))
-    spp = max(1, n_target // (side * side))
-    paths = 0
-    threads = 0
-    t0 = time.perf_counter()
-    for s in sigmas:
-        _, st, threads = oracle.render(synth.render_scene(s, width=side, height=side, spp=spp, mode=mode), decs)
-        paths += int(st[0])
-    dt = time.perf_counter() - t0
+
+    def sample(spp):
+        paths, threads = 0, 0
+        t0 = time.perf_counter()
+        for s in sigmas:
+            _, st, threads = oracle.render(synth.render_scene(s, width=side, height=side, spp=spp, mode=mode), decs)
+            paths += int(st[0])
+        return paths, time.perf_counter() - t0, threads
+
+    # grow the sample (same image, more samples per pixel) until one run fills at least half the budget;
+    # the last run is the one reported
+    spp = 1
+    while True:
+        paths, dt, threads = sample(spp)
+        if dt >= 0.5 * budget_s or spp >= 1 << 16:
+            break
+        spp = int(min(max(2 * spp, spp * 0.9 * budget_s / max(dt, 1e-3)), 1 << 16))
     return dict(value=paths / dt, unit=UNIT, cores=int(threads), kind="oracle",
                 sample=f"{side}x{side} px x {spp} spp at each sigma_t in {list(sigmas)} "
                        f"({'sphere tracing' if mode else 'brute force'} + NEE, same scene and decoders), "
