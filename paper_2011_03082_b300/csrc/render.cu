@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             // ================= transition round: what follows each finished march =================
             if (st == kPending) {
                 const Req& q = B.r[req];
-                bool need_flight = false;
+                bool need_flight = false, finish = false;   // one end_path call site for the whole round
                 if (ev == kEvShadowDone) {
                     cnt[7] += 1u;
                     if (capped) {
@@ -478,8 +478,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                         const float rho = hg_pdf(dot(nW, md), q.g);
                         acc += nwt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
                     }
-                    if (end_after) end_path();
-                    else need_flight = true;
+                    finish = end_after;
+                    need_flight = !end_after;
                 } else if (ev == kEvCollide) {
                     const V c = mo + md * ml;
                     bool sphere = false;
@@ -526,12 +526,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                     need_flight = true;
                 } else {
                     if (ev == kEvCap) cnt[6] += 1u;
-                    end_path();
+                    finish = true;
                 }
                 if (need_flight) {
                     if (seg >= q.max_segments) {
                         cnt[6] += 1u;
-                        end_path();
+                        finish = true;
                     } else {
                         cnt[2] += 1u;
                         const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
@@ -547,6 +547,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                         st = kFlight;
                     }
                 }
+                if (finish) end_path();
             }
             continue;
         }
