@@ -223,8 +223,9 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
 }
 
 constexpr int kUsedStats = 10;
-constexpr int kDrawKeys = 26 * 16;   // staging-tile offset of the draw keys (5 words per row) in a decoder round
-static_assert(kDrawKeys + 5 * 16 <= mmadec::kStageFloats, "decoder-round draws exceed the staging tile");
+constexpr int kDraws = 26 * 16;      // a decoder round's draws: value v of row r at [v * 16 + r]
+constexpr int kDrawKeys = 0;         // staging-tile offset of the draw keys (5 words per row) in a decoder round
+static_assert(kDrawKeys + 5 * 16 <= mmadec::kStageFloats, "decoder-round draw keys exceed the staging tile");
 
 // Scheduling constants of a kernel variant (see ms_render_autotune): kDecodeBatch parked lanes trigger a
 // decoder round, kTransBatch pending (or idle) lanes a transition (or refill) round, and between two
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     constexpr int kRefillBatch = kTransBatch;
     __shared__ __align__(16) unsigned char sw[kBytesL + kBytesP + kBytesE];
     __shared__ float s_stage[kThreads / 32][mmadec::kStageFloats];
+    __shared__ float s_draws[kLearned ? kThreads / 32 : 1][kLearned ? kDraws : 1];
     __shared__ unsigned long long s_stats[kMaxReq * kStats];
     const int tid = threadIdx.x, lane = tid & 31;
     constexpr bool learned = kLearned;
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     unsigned char* wpth = sw + kBytesL;
     unsigned char* wev = sw + kBytesL + kBytesP;
     float* stage = s_stage[tid >> 5];
+    float* draws = s_draws[kLearned ? tid >> 5 : 0];
     if constexpr (learned) {
         mmadec::stage_weights<false, 1>(wl, B.wL, 2 + kLatL, 1);
         mmadec::stage_weights<false, 2>(wpth, B.wP, 3 + kLatP, 3);
@@ -374,45 +377,39 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 const uint32_t* kr = keys + 5 * r;
                 const Words wd = philox(kr[2], kr[0], kr[1], 1u + (uint32_t)c, kr[3], kr[4]);
                 if (c == 0) {
-                    stage[24 * 16 + r] = u24(wd.w0);
-                    stage[25 * 16 + r] = u24(wd.w1);
+                    draws[24 * 16 + r] = u24(wd.w0);
+                    draws[25 * 16 + r] = u24(wd.w1);
                 } else {
                     const float2 a = box_muller(wd.w0, wd.w1), b = box_muller(wd.w2, wd.w3);
-                    float* o = stage + 4 * (c - 1) * 16 + r;
+                    float* o = draws + 4 * (c - 1) * 16 + r;
                     o[0] = a.x; o[16] = a.y; o[32] = b.x; o[48] = b.y;
                 }
             }
             __syncwarp();
-            float n[24];
-            float u_abs = 0.0f, u_psi = 0.0f;
+            // the row's draws are read where they are used (they stay in shared memory, not in registers)
+            const int rr = mine ? rank : 0;
+            auto nrm = [&](int v) -> float { return draws[v * 16 + rr]; };
             float ltau = 0.0f;
             if (mine) {
                 cnt[3] += 1u;
-#pragma unroll
-                for (int v = 0; v < 24; ++v) n[v] = stage[v * 16 + rank];
-                u_abs = stage[24 * 16 + rank];
-                u_psi = stage[25 * 16 + rank];
                 ltau = __logf(tau);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 24; ++k) n[k] = 0.0f;
             }
-            __syncwarp();
             // LengthGen: N (albedo-1 physics, Eq. 3)
-            float xin[16] = {ltau, mine ? qq.g : 0.0f, n[kZL], n[kZL + 1]};
+            float xin[16] = {ltau, mine ? qq.g : 0.0f, nrm(kZL), nrm(kZL + 1)};
             float yL[8];
             mmadec::warp_mlp_rows16<1, 3, false, 1>(wl, stage, xin, yL, rank, mine);
-            const float yN = yL[0] + __expf(0.5f * yL[1]) * n[kEL];
+            const float yN = yL[0] + __expf(0.5f * yL[1]) * nrm(kEL);
             float N = floorf(__expf(yN) + 0.5f);
             N = fminf(fmaxf(N, 1.0f), kNMax);
             const float lnN = mine ? __logf(N) : 0.0f;
             // PathGen: (cos theta, alpha, beta)
-            float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, n[kZP], n[kZP + 1], n[kZP + 2], n[kZP + 3], n[kZP + 4]};
+            float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, nrm(kZP), nrm(kZP + 1), nrm(kZP + 2), nrm(kZP + 3),
+                            nrm(kZP + 4)};
             float yP[8];
             mmadec::warp_mlp_rows16<1, 3, false, 2>(wpth, stage, xp, yP, rank, mine);
-            const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * n[kEP]));
-            float al = yP[1] + __expf(0.5f * yP[4]) * n[kEP + 1];
-            float be = yP[2] + __expf(0.5f * yP[5]) * n[kEP + 2];
+            const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * nrm(kEP)));
+            float al = yP[1] + __expf(0.5f * yP[4]) * nrm(kEP + 1);
+            float be = yP[2] + __expf(0.5f * yP[5]) * nrm(kEP + 2);
             float ab2 = al * al + be * be;
             if (ab2 > 1.0f) {
                 const float s = rsqrtf(ab2);
@@ -420,20 +417,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             }
             // EventGen: representative event (X~, W~)
             float xe[16] = {ltau, mine ? qq.g : 0.0f, mine ? qq.phi : 0.0f, ct, al, be, lnN,
-                            n[kZE], n[kZE + 1], n[kZE + 2], n[kZE + 3], n[kZE + 4]};
+                            nrm(kZE), nrm(kZE + 1), nrm(kZE + 2), nrm(kZE + 3), nrm(kZE + 4)};
             float yE[16];
             mmadec::warp_mlp_rows16<2, 3, false, 2>(wev, stage, xe, yE, rank, mine);
             if (mine) {
                 float e[6];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * n[kEE + k];
+                for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * nrm(kEE + k);
                 const float phiN = __expf(N * qq.log_phi);
                 const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
                 // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
                 V t1, t2;
                 onb(w, &t1, &t2);
                 float sn, cs;
-                sincos_turns_fast(u_psi, &sn, &cs);
+                sincos_turns_fast(nrm(25), &sn, &cs);
                 const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
                 const float nn = sqrtf(fmaxf(0.0f, 1.0f - ab2));
                 V vs[4] = {v3(stt, 0.0f, ct), v3(be * ct + nn * stt, al, -be * stt + nn * ct), v3(e[0], e[1], e[2]),
@@ -451,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 nX = p + vw[2] * rad;                   // p holds the collision point c
                 nW = unit(vw[3]);
                 nwt = lam;
-                if (u_abs >= phiN) {
+                if (nrm(24) >= phiN) {
                     cnt[5] += 1u;
                     end_after = true;
                 } else {
