@@ -1,118 +1,23 @@
 // ms_cvae_infer: batched CVAE decoder sampling (Sec. 3.2) — x = mu + exp(log Sigma / 2) eps with
 // (mu, log Sigma) = Dec([c; z]) and z, eps standard normal.
 //
-// Single precision: one query per thread over a grid-stride loop; the block stages the decoder weights in
-// shared memory once (decoder.cuh); z and eps are read from the caller or drawn in registers from the query's
-// Philox counter.  Half precision (FP16/BF16 with FP32 accumulation) is decoder_mma.cu.
+// Every precision runs on the tensor cores (mma.sync m16n8k16, FP32 accumulation; decoder_mma.cuh), 32 queries
+// per warp over a grid-stride loop; the block stages the decoder weights once in shared memory in fragment
+// order; z and eps are read from the caller or drawn from the query's Philox counter.
+//   MS_FP32: weights and activations split into FP16 head + tail, three products per tile (about 22
+//            significant bits: single-precision results, max |error| <= 1e-5 on the outputs);
+//   MS_FP16 / MS_BF16: weights rounded once to half precision, activations split into head + tail (two
+//            products per tile), so the result is that of the rounded weights.
 #include "decoder.cuh"
 #include "decoder_mma.cuh"
 
 namespace ms {
 namespace dec {
 
-constexpr int kInferThreads = 256;
-
-template <int IN4, int P, int W>
-__global__ void __launch_bounds__(kInferThreads, 2) infer_f32(const float* __restrict__ wts, int p_in, int latent,
-                                                              const float* __restrict__ cond,
-                                                              const float* __restrict__ z_eps, uint64_t seed,
-                                                              uint64_t offset, uint64_t n, float* __restrict__ mlv,
-                                                              float* __restrict__ smp)
-{
-    __shared__ __align__(16) float s[smem_floats<W>(IN4, P)];
-    // per-thread staging row: [c ; z] in the first IN4 entries, then eps (dynamic offsets stay in shared memory)
-    __shared__ __align__(16) float row[kInferThreads][IN4 + 8];
-    stage_weights<W>(s, wts, p_in + latent, IN4, P);
-    __syncthreads();
-    float* my = row[threadIdx.x];
-    const int nz = latent + P;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-#pragma unroll
-        for (int k = 0; k < IN4 + 8; ++k) my[k] = 0.0f;
-        for (int k = 0; k < p_in; ++k) my[k] = cond[q * p_in + k];
-        if (z_eps) {
-            for (int m = 0; m < nz; ++m) my[m < latent ? p_in + m : IN4 + m - latent] = z_eps[q * nz + m];
-        } else {
-            const Stream st(seed, offset + q);
-            for (int j = 0; 4 * j < nz; ++j) {
-                const float4 v = normals4(st, (uint32_t)j, 0xD0u);
-                const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int m = 4 * j + t;
-                    if (m < nz) my[m < latent ? p_in + m : IN4 + m - latent] = vv[t];
-                }
-            }
-        }
-        float x[IN4];
-#pragma unroll
-        for (int k = 0; k < IN4; k += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(my + k);
-            x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
-        }
-        float y[pad4(2 * P)];
-        mlp<IN4, P, W>(s, x, y);
-        if (mlv) {
-#pragma unroll
-            for (int o = 0; o < 2 * P; ++o) mlv[q * (2 * P) + o] = y[o];
-        }
-        if (smp) {
-#pragma unroll
-            for (int o = 0; o < P; ++o) smp[q * P + o] = y[o] + __expf(0.5f * y[P + o]) * my[IN4 + o];
-        }
-    }
-}
-
-template <int IN4, int P, int W>
-cudaError_t launch_f32(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
-                       uint64_t n, float* mlv, float* smp, cudaStream_t stream)
-{
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_f32<IN4, P, W>, kInferThreads, 0);
-    if (e != cudaSuccess) return e;
-    uint64_t grid = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const uint64_t need = (n + kInferThreads - 1) / kInferThreads;
-    if (grid > need) grid = need;
-    infer_f32<IN4, P, W><<<(unsigned)grid, kInferThreads, 0, stream>>>(d.weights, d.p_in, d.latent, cond, z_eps,
-                                                                       seed, offset, n, mlv, smp);
-    return cudaGetLastError();
-}
-
-template <int IN4, int W>
-cudaError_t dispatch_p(const ms_decoder& d, const float* c, const float* z, uint64_t seed, uint64_t off, uint64_t n,
-                       float* mlv, float* smp, cudaStream_t s)
-{
-    switch (d.p_out) {
-    case 1: return launch_f32<IN4, 1, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 2: return launch_f32<IN4, 2, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 3: return launch_f32<IN4, 3, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 4: return launch_f32<IN4, 4, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 5: return launch_f32<IN4, 5, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 6: return launch_f32<IN4, 6, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 7: return launch_f32<IN4, 7, W>(d, c, z, seed, off, n, mlv, smp, s);
-    default: return launch_f32<IN4, 8, W>(d, c, z, seed, off, n, mlv, smp, s);
-    }
-}
-
-template <int W>
-cudaError_t dispatch_in(const ms_decoder& d, const float* c, const float* z, uint64_t seed, uint64_t off, uint64_t n,
-                        float* mlv, float* smp, cudaStream_t s)
-{
-    switch (pad4(d.p_in + d.latent)) {
-    case 4: return dispatch_p<4, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 8: return dispatch_p<8, W>(d, c, z, seed, off, n, mlv, smp, s);
-    case 12: return dispatch_p<12, W>(d, c, z, seed, off, n, mlv, smp, s);
-    default: return dispatch_p<16, W>(d, c, z, seed, off, n, mlv, smp, s);
-    }
-}
-
-// Half precision: 32 queries per warp on the tensor cores (decoder_mma.cuh).  The weights are rounded once to
-// FP16 / BF16; inputs and hidden activations are carried as head + tail halves (two products per tile), and
-// accumulation is FP32, so the result is that of the rounded weights to about 1e-4.
+// Runtime-shaped kernel (any supported shape): rows are staged through shared memory.
 constexpr int kMmaThreads = 128;
 
-template <int NT3, int NTH, bool kBF16>
+template <int NT3, int NTH, bool kBF16, int kSplit>
 __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict__ wts, int p_in, int latent, int p_out,
                                                          const float* __restrict__ cond, const float* __restrict__ z_eps,
                                                          uint64_t seed, uint64_t offset, uint64_t n,
@@ -152,7 +57,7 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict
 #pragma unroll
         for (int k = 0; k < 16; ++k) x[k] = my[k];
         float y[8 * NT3];
-        mmadec::warp_mlp<NT3, 2, kBF16, NTH>(wsm, stage[warp], x, y);
+        mmadec::warp_mlp<NT3, kSplit, kBF16, NTH>(wsm, stage[warp], x, y);
         if (live) {
 #pragma unroll
             for (int j = 0; j < 8 * NT3; ++j) my[24 + j] = y[j];
@@ -168,12 +73,15 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict
 cudaError_t launch_infer_mma(const ms_decoder& d, const float* cond, const float* z_eps, uint64_t seed, uint64_t offset,
                              uint64_t n, float* mlv, float* smp, cudaStream_t stream)
 {
-    const bool bf16 = d.precision == MS_BF16, w8 = d.width == 8;
-    const int nt3 = mmadec::n_tiles_out(d.p_out);
-    auto kern = bf16 ? (nt3 == 1 ? (w8 ? infer_mma<1, 1, true> : infer_mma<1, 2, true>)
-                                 : (w8 ? infer_mma<2, 1, true> : infer_mma<2, 2, true>))
-                     : (nt3 == 1 ? (w8 ? infer_mma<1, 1, false> : infer_mma<1, 2, false>)
-                                 : (w8 ? infer_mma<2, 1, false> : infer_mma<2, 2, false>));
+    const bool w8 = d.width == 8, one = mmadec::n_tiles_out(d.p_out) == 1;
+    auto kern = d.precision == MS_BF16
+                    ? (one ? (w8 ? infer_mma<1, 1, true, 2> : infer_mma<1, 2, true, 2>)
+                           : (w8 ? infer_mma<2, 1, true, 2> : infer_mma<2, 2, true, 2>))
+                : d.precision == MS_FP16
+                    ? (one ? (w8 ? infer_mma<1, 1, false, 2> : infer_mma<1, 2, false, 2>)
+                           : (w8 ? infer_mma<2, 1, false, 2> : infer_mma<2, 2, false, 2>))
+                    : (one ? (w8 ? infer_mma<1, 1, false, 3> : infer_mma<1, 2, false, 3>)
+                           : (w8 ? infer_mma<2, 1, false, 3> : infer_mma<2, 2, false, 3>));
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMmaThreads, 0);
     if (e != cudaSuccess) return e;
@@ -187,7 +95,7 @@ cudaError_t launch_infer_mma(const ms_decoder& d, const float* cond, const float
 
 // ---- shape-specialised kernels (the shapes in use: the decoder benchmark's and Table 1's) ----
 // The query's row [c; z] and its eps are built in registers with compile-time indices, and rows are read and
-// written with the widest aligned vector accesses; the runtime-shaped kernels above stage them through shared
+// written with the widest aligned vector accesses; the runtime-shaped kernel above stages them through shared
 // memory instead.
 
 template <int N>
@@ -250,37 +158,7 @@ __device__ __forceinline__ void query_normals(const float* __restrict__ z_eps, u
     for (int m = 0; m < P; ++m) eps[m] = nz[L + m];
 }
 
-template <int PI, int L, int P, int W>
-__global__ void __launch_bounds__(kInferThreads, 2) infer_f32_fixed(const float* __restrict__ wts,
-                                                                    const float* __restrict__ cond,
-                                                                    const float* __restrict__ z_eps, uint64_t seed,
-                                                                    uint64_t offset, uint64_t n,
-                                                                    float* __restrict__ mlv, float* __restrict__ smp)
-{
-    constexpr int IN4 = pad4(PI + L), O4 = pad4(2 * P);
-    __shared__ __align__(16) float s[smem_floats<W>(IN4, P)];
-    stage_weights<W>(s, wts, PI + L, IN4, P);
-    __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        float x[IN4], eps[P];
-#pragma unroll
-        for (int k = 0; k < IN4; ++k) x[k] = 0.0f;
-        load_row<PI>(cond + q * PI, x);
-        query_normals<PI, L, P>(z_eps, seed, offset + q, q, x, eps);
-        float y[O4];
-        mlp<IN4, P, W>(s, x, y);
-        if (mlv) store_row<2 * P>(mlv + q * (2 * P), y);
-        if (smp) {
-            float o[P];
-#pragma unroll
-            for (int k = 0; k < P; ++k) o[k] = y[k] + __expf(0.5f * y[P + k]) * eps[k];
-            store_row<P>(smp + q * P, o);
-        }
-    }
-}
-
-template <int PI, int L, int P, int NTH, bool kBF16>
+template <int PI, int L, int P, int NTH, bool kBF16, int kSplit>
 __global__ void __launch_bounds__(kMmaThreads) infer_mma_fixed(const float* __restrict__ wts,
                                                                const float* __restrict__ cond,
                                                                const float* __restrict__ z_eps, uint64_t seed,
@@ -308,7 +186,7 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma_fixed(const float* __re
             query_normals<PI, L, P>(z_eps, seed, offset + q, q, x, eps);
         }
         float y[8 * NT3];
-        mmadec::warp_mlp<NT3, 2, kBF16, NTH>(wsm, stage[warp], x, y);
+        mmadec::warp_mlp<NT3, kSplit, kBF16, NTH>(wsm, stage[warp], x, y);
         if (live) {
             if (mlv) store_row<2 * P>(mlv + q * (2 * P), y);
             if (smp) {
@@ -348,13 +226,13 @@ bool launch_fixed(const ms_decoder& d, const float* cond, const float* z_eps, ui
 #define MS_FIXED_CASE(pi, l, p, w)                                                                            \
     if (d.p_in == pi && d.latent == l && d.p_out == p && d.width == w) {                                      \
         if (d.precision == MS_FP32)                                                                            \
-            *err = launch_grid(infer_f32_fixed<pi, l, p, w>, kInferThreads, kInferThreads, n, s, d, cond, z_eps, \
-                               seed, offset, mlv, smp);                                                        \
+            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, false, 3>, kMmaThreads, kMmaThreads, n, s, d,   \
+                               cond, z_eps, seed, offset, mlv, smp);                                           \
         else if (d.precision == MS_BF16)                                                                       \
-            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, true>, kMmaThreads, kMmaThreads, n, s, d, cond, \
-                               z_eps, seed, offset, mlv, smp);                                                 \
+            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, true, 2>, kMmaThreads, kMmaThreads, n, s, d,    \
+                               cond, z_eps, seed, offset, mlv, smp);                                           \
         else                                                                                                   \
-            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, false>, kMmaThreads, kMmaThreads, n, s, d,      \
+            *err = launch_grid(infer_mma_fixed<pi, l, p, w / 8, false, 2>, kMmaThreads, kMmaThreads, n, s, d,   \
                                cond, z_eps, seed, offset, mlv, smp);                                           \
         return true;                                                                                           \
     }
@@ -385,13 +263,6 @@ extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const
         MS_CUDA(fe);
         return MS_OK;
     }
-    if (d->precision != MS_FP32) {
-        MS_CUDA(ms::dec::launch_infer_mma(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s));
-        return MS_OK;
-    }
-    const cudaError_t e =
-        d->width == 8 ? ms::dec::dispatch_in<8>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s)
-                      : ms::dec::dispatch_in<16>(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s);
-    MS_CUDA(e);
+    MS_CUDA(ms::dec::launch_infer_mma(*d, cond, z_eps, seed, offset, n, out_mean_logvar, out_sample, s));
     return MS_OK;
 }

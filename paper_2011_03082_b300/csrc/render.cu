@@ -14,16 +14,15 @@
 //    converged on the same short loop body however long the individual marches are; a lane whose path ends
 //    takes the next camera sample at once (warp-aggregated ticket);
 //  * a lane that reaches a sphere step parks in the decode state; the warp runs the three decoder MLPs only
-//    when at least kDecodeBatch of its lanes are parked (or nothing else is marching), so the decoders —
-//    weights in shared memory, broadcast float4 loads (decoder.cuh) — run on mostly full warps while the
-//    other lanes keep marching, with no block or grid barrier in the loop;
+//    when at least kDecodeBatch of its lanes are parked (or nothing else is marching), on one 16-row
+//    tensor-core tile of up to 16 parked lanes (weights in shared memory in fragment order, decoder_mma.cuh),
+//    while the other lanes keep marching, with no block or grid barrier in the loop;
 //  * a path's NEE sum is kept in a register and added to its pixel (double) once; counters are per-lane
 //    registers flushed to shared, then global, memory;
 //  * everything is bounded: segments per path, steps per march, and the loop ends when the ticket is drained
 //    and no lane holds a path.
 #include <cmath>
 
-#include "decoder.cuh"
 #include "decoder_mma.cuh"
 #include "ms_device.cuh"
 
