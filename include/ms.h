@@ -120,8 +120,10 @@ typedef struct {
     int32_t latent;             /* latent size L, 1..8 (p_in + latent <= 16)                          */
     int32_t width;              /* hidden width W, 8 or 16                                             */
     int32_t p_out;              /* output size P, 1..8                                                 */
-    int32_t precision;          /* MS_FP32 (FP32 FMA), or MS_FP16 / MS_BF16: tensor cores, weights rounded
-                                   to FP16 / BF16, activations carried as two halves, FP32 accumulation */
+    int32_t precision;          /* all on the tensor cores with FP32 accumulation.  MS_FP32: weights and
+                                   activations split into FP16 head + tail, three products per tile
+                                   (single-precision results, max |error| <= 1e-5); MS_FP16 / MS_BF16:
+                                   weights rounded to FP16 / BF16, activations carried as two halves  */
     const float* weights;       /* device, packed float32: W1[W][p_in+L] b1[W] W2[W][W] b2[W]
                                    W3[2P][W] b3[2P] (row-major [out][in])                              */
 } ms_decoder;
