@@ -60,7 +60,12 @@ int ms_version(void);
  * Russian roulette continues with probability albedo and the new direction is drawn from the HG phase
  * function (cosine between old and new propagation direction, mean g); the walk ends at the first crossing
  * of the sphere.  N counts events including the one at the centre; an absorbed photon's N is the event at
- * which it was absorbed.
+ * which it was absorbed.  Random numbers of photon id at step s come from Philox4x32-10 counter
+ * (s, id_lo, id_hi, tag) under key seed: tag 0 gives the free path, HG cosine, azimuth and roulette uniforms
+ * (MS_FP32: word >> 8 as 24-bit uniforms; MS_FP64: 53-bit uniforms with the tag 2 words as low bits), and the
+ * bits those leave unused give the reservoir's uniform (MS_FP32: the low bytes of words 0..2; MS_FP64: the low
+ * 11 bits of the tag 2 words 0..2); tag 1 (and 3) at step 0 gives an isotropic start with an event at the
+ * centre.
  * ---------------------------------------------------------------------------------------------------- */
 typedef struct {
     float optical_radius;       /* sigma_t * R > 0                                  */

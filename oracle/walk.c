@@ -11,7 +11,10 @@
  * Random numbers per photon id and event step s (counter = (s, id_lo, id_hi, tag), key = seed):
  *   tag 0 words (hi) and, for 53-bit uniforms, tag 2 words (lo):
  *       u0 free path, u1 HG cosine (or start z), u2 azimuth, u3 roulette;
- *   tag 1 (hi) / tag 3 (lo): a0 reservoir, a2 a3 isotropic start direction when an event sits at the centre.
+ *       the reservoir uniform from the bits those four leave unused: with 24-bit uniforms
+ *       ((hi0 & 0xff) << 16 | (hi1 & 0xff) << 8 | (hi2 & 0xff)) * 2^-24, with 53-bit uniforms
+ *       ((lo0 & 0x7ff) << 22 | (lo1 & 0x7ff) << 11 | (lo2 & 0x7ff)) * 2^-33;
+ *   tag 1 (hi) / tag 3 (lo): a2 a3 isotropic start direction when an event sits at the centre.
  * A 53-bit uniform is ((hi << 21) | (lo >> 11)) * 2^-53; a 24-bit uniform is (hi >> 8) * 2^-24.
  *
  * Everything is FP64 with only basic operations and the deterministic log/sincos/atan2 of detmath.c, so
@@ -59,7 +62,7 @@ int om_num_threads(int requested)
 
 static double dot3(ov3 a, ov3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-static void draw(const walk_job* J, uint64_t id, uint32_t step, uint32_t tag_hi, double u[4])
+static void draw(const walk_job* J, uint64_t id, uint32_t step, uint32_t tag_hi, double u[4], double* ures)
 {
     uint32_t key[2] = { (uint32_t)J->seed, (uint32_t)(J->seed >> 32) };
     uint32_t ctr[4] = { step, (uint32_t)id, (uint32_t)(id >> 32), tag_hi };
@@ -68,6 +71,8 @@ static void draw(const walk_job* J, uint64_t id, uint32_t step, uint32_t tag_hi,
     if (J->uniform_bits == 24) {
         for (int j = 0; j < 4; ++j)
             u[j] = (double)(hi[j] >> 8) * 0x1.0p-24;
+        if (ures)
+            *ures = (double)(((hi[0] & 0xffu) << 16) | ((hi[1] & 0xffu) << 8) | (hi[2] & 0xffu)) * 0x1.0p-24;
         return;
     }
     uint32_t lo[4];
@@ -75,6 +80,9 @@ static void draw(const walk_job* J, uint64_t id, uint32_t step, uint32_t tag_hi,
     om_philox(ctr, key, lo);
     for (int j = 0; j < 4; ++j)
         u[j] = (double)(((uint64_t)hi[j] << 21) | (uint64_t)(lo[j] >> 11)) * 0x1.0p-53;
+    if (ures)
+        *ures = (double)(((uint64_t)(lo[0] & 0x7ffu) << 22) | ((uint64_t)(lo[1] & 0x7ffu) << 11) |
+                         (uint64_t)(lo[2] & 0x7ffu)) * 0x1.0p-33;
 }
 
 /* Inverse CDF of the HG phase function (Eq. 1): cosine between old and new propagation direction. */
@@ -162,10 +170,10 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
 
     if (m->isotropic_start) {
         if (paper) {
-            draw(J, id, 0u, 1u, ua);
+            draw(J, id, 0u, 1u, ua, NULL);
             w = iso_dir(ua[2], ua[3]);
         } else {
-            draw(J, id, 0u, 0u, um);
+            draw(J, id, 0u, 0u, um, NULL);
             w = iso_dir(um[1], um[2]);
         }
     } else {
@@ -174,7 +182,8 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
     }
 
     for (uint32_t s = 0;; ++s) {
-        draw(J, id, s, 0u, um);
+        double ures;
+        draw(J, id, s, 0u, um, &ures);
         if (s > 0 || paper) {
             /* scattering event at p, arriving with direction w */
             if (n >= J->max_events) {
@@ -183,7 +192,6 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
             }
             n = n + 1;
             if (J->reservoir_mode) {
-                draw(J, id, s, 1u, ua);
                 double wk;
                 if (J->reservoir_mode == 1) {
                     wk = 1.0;
@@ -192,7 +200,7 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
                     wk = pw;
                 }
                 wsum = wsum + wk;
-                if (ua[0] * wsum < wk) {
+                if (ures * wsum < wk) {
                     rep_p = p;
                     rep_w = w;
                     rep_k = (int32_t)n;

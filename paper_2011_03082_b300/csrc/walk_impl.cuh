@@ -36,10 +36,14 @@ constexpr int kChunk = 32;
 
 struct F32 {
     using real = float;
-    static __device__ __forceinline__ void uniforms(const Stream& s, uint32_t step, uint32_t tag, real u[4])
+    // u[4]: the block's four 24-bit uniforms; *ures: a fifth from the low bytes those leave unused
+    static __device__ __forceinline__ void uniforms(const Stream& s, uint32_t step, uint32_t tag, real u[4],
+                                                    real* ures = nullptr)
     {
         const Words w = s.at(step, tag);
         u[0] = u24(w.w0); u[1] = u24(w.w1); u[2] = u24(w.w2); u[3] = u24(w.w3);
+        if (ures)
+            *ures = (float)(((w.w0 & 0xffu) << 16) | ((w.w1 & 0xffu) << 8) | (w.w2 & 0xffu)) * 0x1.0p-24f;
     }
     static __device__ __forceinline__ real log(real x) { return __logf(x); }
     static __device__ __forceinline__ void sincos_turns(real u, real* s, real* c) { sincos_turns_fast(u, s, c); }
@@ -53,10 +57,16 @@ struct F32 {
 
 struct F64 {
     using real = double;
-    static __device__ __forceinline__ void uniforms(const Stream& s, uint32_t step, uint32_t tag, real u[4])
+    // u[4]: 53-bit uniforms from the tag and tag + 2 blocks; *ures: a 33-bit uniform from the low 11 bits of
+    // the tag + 2 words, which those leave unused
+    static __device__ __forceinline__ void uniforms(const Stream& s, uint32_t step, uint32_t tag, real u[4],
+                                                    real* ures = nullptr)
     {
         const Words h = s.at(step, tag), l = s.at(step, tag + 2u);
         u[0] = u53(h.w0, l.w0); u[1] = u53(h.w1, l.w1); u[2] = u53(h.w2, l.w2); u[3] = u53(h.w3, l.w3);
+        if (ures)
+            *ures = (double)(((uint64_t)(l.w0 & 0x7ffu) << 22) | ((uint64_t)(l.w1 & 0x7ffu) << 11) |
+                             (uint64_t)(l.w2 & 0x7ffu)) * 0x1.0p-33;
     }
     static __device__ __forceinline__ real log(real x) { return det::log(x); }
     static __device__ __forceinline__ void sincos_turns(real u, real* s, real* c) { det::sincos_turns(u, s, c); }
@@ -238,8 +248,8 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(Job J)
 
         // ---- one scattering event and one free flight ----
         const Stream s(J.seed, J.offset + ph.i);
-        real u[4];
-        Pol::uniforms(s, ph.step, 0u, u);
+        real u[4], ures;
+        Pol::uniforms(s, ph.step, 0u, u, &ures);
         int done = -1;
         if (ph.step > 0u || ph.paper) {
             if (ph.n >= J.max_events) {
@@ -247,8 +257,6 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(Job J)
             } else {
                 ph.n += 1u;
                 if (J.reservoir) {
-                    real a[4];
-                    Pol::uniforms(s, ph.step, 1u, a);
                     real wk;
                     if (J.reservoir == 1) {
                         wk = (real)1;
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(Job J)
                         wk = ph.pw;
                     }
                     ph.wsum = ph.wsum + wk;
-                    if (a[0] * ph.wsum < wk) {
+                    if (ures * ph.wsum < wk) {
                         ph.rep_p = ph.p;
                         ph.rep_w = ph.w;
                         ph.rep_k = (int32_t)ph.n;

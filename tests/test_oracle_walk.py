@@ -165,6 +165,14 @@ def _u53(seed, pid, step, tag):
     return [mp.mpf((h << 21) | (l >> 11)) / mp.mpf(2) ** 53 for h, l in zip(hi, lo)]
 
 
+def _u_reservoir(seed, pid, step):
+    """The reservoir's uniform at a step: the low 11 bits of the tag 2 words 0..2, which the 53-bit uniforms
+    leave unused, as a 33-bit fraction."""
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    lo = philox_py([step, pid & 0xFFFFFFFF, pid >> 32, 2], key)
+    return mp.mpf(((lo[0] & 0x7FF) << 22) | ((lo[1] & 0x7FF) << 11) | (lo[2] & 0x7FF)) / mp.mpf(2) ** 33
+
+
 def _trace(seed, pid, sigma, g, phi, iso, paper, res_mode, max_events=10**6):
     mp.mp.dps = 60
     if iso:
@@ -187,11 +195,11 @@ def _trace(seed, pid, sigma, g, phi, iso, paper, res_mode, max_events=10**6):
                 break
             n += 1
             if res_mode:
-                a = _u53(seed, pid, s, 1)
+                a = _u_reservoir(seed, pid, s)
                 wk = 1 if res_mode == 1 else pw * phi
                 pw = wk if res_mode == 2 else pw
                 wsum += wk
-                if a[0] * wsum < wk:
+                if a * wsum < wk:
                     rep_k = n
             if res_mode != 2 and u[3] >= phi:
                 status = 1
