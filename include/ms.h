@@ -269,7 +269,9 @@ ms_status ms_sdf_grid_build(float disp_amp, float disp_freq, int32_t n, float* g
 /* The renderer's three decoders have the final shapes of Table 1 (the paper's D = 2 hidden layers):
  * LengthGen latent 2 width 8, PathGen latent 5 width 16, EventGen latent 5 width 16, all MS_FP32.  A sphere
  * step draws 22 normals n[0..21] (tags 2..7 of its segment, four per tag by Box-Muller): LengthGen z = n[0,1],
- * eps = n[2]; PathGen z = n[3..7], eps = n[8..10]; EventGen z = n[11..15], eps = n[16..21]. */
+ * eps = n[2]; PathGen z = n[3..7], eps = n[8..10]; EventGen z = n[11..15], eps = n[16..21].  Its absorption
+ * test and rotation angle psi take the uniforms ((w0 & 0xff) << 16 | (w1 & 0xff) << 8 | (w2 & 0xff)) 2^-24 of
+ * the tag 2 and tag 3 words (the low bytes, unused by the normals). */
 typedef struct {
     ms_decoder length;          /* LengthGen: p_in 2 (ln tau, g), p_out 1 (ln N dequantised)             */
     ms_decoder path;            /* PathGen:   p_in 3 (ln tau, g, ln N), p_out 3 (cos theta, alpha, beta) */

@@ -18,9 +18,10 @@
  *
  * Per path (pixel index -> counter id_hi, sample index -> id_lo) and segment step s (counter word 0):
  *   tag 0: u0 free path, u1 HG cosine, u2 HG azimuth, u3 roulette
- *   tag 1: u0 absorption test, u1 rotation angle psi
  *   tags 2..7: Box-Muller normals n[0..23], tag t words (w0,w1) -> n[4(t-2)], n[4(t-2)+1], (w2,w3) -> next two;
- *       used in order: LengthGen z then eps, PathGen z then eps, EventGen z then eps
+ *       used in order: LengthGen z then eps, PathGen z then eps, EventGen z then eps; the low bytes of words
+ *       0..2, which the uniforms leave unused, give ((w0 & 0xff) << 16 | (w1 & 0xff) << 8 | (w2 & 0xff)) 2^-24:
+ *       from tag 2 the absorption test's uniform, from tag 3 the rotation angle psi's
  *   tag 8 at step 0: pixel jitter.
  * Uniforms are (w >> 8) * 2^-24 (24-bit), identical to the single-precision kernels' stream.
  */
@@ -273,11 +274,13 @@ static void words(const stream* s, uint32_t step, uint32_t tag, uint32_t w[4])
 }
 static double u24(uint32_t w) { return (double)(w >> 8) * 0x1.0p-24; }
 
-static void normals(const stream* s, uint32_t step, double n[24])
+static void normals(const stream* s, uint32_t step, double n[24], double extra[2])
 {
     for (uint32_t t = 2; t < 8; ++t) {
         uint32_t w[4];
         words(s, step, t, w);
+        if (t < 4)
+            extra[t - 2] = (double)(((w[0] & 0xffu) << 16) | ((w[1] & 0xffu) << 8) | (w[2] & 0xffu)) * 0x1.0p-24;
         for (int pair = 0; pair < 2; ++pair) {
             double ua = u24(w[2 * pair]), ub = u24(w[2 * pair + 1]);
             double r = sqrt(-2.0 * log(1.0 - ua));
@@ -458,10 +461,8 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
             if (tau >= P->min_optical_radius) {
                 /* ---- sphere-tracing step: the three models of Eq. 3 at optical radius tau ---- */
                 st[3] += 1;
-                uint32_t a4[4];
-                words(&rs, seg, 1u, a4);
-                double n[24];
-                normals(&rs, seg, n);
+                double n[24], ua[2];
+                normals(&rs, seg, n, ua);
                 /* the normals are used in order: each model's z (its latent size), then its eps (its output
                  * size) — LengthGen, PathGen, EventGen */
                 const om_decoder* D = J->dec;
@@ -490,7 +491,7 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                 /* Eq. 4 and Sec. 4.1: CVAE frame -> world */
                 ov3 t1, t2;
                 onb(w, &t1, &t2);
-                double psi = 2.0 * M_PI * u24(a4[1]);
+                double psi = 2.0 * M_PI * ua[1];
                 double cs = cos(psi), sn = sin(psi);
                 double stt = sqrt(fmax(0.0, 1.0 - ct * ct));
                 double nn = sqrt(fmax(0.0, 1.0 - ab2));
@@ -513,7 +514,7 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                 ov3 Wd = normalize(vw[3]);
                 st[7] += 1;
                 acc += nee(S, P, X, Wd, lam, st);
-                if (u24(a4[0]) >= phiN) {
+                if (ua[0] >= phiN) {
                     st[5] += 1;
                     break;
                 }

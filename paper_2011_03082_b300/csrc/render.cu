@@ -355,10 +355,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             const int rank = __popc(parked & ((1u << lane) - 1u));
             const bool mine = st == kDecode && rank < 16;
             const Req& qq = B.r[req];
-            // The step's draws (tag 1: absorption and azimuth uniforms; tags 2..7: 24 normals) are the same
-            // Philox blocks as drawn lane by lane, but the 7 blocks of each of the nsel selected paths are
-            // spread over all 32 lanes and handed over through the staging tile: value v of row r at
-            // [v * 16 + r], the rows' counter keys after them.
+            // The step's draws (tags 2..7: 24 normals; the low bytes of words 0..2 of tags 2 and 3, unused by
+            // the normals, give the absorption and azimuth uniforms) are the same Philox blocks as drawn lane
+            // by lane, but the 6 blocks of each of the nsel selected paths are spread over all 32 lanes and
+            // handed over through shared memory: value v of row r at draws[v * 16 + r].
             const int nsel = min(16, __popc(parked));
             uint32_t* keys = reinterpret_cast<uint32_t*>(stage) + kDrawKeys;
             if (mine) {
@@ -370,19 +370,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             }
             __syncwarp();
 #pragma unroll 1
-            for (int i = lane; i < 7 * nsel; i += 32) {
-                const int c = (int)__fdividef((float)i + 0.5f, (float)nsel);   // block c of row r
+            for (int i = lane; i < 6 * nsel; i += 32) {
+                const int c = (int)__fdividef((float)i + 0.5f, (float)nsel);   // block c (tag 2 + c) of row r
                 const int r = i - c * nsel;
                 const uint32_t* kr = keys + 5 * r;
-                const Words wd = philox(kr[2], kr[0], kr[1], 1u + (uint32_t)c, kr[3], kr[4]);
-                if (c == 0) {
-                    draws[24 * 16 + r] = u24(wd.w0);
-                    draws[25 * 16 + r] = u24(wd.w1);
-                } else {
-                    const float2 a = box_muller(wd.w0, wd.w1), b = box_muller(wd.w2, wd.w3);
-                    float* o = draws + 4 * (c - 1) * 16 + r;
-                    o[0] = a.x; o[16] = a.y; o[32] = b.x; o[48] = b.y;
-                }
+                const Words wd = philox(kr[2], kr[0], kr[1], 2u + (uint32_t)c, kr[3], kr[4]);
+                const float2 a = box_muller(wd.w0, wd.w1), b = box_muller(wd.w2, wd.w3);
+                float* o = draws + 4 * c * 16 + r;
+                o[0] = a.x; o[16] = a.y; o[32] = b.x; o[48] = b.y;
+                if (c < 2)
+                    draws[(24 + c) * 16 + r] =
+                        (float)(((wd.w0 & 0xffu) << 16) | ((wd.w1 & 0xffu) << 8) | (wd.w2 & 0xffu)) * 0x1.0p-24f;
             }
             __syncwarp();
             // the row's draws are read where they are used (they stay in shared memory, not in registers)
