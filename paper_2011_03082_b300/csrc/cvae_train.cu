@@ -52,6 +52,23 @@ struct Shape {
 
 __device__ __forceinline__ float sigmoidf_fast(float a) { return __fdividef(1.0f, 1.0f + __expf(-a)); }
 
+// 3xTF32: x = head + tail with both rounded to TF32 (10-bit mantissa, FP32 exponent range); head*head +
+// head*tail + tail*head keeps about 21 significant bits of every product, with FP32 accumulation.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo)
+{
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(x - __uint_as_float(hi)));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 // value as the layer sees it: unchanged in FP32, rounded to BF16 (nearest even) in the BF16 variant
 template <bool kBF16>
 __device__ __forceinline__ float rq(float x)
@@ -322,13 +339,78 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     constexpr int T6 = ((2 * PO + 3) / 4) * ((kW + 3) / 4) + (2 * PO + 3) / 4;
     constexpr int B1 = T1, B2 = B1 + T2, B3 = B2 + T3, B4 = B3 + T4, B5 = B4 + T2, B6 = B5 + T6;
     (void)n_items;
-    for (int it = t; it < B6; it += kSamples) {
-        if (it < B1) tiles(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1, it);
-        else if (it < B2) tiles(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2, it - B1);
-        else if (it < B3) tiles(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3, it - B2);
-        else if (it < B4) tiles(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1, it - B3);
-        else if (it < B5) tiles(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2, it - B4);
-        else tiles(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3, it - B5);
+    // FP32: each warp forms whole layers' dW = D^T X and db = D^T 1 on the tensor cores (3xTF32, m16n8k8,
+    // the block's 128 samples as the k dimension in order); the output rows o >= O and columns k >= K read row
+    // padding and are not stored.  BF16 keeps the FFMA tiles above.
+    auto mma_grad = [&](auto O_, auto K_, int dslot, int islot, int bW, int bb) {
+        constexpr int O = decltype(O_)::value, K = decltype(K_)::value;
+        constexpr int NT = (K + 7) / 8;
+        const int lane = t & 31, g = lane >> 2, q = lane & 3;
+        float acc[NT][4], accb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+        const uint32_t one = g == 0 ? 0x3f800000u : 0u;     // B = the ones column (n = 0): the bias gradient
+#pragma unroll 2
+        for (int s0 = 0; s0 < kSamples; s0 += 8) {
+            // A[o][s] = D[s0 + s][o]: (g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4)
+            const float* d0 = row(dslot, s0 + q);
+            const float* d1 = row(dslot, s0 + q + 4);
+            uint32_t ah[4], al[4];
+            split_tf32(d0[g], ah[0], al[0]);
+            split_tf32(d0[g + 8], ah[1], al[1]);
+            split_tf32(d1[g], ah[2], al[2]);
+            split_tf32(d1[g + 8], ah[3], al[3]);
+            const float* x0 = row(islot, s0 + q);
+            const float* x1 = row(islot, s0 + q + 4);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                // B[s][k] = X[s0 + s][8 nt + k]: (q, g), (q + 4, g)
+                uint32_t bh0, bl0, bh1, bl1;
+                split_tf32(x0[8 * nt + g], bh0, bl0);
+                split_tf32(x1[8 * nt + g], bh1, bl1);
+                mma_tf32(acc[nt], al[0], al[1], al[2], al[3], bh0, bh1);
+                mma_tf32(acc[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                mma_tf32(acc[nt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+            }
+            mma_tf32(accb, al[0], al[1], al[2], al[3], one, one);
+            mma_tf32(accb, ah[0], ah[1], ah[2], ah[3], one, one);
+        }
+        // D[o][k] fragments: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int o = g + (i >= 2 ? 8 : 0), k = 8 * nt + 2 * q + (i & 1);
+                if (o < O && k < K) out[bW + o * K + k] = acc[nt][i];
+            }
+        if (q == 0) {
+            if (g < O) out[bb + g] = accb[0];
+            if (g + 8 < O) out[bb + g + 8] = accb[2];
+        }
+    };
+    if constexpr (!kBF16) {
+        // six layers over the block's four warps: E1 + D2, E2 + D3, E3, D1
+        const int warp = t >> 5;
+        if (warp == 0) {
+            mma_grad(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1);
+            mma_grad(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2);
+        } else if (warp == 1) {
+            mma_grad(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2);
+            mma_grad(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3);
+        } else if (warp == 2) {
+            mma_grad(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3);
+        } else {
+            mma_grad(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1);
+        }
+    } else {
+        for (int it = t; it < B6; it += kSamples) {
+            if (it < B1) tiles(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1, it);
+            else if (it < B2) tiles(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2, it - B1);
+            else if (it < B3) tiles(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3, it - B2);
+            else if (it < B4) tiles(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1, it - B3);
+            else if (it < B5) tiles(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2, it - B4);
+            else tiles(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3, it - B5);
+        }
     }
     if (t == 0) {
         float r = 0.0f, k = 0.0f;
