@@ -192,6 +192,7 @@ def main(argv=None):
     ap.add_argument("--res", type=int, default=128)
     ap.add_argument("--ref-spp", type=int, default=8192)
     ap.add_argument("--st-spp", type=int, default=256)
+    ap.add_argument("--sigmas", default="16,32,64,128", help="densities of the equal-RMSE comparison")
     ap.add_argument("--batched", action="store_true", help="run the 64-request batch instead")
     ap.add_argument("--scale", type=float, default=0.25)
     ap.add_argument("--absorption", action="store_true", help="run the absorption sweep instead")
@@ -208,7 +209,8 @@ def main(argv=None):
         for r in fallback_sweep():
             print(json.dumps(r))
         return
-    for r in equal_rmse(res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp):
+    sigmas = tuple(float(v) for v in a.sigmas.split(","))
+    for r in equal_rmse(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp):
         print(json.dumps(r))
 
 
