@@ -8,11 +8,12 @@
 // Kernel design:
 //  * fwd_bwd: one sample per thread, 128 samples per block.  Forward and backward run in registers; the
 //    layer inputs and the back-propagated deltas of every layer are staged in shared memory (rows padded to
-//    an odd stride), after which the block forms its partial weight gradient sum_s delta[s][o] * in[s][k]
-//    with one thread per parameter, summing samples in a fixed order.  Per-block partials go to the
-//    workspace: no floating-point atomics anywhere, so the gradient is bit-reproducible.
-//  * reduce: one thread per parameter sums the block partials in block order and writes the gradient and
-//    the loss terms.
+//    an odd stride), after which the block forms its partial weight gradient sum_s delta[s][o] * in[s][k]:
+//    in FP32 on the tensor cores (each warp takes whole layers, 3xTF32 m16n8k8 products with the samples as
+//    the k dimension), in BF16 mode with FFMA register tiles; either way in a fixed order.  Per-block
+//    partials go to the workspace: no floating-point atomics anywhere, so the gradient is bit-reproducible.
+//  * reduce: each block sums 32 parameters' block partials, eight warps over interleaved block rows, the
+//    warp sums added in warp order, and writes the gradient and the loss terms.
 //  * adam: element-wise bias-corrected Adam (AdamW decay when weight_decay > 0).
 // Precision: MS_FP32, or MS_BF16 — weight matrices and every layer's input rounded to BF16 (round to nearest
 // even) in the forward and backward passes, with biases, pre-activations, accumulation, losses, gradients,
@@ -331,14 +332,12 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     using W_ = std::integral_constant<int, kW>;
     using L2 = std::integral_constant<int, 2 * kL>;
     using P2 = std::integral_constant<int, 2 * PO>;
-    auto n_items = [](int O, int K) { return ((O + 3) / 4) * ((K + 3) / 4) + (O + 3) / 4; };
     constexpr int T1 = ((kW + 3) / 4) * ((S::IE + 3) / 4) + (kW + 3) / 4;
     constexpr int T2 = ((kW + 3) / 4) * ((kW + 3) / 4) + (kW + 3) / 4;
     constexpr int T3 = ((2 * kL + 3) / 4) * ((kW + 3) / 4) + (2 * kL + 3) / 4;
     constexpr int T4 = ((kW + 3) / 4) * ((S::ID + 3) / 4) + (kW + 3) / 4;
     constexpr int T6 = ((2 * PO + 3) / 4) * ((kW + 3) / 4) + (2 * PO + 3) / 4;
     constexpr int B1 = T1, B2 = B1 + T2, B3 = B2 + T3, B4 = B3 + T4, B5 = B4 + T2, B6 = B5 + T6;
-    (void)n_items;
     // FP32: each warp forms whole layers' dW = D^T X and db = D^T 1 on the tensor cores (3xTF32, m16n8k8,
     // the block's 128 samples as the k dimension in order); the output rows o >= O and columns k >= K read row
     // padding and are not stored.  BF16 keeps the FFMA tiles above.
