@@ -245,3 +245,27 @@ def test_tiny_cases_against_high_precision_restatement(orc, iso, paper, res_mode
         if status == 0:
             assert np.allclose(r["exit_pos"][i], x, atol=1e-12)
             assert np.allclose(r["exit_dir"][i], w, atol=1e-12)
+
+
+def test_spare_bit_uniforms_are_uniform_and_independent(orc):
+    """The uniforms drawn from bits the main uniforms leave unused (the walk's reservoir uniform: low bytes of
+    words 0..2 at 24 bits, low 11 bits of the tag 2 words at 53 bits; the sphere step's absorption and azimuth
+    uniforms: low bytes of the tag 2 and tag 3 words) are uniform on [0, 1) and uncorrelated with the uniforms
+    taken from the same words' other bits, over 200,000 counters.  (Taking bits the main uniforms use, such
+    as a word's top byte, would correlate with them.)"""
+    from scipy import stats
+    n = 200_000
+    hi = orc.philox_words(9, 0, n, 5, 0).astype(np.uint64)
+    lo = orc.philox_words(9, 0, n, 5, 2).astype(np.uint64)
+    spare24 = ((hi[:, 0] & 0xFF) << 16 | (hi[:, 1] & 0xFF) << 8 | (hi[:, 2] & 0xFF)) / 2.0 ** 24
+    spare33 = ((lo[:, 0] & 0x7FF) << 22 | (lo[:, 1] & 0x7FF) << 11 | (lo[:, 2] & 0x7FF)) / 2.0 ** 33
+    u24 = (hi >> 8) / 2.0 ** 24
+    u53 = ((hi << 21) | (lo >> 11)).astype(np.float64) / 2.0 ** 53
+    bound = 5.0 / np.sqrt(n)
+    for spare, main in ((spare24, u24), (spare33, u53)):
+        assert stats.kstest(spare, "uniform").pvalue > 1e-4
+        for j in range(4):
+            assert abs(np.corrcoef(spare, main[:, j])[0, 1]) < bound
+    # a "spare" uniform from bits the main uniform uses (the top byte of word 0) is not independent of it
+    bad = (hi[:, 0] >> 24) / 256.0
+    assert abs(np.corrcoef(bad, u24[:, 0])[0, 1]) > 10 * bound
