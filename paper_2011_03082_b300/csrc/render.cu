@@ -649,9 +649,9 @@ Variant make_variant()
 }
 // A decoder round takes at most 16 parked lanes (one tensor-core tile), so the decode thresholds stay <= 16.
 static const Variant kVariants[] = {
-    make_variant<12, 12, 24, 3>(), make_variant<12, 12, 20, 3>(), make_variant<12, 12, 16, 3>(),
-    make_variant<10, 10, 16, 3>(), make_variant<12, 10, 16, 3>(), make_variant<12, 12, 28, 3>(),
-    make_variant<8, 8, 16, 3>(), make_variant<10, 10, 20, 3>(), make_variant<12, 12, 12, 3>(),
+    make_variant<10, 12, 24, 3>(), make_variant<12, 12, 24, 3>(), make_variant<8, 12, 24, 3>(),
+    make_variant<10, 14, 24, 3>(), make_variant<10, 12, 20, 3>(), make_variant<10, 12, 28, 3>(),
+    make_variant<10, 16, 24, 3>(), make_variant<10, 10, 28, 3>(), make_variant<8, 14, 28, 3>(),
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
