@@ -86,6 +86,8 @@ def lib():
         L.om_walk.restype = C.c_int
         L.om_render.argtypes = [P, P, P, P, C.c_int]
         L.om_render.restype = C.c_int
+        L.om_render_pixels.argtypes = [P, P, P, C.c_int, P, P, C.c_int]
+        L.om_render_pixels.restype = C.c_int
         L.om_decoder_sample.argtypes = [P, P, P, P, P]
         L.om_hg_cosine.argtypes = [C.c_double, C.c_double]
         L.om_hg_cosine.restype = C.c_double
@@ -210,10 +212,9 @@ def _decoder_struct(wvec, p_in, p_out, latent=4, width=16):
     return Decoder(p_in, latent, width, p_out, w.ctypes.data_as(C.POINTER(C.c_double))), w
 
 
-def render(params: dict, decoders=None, n_threads=0):
-    """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out) or
-    (weights, p_in, p_out, latent, width) for LengthGen, PathGen, EventGen (latent 4, width 16 when not given).
-    Returns (image_sum[h][w], stats[16], threads)."""
+def _render_setup(params: dict, decoders):
+    """RenderParams and decoder structs for ``params`` (keys follow RenderParams) and ``decoders``; the arrays
+    in the returned list must outlive the call."""
     P = RenderParams()
     for k, v in params.items():
         if k == "sdf_grid":
@@ -234,12 +235,34 @@ def render(params: dict, decoders=None, n_threads=0):
             d, arr = _decoder_struct(*dd)
             decs[i] = d
             keep.append(arr)
+    return P, decs, keep
+
+
+def render(params: dict, decoders=None, n_threads=0):
+    """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out) or
+    (weights, p_in, p_out, latent, width) for LengthGen, PathGen, EventGen (latent 4, width 16 when not given).
+    Returns (image_sum[h][w], stats[16], threads)."""
+    P, decs, keep = _render_setup(params, decoders)
     image = np.zeros((P.height, P.width), np.float64)
     stats = np.zeros(16, np.uint64)
     nt = lib().om_render(C.byref(P), C.cast(decs, C.c_void_p), _ptr(image), _ptr(stats), n_threads)
     if nt < 0:
         raise ValueError("om_render: the decoders need more than 24 normals per sphere step, or are too wide")
     return image, stats, nt
+
+
+def render_pixels(params: dict, pixels, decoders=None, n_threads=0):
+    """The same render restricted to the pixels with flat indices ``pixels`` (py * width + px): returns
+    (their sums over the spp samples, stats[16] of those paths), on the streams the whole image uses."""
+    P, decs, keep = _render_setup(params, decoders)
+    pix = np.ascontiguousarray(pixels, np.int64)
+    values = np.zeros(pix.size, np.float64)
+    stats = np.zeros(16, np.uint64)
+    nt = lib().om_render_pixels(C.byref(P), C.cast(decs, C.c_void_p), _ptr(pix), int(pix.size), _ptr(values),
+                                _ptr(stats), n_threads)
+    if nt < 0:
+        raise ValueError("om_render_pixels: bad pixel index or decoders")
+    return values, stats
 
 
 def decoder_sample_one(wvec, p_in, p_out, c, z, eps):

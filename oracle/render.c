@@ -616,6 +616,99 @@ int om_render(const om_render_params* P, const om_decoder* dec3, double* image, 
     return nt;
 }
 
+/*
+ * Selected pixels of the same render: values[i] = the sum over the spp samples of pixel pixels[i] (index
+ * py * width + px), on exactly the streams the whole-image render uses for that pixel; stats as om_render.
+ * Lets a test check sampled pixels of a full-size render one by one.  Returns the threads used, or -1.
+ */
+typedef struct {
+    render_job* J;
+    const int64_t* pixels;
+    int n_pixels;
+    double* values;
+    int next;
+} pixel_job;
+
+static void* pixel_worker(void* arg)
+{
+    pixel_job* Q = (pixel_job*)arg;
+    render_job* J = Q->J;
+    const om_render_params* P = J->P;
+    scene S;
+    S.A = P->disp_amp;
+    S.k = P->disp_freq;
+    S.lip = 1.0 + P->disp_amp * P->disp_freq;
+    double rb = 1.0 + P->disp_amp + 1e-3;
+    S.rb2 = rb * rb;
+    S.grid = J->grid;
+    S.gn = P->sdf_grid_n;
+    S.gh = S.grid ? 2.0 * (1.0 + S.A) / (double)(S.gn - 2) : 0.0;
+    S.gb = 1.0 + S.A + S.gh;
+    uint64_t st[16] = { 0 };
+    t_sdf_evals = 0;
+    t_grad_evals = 0;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int i = Q->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (i >= Q->n_pixels)
+            break;
+        int px = (int)(Q->pixels[i] % P->width), py = (int)(Q->pixels[i] / P->width);
+        double acc = 0.0;
+        for (uint32_t smp = 0; smp < P->spp; ++smp)
+            acc += trace_path(J, &S, px, py, P->sample_offset + smp, st);
+        Q->values[i] = acc;
+    }
+    st[8] = t_sdf_evals;
+    st[9] = t_grad_evals;
+    pthread_mutex_lock(&J->lock);
+    for (int k = 0; k < 16; ++k) J->stats[k] += st[k];
+    pthread_mutex_unlock(&J->lock);
+    return NULL;
+}
+
+int om_render_pixels(const om_render_params* P, const om_decoder* dec3, const int64_t* pixels, int n_pixels,
+                     double* values, uint64_t* stats, int n_threads)
+{
+    if (n_pixels < 0 || (n_pixels > 0 && (!pixels || !values)))
+        return -1;
+    for (int i = 0; i < n_pixels; ++i)
+        if (pixels[i] < 0 || pixels[i] >= (int64_t)P->width * P->height)
+            return -1;
+    if (P->mode == 1 && dec3) {
+        int used = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (dec3[k].width > 64 || dec3[k].p_in + dec3[k].latent > 64) return -1;
+            used += dec3[k].latent + dec3[k].p_out;
+        }
+        if (used > 24) return -1;
+    }
+    const double* grid = NULL;
+    if (P->mode == 1 && P->sdf_grid_n > 0) {
+        if (P->sdf_grid_n < 4 || P->disp_amp >= 1.0 || !P->sdf_grid) return -1;
+        grid = P->sdf_grid;
+    }
+    render_job J;
+    J.P = P;
+    J.dec = dec3;
+    J.grid = grid;
+    J.image = NULL;
+    J.stats = stats;
+    J.next_row = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    pixel_job Q = { &J, pixels, n_pixels, values, 0 };
+    int nt = om_num_threads(n_threads);
+    if (nt > n_pixels) nt = n_pixels > 0 ? n_pixels : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+    for (int t = 0; t < nt; ++t)
+        pthread_create(&th[t], NULL, pixel_worker, &Q);
+    for (int t = 0; t < nt; ++t)
+        pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    return nt;
+}
+
 /* Single-query decoder sample, exposed for the tests. */
 void om_decoder_sample(const om_decoder* D, const double* c, const double* z, const double* eps, double* x)
 {

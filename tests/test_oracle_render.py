@@ -335,3 +335,18 @@ def test_march_step_never_crosses_and_closes_in(orc, A, k):
             ratios.append(orc.march_step(A, k, x, w) / cross)
     ratios = np.array(ratios)
     assert ratios.max() < 1.0 and np.median(ratios) > 0.9, (ratios.max(), np.median(ratios))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_render_pixels_equal_the_whole_image(orc, mode):
+    """Rendering selected pixels one by one uses exactly the whole image's streams: the values equal the full
+    render's pixels bit for bit, in both modes (the check of full-size renders at sampled pixels rests on it)."""
+    decs = None
+    if mode:
+        decs = [(synth.xavier_decoder(100 + i, *shape).astype(np.float64), *shape)
+                for i, shape in enumerate(synth.MODEL_SHAPES.values())]
+    p = synth.render_scene(48.0, width=20, height=14, spp=3, mode=mode, seed=5)
+    img, _, _ = orc.render(p, decs)
+    pix = np.array([0, 7, 131, 139, 150, 279])
+    v, _ = orc.render_pixels(p, pix, decs)
+    assert np.array_equal(v, img.reshape(-1)[pix])
