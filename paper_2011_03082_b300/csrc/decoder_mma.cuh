@@ -230,16 +230,20 @@ __device__ __forceinline__ void warp_mlp(const unsigned char* __restrict__ wsm, 
 // Rows no active lane supplied carry whatever the staging tile held: every output row depends on its own input
 // row only, so those rows are computed and ignored.  Every lane of the warp must call it.  Used where fewer
 // than half a warp's lanes have a query: the work is that of one tile instead of two.
-template <int NT3, int kSplit, bool kBF16, int NTH = 2>
+// KIN: the number of input columns in use (x[j] = 0 for j >= KIN is assumed); with KIN <= 8 the upper half of
+// the input tile is known to be zero and is neither staged nor loaded.  KOUT: the outputs the caller uses (the
+// rest of y is zero).
+template <int NT3, int kSplit, bool kBF16, int NTH = 2, int KIN = 16, int KOUT = 8 * NT3>
 __device__ __forceinline__ void warp_mlp_rows16(const unsigned char* __restrict__ wsm, float* __restrict__ stage,
                                                 const float (&x)[16], float (&y)[8 * NT3], int row, bool active)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint4* frag = reinterpret_cast<const uint4*>(wsm);
     const float* bias = reinterpret_cast<const float*>(wsm + (2 * NTH + NT3) * 32 * 16);
+    constexpr int kCols = KIN <= 8 ? 8 : 16;
     if (active) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) stage[row * kStageStride + j] = x[j];
+        for (int j = 0; j < kCols; ++j) stage[row * kStageStride + j] = x[j];
     }
     __syncwarp();
     uint32_t ah[1][4], al[1][4];
@@ -248,8 +252,12 @@ __device__ __forceinline__ void warp_mlp_rows16(const unsigned char* __restrict_
         const float* r1 = r0 + 8 * kStageStride;
         split2<kBF16>(r0[2 * t], r0[2 * t + 1], ah[0][0], al[0][0]);
         split2<kBF16>(r1[2 * t], r1[2 * t + 1], ah[0][1], al[0][1]);
-        split2<kBF16>(r0[2 * t + 8], r0[2 * t + 9], ah[0][2], al[0][2]);
-        split2<kBF16>(r1[2 * t + 8], r1[2 * t + 9], ah[0][3], al[0][3]);
+        if constexpr (kCols == 16) {
+            split2<kBF16>(r0[2 * t + 8], r0[2 * t + 9], ah[0][2], al[0][2]);
+            split2<kBF16>(r1[2 * t + 8], r1[2 * t + 9], ah[0][3], al[0][3]);
+        } else {
+            ah[0][2] = al[0][2] = ah[0][3] = al[0][3] = 0u;
+        }
     }
     __syncwarp();
     float h[1][NTH][4];
@@ -269,7 +277,7 @@ __device__ __forceinline__ void warp_mlp_rows16(const unsigned char* __restrict_
         }
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 8 * NT3; ++j) y[j] = active ? stage[row * kStageStride + j] : 0.0f;
+    for (int j = 0; j < 8 * NT3; ++j) y[j] = (active && j < KOUT) ? stage[row * kStageStride + j] : 0.0f;
     __syncwarp();
 }
 

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             // LengthGen: N (albedo-1 physics, Eq. 3)
             float xin[16] = {ltau, mine ? qq.g : 0.0f, nrm(kZL), nrm(kZL + 1)};
             float yL[8];
-            mmadec::warp_mlp_rows16<1, 3, false, 1>(wl, stage, xin, yL, rank, mine);
+            mmadec::warp_mlp_rows16<1, 3, false, 1, 2 + kLatL, 2>(wl, stage, xin, yL, rank, mine);
             const float yN = yL[0] + __expf(0.5f * yL[1]) * nrm(kEL);
             float N = floorf(__expf(yN) + 0.5f);
             N = fminf(fmaxf(N, 1.0f), kNMax);
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, nrm(kZP), nrm(kZP + 1), nrm(kZP + 2), nrm(kZP + 3),
                             nrm(kZP + 4)};
             float yP[8];
-            mmadec::warp_mlp_rows16<1, 3, false, 2>(wpth, stage, xp, yP, rank, mine);
+            mmadec::warp_mlp_rows16<1, 3, false, 2, 3 + kLatP, 6>(wpth, stage, xp, yP, rank, mine);
             const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * nrm(kEP)));
             float al = yP[1] + __expf(0.5f * yP[4]) * nrm(kEP + 1);
             float be = yP[2] + __expf(0.5f * yP[5]) * nrm(kEP + 2);
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             float xe[16] = {ltau, mine ? qq.g : 0.0f, mine ? qq.phi : 0.0f, ct, al, be, lnN,
                             nrm(kZE), nrm(kZE + 1), nrm(kZE + 2), nrm(kZE + 3), nrm(kZE + 4)};
             float yE[16];
-            mmadec::warp_mlp_rows16<2, 3, false, 2>(wev, stage, xe, yE, rank, mine);
+            mmadec::warp_mlp_rows16<2, 3, false, 2, 16, 12>(wev, stage, xe, yE, rank, mine);
             if (mine) {
                 float e[6];
 #pragma unroll
