@@ -63,8 +63,8 @@ class RenderParams(C.Structure):
                 ("light_pos", C.c_double * 3), ("light_I", C.c_double),
                 ("sigma_t", C.c_double), ("g", C.c_double), ("albedo", C.c_double),
                 ("disp_amp", C.c_double), ("disp_freq", C.c_double),
-                ("mode", C.c_int32), ("sdf_grid_n", C.c_int32),
-                ("min_optical_radius", C.c_double), ("max_optical_radius", C.c_double),
+                ("mode", C.c_int32), ("sdf_grid_n", C.c_int32), ("march_mode", C.c_int32),
+                ("max_march", C.c_int32), ("min_optical_radius", C.c_double), ("max_optical_radius", C.c_double),
                 ("seed", C.c_uint64), ("sample_offset", C.c_uint64), ("sdf_grid", C.c_void_p)]
 
 
@@ -94,12 +94,16 @@ def lib():
         L.om_scatter_dir.argtypes = [P, C.c_double, C.c_double, P]
         L.om_inside_length.argtypes = [C.c_double, C.c_double, P, P]
         L.om_inside_length.restype = C.c_double
-        L.om_ray_crossing.argtypes = [C.c_double, C.c_double, P, P, P]
+        L.om_ray_crossing.argtypes = [C.c_double, C.c_double, P, P, P, C.c_int]
         L.om_ray_crossing.restype = C.c_int
         L.om_band_step.argtypes = [C.c_double, C.c_double, P, P]
         L.om_band_step.restype = C.c_double
         L.om_march_step.argtypes = [C.c_double, C.c_double, P, P]
         L.om_march_step.restype = C.c_double
+        L.om_walk_nee.argtypes = [C.c_uint64, C.c_uint64, C.c_double, C.c_double, C.c_double, P, P, P, P, P, P,
+                                  C.c_int]
+        L.om_walk_nee.restype = C.c_int
+        L.om_set_plant.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -205,6 +209,25 @@ def walk(seed, n_photons, media, *, photon_offset=0, max_events=1 << 20, reservo
     return out
 
 
+def walk_nee(seed, n_photons, tau, g, phi, light, n_threads=0):
+    """Training-record walks (paper convention, w_in = (0,0,1), albedo-1 physics, representative event with
+    weights phi^k) with, per photon, the brute-force next-event sum over all events toward a point light at
+    ``light`` (outside the unit sphere): sum_k phi^k rho_g(W_k . w_L) exp(-tau d_k) / |x_L - X_k|^2.  Returns
+    dict(n_events, rep_pos, rep_dir, rep_index, nee_sum)."""
+    xl = np.ascontiguousarray(light, np.float64)
+    out = dict(n_events=np.zeros(n_photons, np.int32), rep_pos=np.zeros((n_photons, 3)),
+               rep_dir=np.zeros((n_photons, 3)), rep_index=np.zeros(n_photons, np.int32),
+               nee_sum=np.zeros(n_photons))
+    lib().om_walk_nee(seed, n_photons, tau, g, phi, _ptr(xl), _ptr(out["n_events"]), _ptr(out["rep_pos"]),
+                      _ptr(out["rep_dir"]), _ptr(out["rep_index"]), _ptr(out["nee_sum"]), n_threads)
+    return out
+
+
+def set_plant(k: int):
+    """Test hook: plant a deliberate mistake in the renderer's sphere step (0 removes it); see render.c."""
+    lib().om_set_plant(int(k))
+
+
 # ---------------------------------------------------------------- renderer
 
 def _decoder_struct(wvec, p_in, p_out, latent=4, width=16):
@@ -224,7 +247,7 @@ def _render_setup(params: dict, decoders):
         else:
             setattr(P, k, v)
     keep = []
-    if params.get("sdf_grid_n", 0) and params.get("mode", 0) == 1:
+    if params.get("sdf_grid_n", 0) and params.get("mode", 0) != 0:
         g, _, _ = sdf_grid(P.disp_amp, P.disp_freq, int(params["sdf_grid_n"]))
         g = np.ascontiguousarray(g)
         keep.append(g)
@@ -241,6 +264,9 @@ def _render_setup(params: dict, decoders):
 def render(params: dict, decoders=None, n_threads=0):
     """Render; ``params`` keys follow RenderParams; ``decoders`` is a list of three (weights, p_in, p_out) or
     (weights, p_in, p_out, latent, width) for LengthGen, PathGen, EventGen (latent 4, width 16 when not given).
+    mode 0 is brute force, 1 sphere tracing with the decoders, 2 sphere tracing with the exact sampler (a walk
+    in the sphere in place of the decoders; no decoders needed); march_mode 1 marches with the Lipschitz step
+    alone (give a larger max_march).
     Returns (image_sum[h][w], stats[16], threads)."""
     P, decs, keep = _render_setup(params, decoders)
     image = np.zeros((P.height, P.width), np.float64)
@@ -319,11 +345,11 @@ def march_step(A, k, p, w):
     return float(lib().om_march_step(A, k, _ptr(p), _ptr(w)))
 
 
-def ray_crossing(A, k, p, w):
+def ray_crossing(A, k, p, w, plain=False):
     """First boundary crossing along p + t w of the displaced sphere: (status, t) with status 1 crossing,
-    0 escape (outside rays only), 2 step cap."""
+    0 escape (outside rays only), 2 step cap; ``plain`` marches with the Lipschitz step alone."""
     p = np.ascontiguousarray(p, np.float64)
     w = np.ascontiguousarray(w, np.float64)
     t = np.zeros(1)
-    r = lib().om_ray_crossing(A, k, _ptr(p), _ptr(w), _ptr(t))
+    r = lib().om_ray_crossing(A, k, _ptr(p), _ptr(w), _ptr(t), int(bool(plain)))
     return r, float(t[0])

@@ -16,6 +16,15 @@
  *       event, sphere tracing adds Lambda^(N) * rho_g * gamma at the representative event.
  * The readings taken where the paper is silent are listed beside each step below.
  *
+ * Mode 2 (exact sampler) runs the same sphere step with the three learned samplers replaced by what they
+ * approximate: one brute-force walk in the unit sphere at optical radius sigma_t r (walk.c, the albedo-1
+ * physics with the representative event chosen with weights phi^k, i.e. a training record), turned into the
+ * models' outputs (N; cos theta, alpha, beta; X~, W~ in the frame where the exit is (sin theta, 0, cos theta))
+ * and then put through the same Eq. 4 frame, Lambda, NEE and absorption code as the learned samplers' outputs.
+ * Its image must equal the brute-force image in expectation, which pins that composition to the paper's
+ * physics.  march_mode 1 replaces the march's step by the plain Lipschitz step |f| / (1 + A k) (Hart's sphere
+ * tracing with nothing else), to show that the larger conservative steps find the same crossings.
+ *
  * Per path (pixel index -> counter id_hi, sample index -> id_lo) and segment step s (counter word 0):
  *   tag 0: u0 free path, u1 HG cosine, u2 HG azimuth, u3 roulette
  *   tags 2..7: Box-Muller normals n[0..23], tag t words (w0,w1) -> n[4(t-2)], n[4(t-2)+1], (w2,w3) -> next two;
@@ -47,8 +56,10 @@ typedef struct {
     double light_pos[3], light_I;
     double sigma_t, g, albedo;
     double disp_amp, disp_freq;
-    int32_t mode;              /* 0 brute force, 1 sphere tracing */
+    int32_t mode;              /* 0 brute force, 1 sphere tracing, 2 sphere tracing with the exact sampler */
     int32_t sdf_grid_n;        /* 0, or n: sphere radii also from an n^3 voxel grid of conservative distances */
+    int32_t march_mode;        /* 0 the largest of the three conservative steps, 1 the Lipschitz step alone */
+    int32_t max_march;         /* steps per march, 0 for the default R_MAX_MARCH */
     double min_optical_radius, max_optical_radius;
     uint64_t seed, sample_offset;
     const double* sdf_grid;    /* sdf_grid_n^3 voxel values (index (iz n + iy) n + ix) over [-b, b]^3, voxel side
@@ -80,7 +91,15 @@ typedef struct {
     const double* grid;        /* voxel grid of conservative distances (NULL: none), n^3, index (iz n + iy) n + ix */
     int gn;
     double gb, gh;             /* the grid covers [-gb, gb]^3 in voxels of side gh */
+    int plain;                 /* 1: Lipschitz steps only */
+    int max_march;             /* steps per march */
 } scene;
+
+/* Test hook: a deliberate mistake in the sphere step, so that a test can show its pin catches it (0: none;
+ * 1: Lambda summed over i = 0..N; 2: the exit frame's e_t negated; 3: no NEE on a step that absorbs; 4: the
+ * representative event not scaled by the sphere's radius). */
+static int g_plant = 0;
+void om_set_plant(int k) { g_plant = k; }
 
 static _Thread_local uint64_t t_sdf_evals, t_grad_evals;
 
@@ -179,8 +198,12 @@ static double march_step(const scene* S, ov3 r, ov3 w, int inside, int* crossing
             *crossing = 1;
             return 0.0;
         }
+        if (S->plain)
+            return R_EPS;
         return fmax(R_EPS, curve_step(S, rp, fmax(h, 0.0), h1, inside));
     }
+    if (S->plain)
+        return h / S->lip;
     double q = safe_step(S, r, w, f);
     if (q == INFINITY) {
         *escape = 1;
@@ -194,7 +217,7 @@ static double march_step(const scene* S, ov3 r, ov3 w, int inside, int* crossing
 static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
 {
     double t = 0.0;
-    for (int it = 0; it < R_MAX_MARCH; ++it) {
+    for (int it = 0; it < S->max_march; ++it) {
         ov3 r = add(p, mul(w, t));
         int crossing, escape;
         double d = march_step(S, r, w, 1, &crossing, &escape);
@@ -216,7 +239,7 @@ static int march_inside(const scene* S, ov3 p, ov3 w, double l, ov3* q)
 static int march_outside(const scene* S, ov3 p, ov3 w, ov3* q)
 {
     double t = 0.0;
-    for (int it = 0; it < R_MAX_MARCH; ++it) {
+    for (int it = 0; it < S->max_march; ++it) {
         ov3 r = add(p, mul(w, t));
         if (dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
             return 0;
@@ -242,7 +265,7 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
     ov3 w = mul(dl, 1.0 / D);
     double t = 0.0, din = 0.0;
     int inside = 1;
-    for (int it = 0; it < R_MAX_MARCH; ++it) {
+    for (int it = 0; it < S->max_march; ++it) {
         if (t >= D)
             return din;
         ov3 r = add(X, mul(w, t));
@@ -393,6 +416,38 @@ static double nee(const scene* S, const om_render_params* P, ov3 X, ov3 W, doubl
     return weight * rho * exp(-P->sigma_t * din) * P->light_I / d2;
 }
 
+int om_walk_record(uint64_t seed, uint64_t id, double tau, double g, double phi, uint32_t max_events,
+                   int32_t* n, double x[3], double w[3], double X[3], double W[3]);
+
+/*
+ * The exact sampler of one sphere step: a walk record at optical radius tau (N, exit x and w, representative
+ * event X and W, the albedo-1 physics with weights phi^k), drawn on its own stream (key: the render seed mixed
+ * with the segment, counter id: the path's), turned into the three models' outputs (Sec. 4.1): rotated about
+ * (0,0,1) by -psi_exit, psi_exit = atan2(x_y, x_x), so that the exit is (sin theta, 0, cos theta); then
+ * cos theta = x~_z, alpha = w~ . e_b = w~_y, beta = w~ . e_t = w~_x cos theta - w~_z sin theta, and (X~, W~)
+ * the rotated event.  Returns 0 when the walk ran out of events.
+ */
+static int exact_sample(const om_render_params* P, uint64_t id, uint32_t seg, double tau, double* N, double* ct,
+                        double* al, double* be, double xe[6])
+{
+    uint64_t key = P->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(seg + 1u));
+    int32_t n = 0;
+    double x[3], w[3], X[3], W[3];
+    if (om_walk_record(key, id, tau, P->g, P->albedo, 1u << 24, &n, x, w, X, W) != 0)
+        return 0;
+    double ps = atan2(x[1], x[0]);
+    double c = cos(ps), s = sin(ps);
+    double xr[3] = { c * x[0] + s * x[1], -s * x[0] + c * x[1], x[2] };
+    double wr[3] = { c * w[0] + s * w[1], -s * w[0] + c * w[1], w[2] };
+    *N = (double)n;
+    *ct = xr[2];
+    *al = wr[1];
+    *be = wr[0] * xr[2] - wr[2] * xr[0];
+    xe[0] = c * X[0] + s * X[1]; xe[1] = -s * X[0] + c * X[1]; xe[2] = X[2];
+    xe[3] = c * W[0] + s * W[1]; xe[4] = -s * W[0] + c * W[1]; xe[5] = W[2];
+    return 1;
+}
+
 /* One camera path; returns its contribution and updates the counters. */
 static double trace_path(const render_job* J, const scene* S, int px, int py, uint64_t sample, uint64_t* st)
 {
@@ -452,7 +507,7 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
             p = re;                         /* re-entered: fresh flight (memoryless) */
             continue;
         }
-        if (P->mode == 1) {
+        if (P->mode == 1 || P->mode == 2) {
             double d = -sdf(S, c) / S->lip;
             if (S->grid)
                 d = fmax(d, grid_value(S, c));
@@ -463,30 +518,43 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                 st[3] += 1;
                 double n[24], ua[2];
                 normals(&rs, seg, n, ua);
-                /* the normals are used in order: each model's z (its latent size), then its eps (its output
-                 * size) — LengthGen, PathGen, EventGen */
-                const om_decoder* D = J->dec;
-                int zL = 0, eL = zL + D[0].latent, zP = eL + D[0].p_out, eP = zP + D[1].latent;
-                int zE = eP + D[1].p_out, eE = zE + D[2].latent;
-                double ltau = log(tau);
-                double cL[2] = { ltau, g }, yN;
-                decoder_sample(&D[0], cL, n + zL, n + eL, &yN);
-                double N = floor(exp(yN) + 0.5);
-                if (!(N >= 1.0)) N = 1.0;
-                if (N > R_N_MAX) N = R_N_MAX;
-                double lnN = log(N);
-                double cP[3] = { ltau, g, lnN }, xp[3];
-                decoder_sample(&D[1], cP, n + zP, n + eP, xp);
-                double ct = fmin(1.0, fmax(-1.0, xp[0])), al = xp[1], be = xp[2];
-                double ab2 = al * al + be * be;
-                if (ab2 > 1.0) {
-                    double s = 1.0 / sqrt(ab2);
-                    al = al * s; be = be * s; ab2 = 1.0;
+                double N, ct, al, be, ab2, xe[6];
+                if (P->mode == 2) {
+                    if (!exact_sample(P, rs.id, seg, tau, &N, &ct, &al, &be, xe)) {
+                        st[6] += 1;
+                        break;
+                    }
+                    ab2 = al * al + be * be;
+                } else {
+                    /* the normals are used in order: each model's z (its latent size), then its eps (its
+                     * output size) — LengthGen, PathGen, EventGen */
+                    const om_decoder* D = J->dec;
+                    int zL = 0, eL = zL + D[0].latent, zP = eL + D[0].p_out, eP = zP + D[1].latent;
+                    int zE = eP + D[1].p_out, eE = zE + D[2].latent;
+                    double ltau = log(tau);
+                    double cL[2] = { ltau, g }, yN;
+                    decoder_sample(&D[0], cL, n + zL, n + eL, &yN);
+                    N = floor(exp(yN) + 0.5);
+                    if (!(N >= 1.0)) N = 1.0;
+                    if (N > R_N_MAX) N = R_N_MAX;
+                    double lnN = log(N);
+                    double cP[3] = { ltau, g, lnN }, xp[3];
+                    decoder_sample(&D[1], cP, n + zP, n + eP, xp);
+                    ct = fmin(1.0, fmax(-1.0, xp[0]));
+                    al = xp[1];
+                    be = xp[2];
+                    ab2 = al * al + be * be;
+                    if (ab2 > 1.0) {
+                        double s = 1.0 / sqrt(ab2);
+                        al = al * s; be = be * s; ab2 = 1.0;
+                    }
+                    double cE[7] = { ltau, g, phi, ct, al, be, lnN };
+                    decoder_sample(&D[2], cE, n + zE, n + eE, xe);
                 }
-                double cE[7] = { ltau, g, phi, ct, al, be, lnN }, xe[6];
-                decoder_sample(&D[2], cE, n + zE, n + eE, xe);
                 double phiN = pow(phi, N);
                 double lam = (phi < 1.0) ? phi * (1.0 - phiN) / (1.0 - phi) : N;
+                if (g_plant == 1)
+                    lam = lam + 1.0;
 
                 /* Eq. 4 and Sec. 4.1: CVAE frame -> world */
                 ov3 t1, t2;
@@ -495,8 +563,9 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                 double cs = cos(psi), sn = sin(psi);
                 double stt = sqrt(fmax(0.0, 1.0 - ct * ct));
                 double nn = sqrt(fmax(0.0, 1.0 - ab2));
+                double bt = g_plant == 2 ? -be : be;
                 ov3 xt = v3(stt, 0.0, ct);
-                ov3 wt = v3(be * ct + nn * stt, al, -be * stt + nn * ct);
+                ov3 wt = v3(bt * ct + nn * stt, al, -bt * stt + nn * ct);
                 ov3 Xt = v3(xe[0], xe[1], xe[2]);
                 double xn = sqrt(dot(Xt, Xt));
                 if (xn > 1.0) Xt = mul(Xt, 1.0 / xn);
@@ -510,11 +579,13 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                 }
                 ov3 xexit = add(c, mul(vw[0], r));
                 ov3 wout = normalize(vw[1]);
-                ov3 X = add(c, mul(vw[2], r));
+                ov3 X = add(c, mul(vw[2], g_plant == 4 ? 1.0 : r));
                 ov3 Wd = normalize(vw[3]);
                 st[7] += 1;
-                acc += nee(S, P, X, Wd, lam, st);
-                if (ua[0] >= phiN) {
+                int absorbed = ua[0] >= phiN;
+                if (!(g_plant == 3 && absorbed))
+                    acc += nee(S, P, X, Wd, lam, st);
+                if (absorbed) {
                     st[5] += 1;
                     break;
                 }
@@ -551,6 +622,8 @@ static void* render_worker(void* arg)
     S.gn = P->sdf_grid_n;
     S.gh = S.grid ? 2.0 * (1.0 + S.A) / (double)(S.gn - 2) : 0.0;
     S.gb = 1.0 + S.A + S.gh;
+    S.plain = P->march_mode == 1;
+    S.max_march = P->max_march > 0 ? P->max_march : R_MAX_MARCH;
     uint64_t st[16] = { 0 };
     t_sdf_evals = 0;
     t_grad_evals = 0;
@@ -592,7 +665,7 @@ int om_render(const om_render_params* P, const om_decoder* dec3, double* image, 
         if (used > 24) return -1;   /* a sphere step draws 24 normals */
     }
     const double* grid = NULL;
-    if (P->mode == 1 && P->sdf_grid_n > 0) {
+    if (P->mode != 0 && P->sdf_grid_n > 0) {
         if (P->sdf_grid_n < 4 || P->disp_amp >= 1.0 || !P->sdf_grid) return -1;
         grid = P->sdf_grid;
     }
@@ -644,6 +717,8 @@ static void* pixel_worker(void* arg)
     S.gn = P->sdf_grid_n;
     S.gh = S.grid ? 2.0 * (1.0 + S.A) / (double)(S.gn - 2) : 0.0;
     S.gb = 1.0 + S.A + S.gh;
+    S.plain = P->march_mode == 1;
+    S.max_march = P->max_march > 0 ? P->max_march : R_MAX_MARCH;
     uint64_t st[16] = { 0 };
     t_sdf_evals = 0;
     t_grad_evals = 0;
@@ -684,7 +759,7 @@ int om_render_pixels(const om_render_params* P, const om_decoder* dec3, const in
         if (used > 24) return -1;
     }
     const double* grid = NULL;
-    if (P->mode == 1 && P->sdf_grid_n > 0) {
+    if (P->mode != 0 && P->sdf_grid_n > 0) {
         if (P->sdf_grid_n < 4 || P->disp_amp >= 1.0 || !P->sdf_grid) return -1;
         grid = P->sdf_grid;
     }
@@ -716,11 +791,13 @@ void om_decoder_sample(const om_decoder* D, const double* c, const double* z, co
 }
 
 /* First boundary crossing along p + t w, exposed for the tests: from outside (f(p) > 0) the re-entry
- * march, from inside the exit march with no collision.  Returns 1 with *t at the crossing, 0 when an
- * outside ray escapes, 2 when the step cap runs out. */
-int om_ray_crossing(double A, double k, const double* p, const double* w, double* t)
+ * march, from inside the exit march with no collision, with the three-bound step (plain = 0) or the Lipschitz
+ * step alone (plain = 1, with a step cap of 2^22).  Returns 1 with *t at the crossing, 0 when an outside ray
+ * escapes, 2 when the step cap runs out. */
+int om_ray_crossing(double A, double k, const double* p, const double* w, double* t, int plain)
 {
-    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3), NULL, 0, 0.0, 0.0, plain != 0,
+                plain ? (1 << 22) : R_MAX_MARCH };
     ov3 o = v3(p[0], p[1], p[2]), d = v3(w[0], w[1], w[2]), q = o;
     int r;
     if (sdf(&S, o) > 0.0) {
@@ -737,7 +814,7 @@ int om_ray_crossing(double A, double k, const double* p, const double* w, double
  * moves toward it), exposed for the tests. */
 double om_band_step(double A, double k, const double* p, const double* w)
 {
-    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3), NULL, 0, 0.0, 0.0, 0, R_MAX_MARCH };
     ov3 r = v3(p[0], p[1], p[2]), d = v3(w[0], w[1], w[2]);
     double f = sdf(&S, r);
     int inside = f < 0.0;
@@ -750,7 +827,7 @@ double om_band_step(double A, double k, const double* p, const double* w)
  * for the tests. */
 double om_march_step(double A, double k, const double* p, const double* w)
 {
-    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3), NULL, 0, 0.0, 0.0, 0, R_MAX_MARCH };
     ov3 r = v3(p[0], p[1], p[2]), d = v3(w[0], w[1], w[2]);
     int crossing, escape;
     double s = march_step(&S, r, d, sdf(&S, r) < 0.0, &crossing, &escape);
@@ -760,6 +837,6 @@ double om_march_step(double A, double k, const double* p, const double* w)
 /* Inside length of one segment, exposed for the tests. */
 double om_inside_length(double A, double k, const double* X, const double* xl)
 {
-    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3) };
+    scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3), NULL, 0, 0.0, 0.0, 0, R_MAX_MARCH };
     return inside_length(&S, v3(X[0], X[1], X[2]), v3(xl[0], xl[1], xl[2]));
 }

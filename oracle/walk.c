@@ -45,6 +45,8 @@ typedef struct {
     int32_t* rep_index;
     uint64_t *hist_n, *hist_pos, *hist_cos, *counters;
     pthread_mutex_t lock;
+    const double* nee_light;   /* optional: a point light outside the unit sphere; then nee_sum[i] receives */
+    double* nee_sum;           /* sum_k phi^k rho_g(W_k . w_L) exp(-tau d_k) / |x_L - X_k|^2 over the events */
 } walk_job;
 
 typedef struct {
@@ -154,6 +156,24 @@ typedef struct {
     uint64_t hist_n[64], hist_pos[32 * 64], hist_cos[64], counters[8];
 } walk_local;
 
+/* The Eq. 5 term of one event at X (inside the unit sphere) arriving with direction W, toward a point light
+ * at xl outside it, per unit light intensity: rho_g(W . w_L) exp(-tau d) / |xl - X|^2 with d the distance
+ * from X to the sphere along w_L (the medium fills the sphere of radius 1, optical radius tau). */
+static double event_nee(const double* xl, ov3 X, ov3 W, double tau, double g)
+{
+    ov3 dl = { xl[0] - X.x, xl[1] - X.y, xl[2] - X.z };
+    double d2 = dot3(dl, dl);
+    double D = sqrt(d2);
+    ov3 wl = { dl.x / D, dl.y / D, dl.z / D };
+    double b = dot3(X, wl), c = dot3(X, X) - 1.0;
+    double disc = b * b - c;
+    double d = -b + sqrt(disc > 0.0 ? disc : 0.0);
+    double mu = dot3(W, wl);
+    double den = 1.0 + g * g - 2.0 * g * mu;
+    double rho = (1.0 - g * g) / (4.0 * OM_PI * den * sqrt(den));
+    return rho * exp(-tau * d) / d2;
+}
+
 static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
 {
     const om_medium* m = J->media + (J->per_photon_media ? i : 0);
@@ -164,7 +184,7 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
     ov3 p = { 0.0, 0.0, 0.0 }, w, x = { 0.0, 0.0, 0.0 };
     ov3 rep_p = { 0.0, 0.0, 0.0 }, rep_w = { 0.0, 0.0, 0.0 };
     int32_t rep_k = 0;
-    double pw = 1.0, wsum = 0.0;
+    double pw = 1.0, wsum = 0.0, pe = 1.0, esum = 0.0;
     uint32_t n = 0;
     int status = OM_ESCAPED;
 
@@ -191,6 +211,10 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
                 break;
             }
             n = n + 1;
+            if (J->nee_light) {
+                pe = pe * phi;
+                esum = esum + pe * event_nee(J->nee_light, p, w, sig, g);
+            }
             if (J->reservoir_mode) {
                 double wk;
                 if (J->reservoir_mode == 1) {
@@ -256,6 +280,7 @@ static void walk_one(const walk_job* J, uint64_t i, walk_local* L)
         J->rep_dir[3 * i] = rep_w.x; J->rep_dir[3 * i + 1] = rep_w.y; J->rep_dir[3 * i + 2] = rep_w.z;
     }
     if (J->rep_index) J->rep_index[i] = rep_k;
+    if (J->nee_sum) J->nee_sum[i] = esum;
 }
 
 static void* walk_worker(void* arg)
@@ -280,25 +305,41 @@ static void* walk_worker(void* arg)
 }
 
 /*
+ * One walk record: photon `id` of key `seed` in the unit sphere at optical radius tau in the paper's
+ * convention (first event at the centre, incoming direction (0,0,1)), following the albedo-1 physics with
+ * the representative event chosen with weights phi^k (Sec. 3.2 and Sec. 4.3: the records the three models
+ * are trained on).  Outputs N, the exit point x and direction w, the representative event's position X and
+ * arriving direction W.  Returns the status (OM_ESCAPED, or OM_TRUNCATED after max_events events).  Used by
+ * the renderer's exact-sampler mode, which puts this walk where the three learned samplers would be.
+ */
+int om_walk_record(uint64_t seed, uint64_t id, double tau, double g, double phi, uint32_t max_events,
+                   int32_t* n, double x[3], double w[3], double X[3], double W[3])
+{
+    om_medium m = { tau, g, phi, { 0.0, 0.0, 1.0 }, 0, 1 };
+    uint8_t status = 0;
+    int32_t k = 0;
+    walk_job J = { seed, id, 1, &m, 0, max_events, 2, 53, n, &status, x, w, X, W, &k,
+                   NULL, NULL, NULL, NULL, PTHREAD_MUTEX_INITIALIZER, NULL, NULL };
+    walk_local L;
+    memset(&L, 0, sizeof(L));
+    walk_one(&J, 0, &L);
+    return (int)status;
+}
+
+/*
  * Run n_photons walks.  Per-photon arrays may be NULL; histograms and counters are accumulated into.
  * counters: [0] escaped, [1] absorbed, [2] truncated, [3] total events, [4..7] zero.
  * Returns the number of threads used.
  */
-int om_walk(uint64_t seed, uint64_t photon_offset, uint64_t n_photons, const om_medium* media,
-            int per_photon_media, uint32_t max_events, int reservoir_mode, int uniform_bits,
-            int32_t* n_events, uint8_t* status, double* exit_pos, double* exit_dir, double* rep_pos,
-            double* rep_dir, int32_t* rep_index, uint64_t* hist_n, uint64_t* hist_pos, uint64_t* hist_cos,
-            uint64_t* counters, int n_threads)
+static int run_walks(walk_job* J, int n_threads)
 {
-    walk_job J = { seed, photon_offset, n_photons, media, per_photon_media, max_events, reservoir_mode,
-                   uniform_bits == 24 ? 24 : 53, n_events, status, exit_pos, exit_dir, rep_pos, rep_dir,
-                   rep_index, hist_n, hist_pos, hist_cos, counters, PTHREAD_MUTEX_INITIALIZER };
+    uint64_t n_photons = J->n_photons;
     int nt = om_num_threads(n_threads);
     if ((uint64_t)nt > n_photons) nt = n_photons > 0 ? (int)n_photons : 1;
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
     walk_chunk* ch = (walk_chunk*)malloc(sizeof(walk_chunk) * (size_t)nt);
     for (int t = 0; t < nt; ++t) {
-        ch[t].job = &J;
+        ch[t].job = J;
         ch[t].begin = n_photons * (uint64_t)t / (uint64_t)nt;
         ch[t].end = n_photons * (uint64_t)(t + 1) / (uint64_t)nt;
         pthread_create(&th[t], NULL, walk_worker, &ch[t]);
@@ -308,4 +349,35 @@ int om_walk(uint64_t seed, uint64_t photon_offset, uint64_t n_photons, const om_
     free(th);
     free(ch);
     return nt;
+}
+
+int om_walk(uint64_t seed, uint64_t photon_offset, uint64_t n_photons, const om_medium* media,
+            int per_photon_media, uint32_t max_events, int reservoir_mode, int uniform_bits,
+            int32_t* n_events, uint8_t* status, double* exit_pos, double* exit_dir, double* rep_pos,
+            double* rep_dir, int32_t* rep_index, uint64_t* hist_n, uint64_t* hist_pos, uint64_t* hist_cos,
+            uint64_t* counters, int n_threads)
+{
+    walk_job J = { seed, photon_offset, n_photons, media, per_photon_media, max_events, reservoir_mode,
+                   uniform_bits == 24 ? 24 : 53, n_events, status, exit_pos, exit_dir, rep_pos, rep_dir,
+                   rep_index, hist_n, hist_pos, hist_cos, counters, PTHREAD_MUTEX_INITIALIZER, NULL, NULL };
+    return run_walks(&J, n_threads);
+}
+
+/*
+ * Walks of the training-record kind (paper convention, incoming direction (0,0,1), albedo-1 physics, the
+ * representative event chosen with weights phi^k: reservoir mode 2) that also return, per photon, the
+ * brute-force next-event sum over all of its events toward a point light at xl outside the unit sphere,
+ * nee_sum[i] = sum_{k=1..N} phi^k rho_g(W_k . w_L) exp(-tau d_k) / |xl - X_k|^2 (Eq. 5: the k-th event's
+ * estimate, weighted by the probability phi^(k-1) of reaching it and phi of its own survival term), beside
+ * N, the representative event's position, direction and index.  Lets a test compare Lambda^(N) times the
+ * representative event's term with the sum on the same walks (Sec. 4.3).  Returns the threads used.
+ */
+int om_walk_nee(uint64_t seed, uint64_t n_photons, double tau, double g, double phi, const double* xl,
+                int32_t* n_events, double* rep_pos, double* rep_dir, int32_t* rep_index, double* nee_sum,
+                int n_threads)
+{
+    om_medium m = { tau, g, phi, { 0.0, 0.0, 1.0 }, 0, 1 };
+    walk_job J = { seed, 0, n_photons, &m, 0, 1u << 24, 2, 53, n_events, NULL, NULL, NULL, rep_pos, rep_dir,
+                   rep_index, NULL, NULL, NULL, NULL, PTHREAD_MUTEX_INITIALIZER, xl, nee_sum };
+    return run_walks(&J, n_threads);
 }
