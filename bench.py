@@ -17,6 +17,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -29,17 +30,24 @@ SIGMAS = (16.0, 32.0, 64.0, 128.0)
 WORKLOAD = ("render of the displaced sphere 0.1 sin(6x)sin(6y)sin(6z), point light, 512x512 px, 256 spp, "
             "sigma_t {16,32,64,128}, g 0.8, albedo 0.999, CVAE sphere tracing + NEE (trained decoders)")
 
-# Algorithmic work per counted unit of the renderer's roofline: special-function (MUFU) operations per march
-# step (f and its derivative along the ray: sqrt + 3 sin/cos pairs), per sphere-radius evaluation at a
-# collision (f alone: sqrt + 3 sin), per sphere step (the three decoders' 2 x width Softplus each, as exp +
-# log; 10 posterior exps; 11 Box-Muller pairs x 4; 3 logs) and per brute-force event (log, sin/cos, rsqrt,
-# divide).
-MUFU_PER_MARCH = 7
-MUFU_PER_RADIUS = 4
-MUFU_PER_SPHERE = sum(2 * shape[3] * 2 for shape in (
-    (2, 1, 2, 8), (3, 3, 5, 16), (7, 6, 5, 16))) + 10 + 11 * 4 + 3      # Table 1 decoder shapes: 217
-MUFU_PER_EVENT = 5
-MUFU_PER_NEE = 4
+# Algorithmic work per counted unit of the renderer's roofline: special-function (MUFU) operations, split into
+# 2^x (which issues at twice the rate of the unit's other functions on this GPU) and the others (log2, sin, cos,
+# reciprocal square root, reciprocal), as (ex2, other):
+#   march step: f and its derivative along the ray, sqrt + 3 sin/cos pairs               (0, 7)
+#   sphere radius at a collision: f alone, sqrt + 3 sin                                   (0, 4)
+#   sphere step: the Table 1 decoders' Softplus (2 x width per decoder: 80 units, exp + log each), the 10
+#     posterior standard deviations exp(log Sigma / 2), N = exp(y), phi^N; 11 Box-Muller pairs (log, sqrt,
+#     sin, cos), log tau and log N, the rotation angle's sin/cos                          (92, 128)
+#   brute-force event: HG cosine (reciprocal), the scattering rotation (sin, cos, sqrt, rsqrt)  (0, 5)
+#   next-event estimate: the segment's length and direction (sqrt, reciprocal), rho_g (rsqrt, reciprocal),
+#     transmittance exp(-sigma_t d), 1 / d^2                                              (1, 5)
+#   flight: -log(1 - u) / sigma_t                                                         (0, 2)
+MUFU_MARCH = (0, 7)
+MUFU_RADIUS = (0, 4)
+MUFU_SPHERE = (2 * (8 + 16 + 16) + 10 + 1 + 1, 2 * (8 + 16 + 16) + 11 * 4 + 2 + 2)
+MUFU_EVENT = (0, 5)
+MUFU_NEE = (1, 5)
+MUFU_FLIGHT = (0, 2)
 
 
 def nproc():
@@ -107,10 +115,11 @@ def measured_peaks():
     return {}
 
 
-def recorded_traffic(variant: dict):
-    """DRAM bytes per launch of the render kernel from the committed one-pass ncu captures of the benchmark
-    launch (one per kernel variant), or None when the kernel sources changed since or the selected variant was
-    not captured."""
+def recorded_traffic(variant: dict, pixels: int):
+    """DRAM bytes of one render launch of ``pixels`` image pixels, from the committed ncu capture of smaller
+    launches of the same four-density batch (one launch each, ``profiles/``): the traffic is the images' reads and
+    write-backs plus a few register spills, so it scales with the pixels (checked between the two captured sizes),
+    not with the paths.  None when the kernel's sources changed since the capture, or for another variant."""
     import hashlib
     rec = json.loads((ROOT / "paper_2011_03082_b300" / "measured_traffic.json").read_text())["render_kernel"]
     h = hashlib.sha256()
@@ -118,9 +127,9 @@ def recorded_traffic(variant: dict):
         h.update((ROOT / f).read_bytes())
     if h.hexdigest() != rec["sha256"]:
         return None
-    key = "{decode_batch},{trans_batch},{steps},{min_blocks}".format(**variant)
-    v = rec["dram_bytes_per_launch"].get(key)
-    return None if v is None else float(v)
+    if "{decode_batch},{trans_batch},{steps},{min_blocks}".format(**variant) != rec["variant"]:
+        return None
+    return float(rec["bytes_per_pixel"]) * pixels
 
 
 # --------------------------------------------------------------------------------------------- CPU oracle
@@ -198,6 +207,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-equal-rmse", action="store_true", help="skip the equal-RMSE comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-request batch")
+    ap.add_argument("--eq-res", type=int, default=512, help="image side of the equal-RMSE comparison")
+    ap.add_argument("--eq-ref-spp", type=int, default=16384, help="spp of its brute-force reference")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="resolution and spp scale of the 64 requests")
     ap.add_argument("--variant", type=int, default=None, help="renderer variant to use instead of autotuning")
     args = ap.parse_args(argv)
     if args.impl == "reference":
@@ -240,6 +253,14 @@ def main(argv=None):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # measured issue rates of the ALU units (the roofline's denominators), with the SM clock while they ran
+    clock_dir = tempfile.mkdtemp(prefix="ms_bench_clocks_")
+    with ClockSampler(local, Path(clock_dir) / f"peaks_rank{rank}.csv") as pclk:
+        time.sleep(1.5)             # let the sampler start
+        alu = ms.ms_alu_peaks(dev)
+        alu = ms.ms_alu_peaks(dev)  # the second pass, with the clocks settled, is the one kept
+    alu_clocks = pclk.summary()
+
     # autotune the renderer's scheduling variant on a reduced sample of the same requests (untimed), unless a
     # variant is given
     if args.variant is None:
@@ -258,9 +279,7 @@ def main(argv=None):
     # ---------------- timed region: K steps, L2 flushed between steps ----------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats_acc = torch.zeros_like(stats)
-    out_dir = ROOT / "gpurun_out"
-    out_dir.mkdir(exist_ok=True)
-    with ClockSampler(local, out_dir / f"bench_clocks_rank{rank}.csv") as clk:
+    with ClockSampler(local, Path(clock_dir) / f"clocks_rank{rank}.csv") as clk:
         barrier()
         for k in range(args.steps):
             images.zero_()
@@ -272,6 +291,7 @@ def main(argv=None):
             stats_acc += stats
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    img_fp32 = images.clone()        # the last timed step's images (FP32 decoders), for the precision form below
     t_ms = float(np.sum(step_ms))
     paths_rank = float(stats_acc[:, 0].sum().item())
     t_max = t_ms
@@ -284,6 +304,8 @@ def main(argv=None):
         dist.all_reduce(pp)
         paths_all = float(pp.item())
     value = paths_all / (t_max / 1e3)
+    # light paths that enter the medium (the rest miss the object and cost one march)
+    entering = float(stats_acc[:, 1].sum().item()) * world / (t_max / 1e3)
     st = stats_acc.sum(dim=0).cpu().numpy().astype(np.float64)
     per_req = (stats_acc.cpu().numpy() / args.steps).astype(np.int64).tolist()
 
@@ -292,17 +314,29 @@ def main(argv=None):
     clocks = clk.summary()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2032.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    mufu_peak = n_sm * 16 * sm_mhz_max * 1e6 / 1e12              # Tops/s at the maximum SM clock
     # every collision of a sphere-tracing request evaluates f once for the sphere's radius (counted in st[8])
     radius_evals = st[3] + st[4]
-    mufu_ops = ((st[8] - radius_evals) * MUFU_PER_MARCH + radius_evals * MUFU_PER_RADIUS + st[3] * MUFU_PER_SPHERE
-                + st[4] * MUFU_PER_EVENT + st[7] * MUFU_PER_NEE + st[2] * 2)
+    units = ((st[8] - radius_evals, MUFU_MARCH), (radius_evals, MUFU_RADIUS), (st[3], MUFU_SPHERE),
+             (st[4], MUFU_EVENT), (st[7], MUFU_NEE), (st[2], MUFU_FLIGHT))
+    ex2_ops = sum(n * c[0] for n, c in units)
+    other_ops = sum(n * c[1] for n, c in units)
+    # the special-function unit's shortest time for this mix at the measured rates, hence its effective peak
+    t_min = ex2_ops / alu["ex2"] + other_ops / min(alu["lg2"], alu["sin"], alu["rsqrt"])
+    mufu_ops = ex2_ops + other_ops
+    mufu_peak = mufu_ops / t_min / 1e12
     achieved = mufu_ops / (t_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
-                "frac": achieved / mufu_peak, "traffic": recorded_traffic(ms.ms_render_variant_info(variant)),
-                "traffic_unit": "DRAM bytes per launch (committed ncu capture; null if the kernel changed)",
+                "frac": achieved / mufu_peak, "traffic": recorded_traffic(ms.ms_render_variant_info(variant), W * H *
+                                                                           len(reqs)),
+                "traffic_unit": "DRAM bytes per launch (ncu capture of a smaller launch scaled by pixels; null if the "
+                                "kernel changed)",
                 "kernel": "render_kernel",
-                "peak_source": f"{n_sm} SMs x 16 MUFU ops/clk x {sm_mhz_max:.0f} MHz (recipe unit counts, max clock)"}
+                "peak_source": "measured (ms_alu_peaks, of measured): the special-function unit's rate for this "
+                               f"kernel's mix of {ex2_ops:.3e} 2^x and {other_ops:.3e} other operations per step "
+                               "(2^x at its own measured rate, the rest at that of log2 / sin / rsqrt); SM clock "
+                               f"{alu_clocks.get('sm_mhz')} MHz while measured",
+                "mufu_ops_per_step": {"ex2": ex2_ops / args.steps, "other": other_ops / args.steps},
+                "alu_peaks_tops": {k: v / 1e12 for k, v in alu.items()}}
 
     # ---------------- end to end through the C ABI with host buffers ----------------
     host_w = {k: (torch.from_numpy(pipeline.decoder_part(k, models[k]["params"])).pin_memory(), *synth.MODEL_SHAPES[k])
@@ -360,14 +394,54 @@ def main(argv=None):
                  "speedup_equal_spp": (bpaths / (bt / 1e3)) and value / world / (bpaths / (bt / 1e3)),
                  "events_per_path": float(stats[:, 4].sum().item()) / max(1.0, float(stats[:, 1].sum().item()))}
 
-    # ---------------- equal-RMSE comparison with brute force (context; after the timed region) ----------------
-    equal = None
-    if rank == 0 and not args.no_equal_rmse:
+    # ---------------- the precision form: the same step with FP16 and BF16 decoders (context) ----------------
+    precision = {}
+    for name, code in (("fp16", ms.MS_FP16), ("bf16", ms.MS_BF16)):
+        cs_h = ms.cvae_set(dm, precision=code)
+        images.zero_()
+        stats.zero_()
+        ms.ms_render_batch(preqs, cs_h, images, stats, ws=ws)      # warm-up
+        images.zero_()
+        stats.zero_()
+        flush.fill_(9)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ms.ms_render_batch(preqs, cs_h, images, stats, ws=ws)
+        b.record(stream)
+        b.synchronize()
+        th = a.elapsed_time(b)
+        d = (images - img_fp32).double()
+        precision[name] = {"paths_per_s": float(stats[:, 0].sum().item()) / (th / 1e3), "ms_per_step": th,
+                           "image_rmse_vs_fp32_decoders": float(torch.sqrt(torch.mean(d * d)).item()) / spp,
+                           "image_rms": float(torch.sqrt(torch.mean(img_fp32.double() ** 2)).item()) / spp}
+
+    # ---------------- equal-RMSE comparison with brute force and the fallback policy (after the timed region) --
+    equal = policy = batch = None
+    if rank == 0 and world == 1 and not args.no_equal_rmse:
         from paper_2011_03082_b300 import experiments
-        rows = experiments.equal_rmse(res=128, ref_spp=8192, st_spp=256, cset=cset, variant=variant)
-        equal = {"res": 128, "ref_spp": 8192, "st_spp": 256,
-                 "per_sigma": [{k: r[k] for k in ("sigma_t", "rmse_st", "spp_bf_equal", "t_st_s", "t_bf_equal_s",
-                                                  "speedup", "note")} for r in rows]}
+        refs = experiments.reference_images(SIGMAS, args.eq_res, args.eq_ref_spp, variant, cset)
+        rows = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
+                                      variant=variant, refs=refs, tau_min=1.0)
+        rows_auto = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
+                                           variant=variant, refs=refs, tau_min=0.0)
+        keys = ("sigma_t", "tau_min", "rmse_st", "spp_bf_equal", "t_st_s", "t_bf_equal_s", "speedup", "note")
+        equal = {"res": args.eq_res, "ref_spp": args.eq_ref_spp, "st_spp": spp,
+                 "per_sigma": [{k: r[k] for k in keys} for r in rows],
+                 "per_sigma_default_policy": [dict({k: r[k] for k in keys},
+                                                   tau_min_used=float(
+                                                       ms.lib().ms_render_default_min_optical_radius(r["sigma_t"])))
+                                              for r in rows_auto]}
+        pol = experiments.fallback_policy(SIGMAS, res=args.eq_res, spp=spp, ref_spp=args.eq_ref_spp, cset=cset,
+                                          variant=variant, refs=refs)
+        policy = [{"sigma_t": r["sigma_t"], "best_tau_min": r["best_tau_min"],
+                   "library_default": r["library_default"],
+                   "sweep": [{k: v for k, v in x.items() if k != "mode"} for x in r["sweep"]]} for r in pol]
+        del refs
+    if rank == 0 and world == 1 and not args.no_batched:
+        from paper_2011_03082_b300 import experiments
+        b = experiments.batched(seed=5, n=64, scale=args.batch_scale, repeats=1, cset=cset, sequential=False)
+        batch = {k: b[k] for k in ("requests", "scale", "paths", "seconds", "paths_per_s", "variant", "p50_ms",
+                                   "p99_ms", "launch")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -385,7 +459,9 @@ def main(argv=None):
                            "kernel_variant": dict(index=variant, **ms.ms_render_variant_info(variant)),
                            "autotune_ms": [round(t, 2) for t in variant_ms]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clocks, "brute_force": brute, "equal_rmse": equal, "step_ms": step_ms}
+                "clocks": clocks, "entering_paths_per_s": entering, "brute_force": brute,
+                "decoder_precision": precision, "equal_rmse": equal,
+                "fallback_policy": policy, "batched_64": batch, "step_ms": step_ms}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -17,9 +17,15 @@
  *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL means the legacy default stream);
  *    the call returns before the GPU finishes.  Outputs documented as "accumulated" are added to, so calls
  *    on disjoint photon or sample ranges (photon_offset, sample_offset) compose; the caller zeroes them.
- *  - Arguments are validated on the host before anything is enqueued.  Errors return a negative ms_status
- *    and leave a message for ms_last_error() (per host thread); no exception crosses the ABI.  A call that
- *    returns an error has enqueued nothing.
+ *  - Arguments passed by value or in host structs are validated on the host before anything is enqueued.
+ *    Errors return a negative ms_status and leave a message for ms_last_error() (per host thread); no
+ *    exception crosses the ABI.  A call that returns an error has enqueued nothing.  Values the caller keeps
+ *    in device memory (per-photon media, weights, training data) are not read by the host and are not
+ *    validated; out-of-range values there give meaningless results but cannot fault: every device loop has a
+ *    cap and every histogram or voxel index is clamped.
+ *  - Caps that are reached (events per photon, segments per path, steps per march) are counted in the
+ *    asynchronous counters of the call (walk counters[2], render stats[6]); they are not return codes,
+ *    because every call returns before the GPU finishes.
  *  - Random numbers come from the counter-based generator Philox4x32-10 keyed by `seed`; results depend only
  *    on (seed, ids, offsets) and not on launch configuration.
  */
@@ -35,10 +41,8 @@ extern "C" {
 
 typedef enum {
     MS_OK = 0,
-    MS_WARN_TRUNCATED = 1,      /* reserved: caps are reported in the asynchronous counters instead         */
     MS_ERR_INVALID_ARG = -1,
     MS_ERR_CUDA = -2,           /* a CUDA runtime call failed; ms_last_error() has the CUDA error string   */
-    MS_ERR_TIMEOUT = -3,        /* a device loop exhausted its iteration budget                           */
     MS_ERR_UNSUPPORTED = -4     /* unsupported shape or precision                                         */
 } ms_status;
 
@@ -112,7 +116,8 @@ typedef struct {
 
 size_t ms_walk_workspace_size(const ms_walk_params* p);
 /* Truncated photons are counted in counters[2]; the call does not wait for the GPU, so it returns MS_OK
- * and the caller reads the counters. */
+ * and the caller reads the counters.  The media are device memory and are not validated (see the
+ * conventions above): the ranges in ms_medium are the caller's to respect. */
 ms_status ms_simulate_walks(const ms_walk_params* p, const ms_walk_out* out, void* workspace,
                             size_t workspace_bytes, void* stream);
 
@@ -167,6 +172,13 @@ ms_status ms_cvae_forward_backward(const ms_cvae_shape* s, const float* params, 
                                    const float* eps_z, uint64_t B, uint64_t seed, uint64_t step, float* grad,
                                    float* loss3, void* workspace, size_t workspace_bytes, void* stream);
 
+/* The loss alone (no gradient): loss3 (device [3], overwritten) = loss, rec, kl of the batch, from the same
+ * forward pass, normals and fixed-order reduction as ms_cvae_forward_backward (equal to its loss3 bit for
+ * bit).  Workspace as for ms_cvae_forward_backward.  The forward half of the torch.autograd.Function. */
+ms_status ms_cvae_forward(const ms_cvae_shape* s, const float* params, const float* x, const float* c,
+                          const float* eps_z, uint64_t B, uint64_t seed, uint64_t step, float* loss3,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
 /* One bias-corrected Adam step t >= 1 on n parameters (device arrays, in place). */
 ms_status ms_adam_step(float* params, float* m, float* v, const float* grad, uint64_t n, uint64_t t, float lr,
                        float beta1, float beta2, float eps, float weight_decay, void* stream);
@@ -199,8 +211,10 @@ ms_status ms_cvae_train_step_dev(const ms_cvae_shape* s, float* params, float* m
  *  - Every device that loads the library keeps the array until the process exits.
  *  - All calls share the array: calls whose work overlaps on the GPU race and corrupt each other's
  *    gradients.  Nothing in it needs clearing between calls (each call overwrites what it reads).
- *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress); make that first
- *    call before any stream capture. */
+ *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress) and keeps it with
+ *    the identity of the current CUDA context; a call in a later context of that device (after
+ *    cudaDeviceReset) looks it up again.  Make the first call on a device, and the first call after a reset,
+ *    before any stream capture. */
 size_t ms_cvae_static_scratch_bytes(void);
 ms_status ms_cvae_train_step_static(const ms_cvae_shape* s, float* params, float* m, float* v, const float* x,
                                     const float* c, const float* eps_z, uint64_t B, uint64_t seed, uint64_t step,
@@ -242,7 +256,8 @@ typedef struct {
     float sigma_t, g, albedo;
     float disp_amp, disp_freq;  /* A, k of the SDF                                                     */
     int32_t mode;               /* MS_BRUTE or MS_SPHERE                                               */
-    float min_optical_radius;   /* smallest sigma_t * r for a sphere step (thin-region fallback)      */
+    float min_optical_radius;   /* smallest sigma_t * r for a sphere step (thin-region fallback); <= 0
+                                   takes ms_render_default_min_optical_radius(sigma_t)                  */
     float max_optical_radius;   /* largest sigma_t * r (the training range of the models)             */
     uint64_t seed, sample_offset;
     int32_t variant;            /* kernel variant (scheduling constants), 0..ms_render_variants()-1, 0 by
@@ -254,14 +269,17 @@ typedef struct {
 } ms_render_params;
 
 /* The voxel grid of conservative distances that sizes sphere steps (Sec. 3: the bounding volume is voxelised
- * in a pre-process, each voxel holding a conservative shortest Chebyshev distance to the surface).  grid:
- * device [n][n][n] floats, index (iz * n + iy) * n + ix; with h = 2 (1 + disp_amp) / (n - 2) and
- * b = 1 + disp_amp + h, voxel (ix, iy, iz) is the cube [-b + ix h, -b + (ix + 1) h] x ... (one voxel of
- * margin around the bounding sphere).  A voxel may hold surface if |f(c)| <= (1 + A k) h sqrt(3) / 2 at its
- * centre c; every voxel's value is (m - 1) h, clamped at 0, with m its Chebyshev (L-infinity) index distance
- * to the nearest such voxel — a lower bound of the distance from each of its points to the surface.
- * workspace: device, 16-byte aligned, ms_sdf_grid_workspace_size(n) bytes (two integer grids).
- * n in 4..1024, 0 <= disp_amp < 1.  Asynchronous on `stream` (n + 2 kernel launches). */
+ * in a pre-process, each voxel holding a conservative shortest distance to the surface).  grid: device
+ * [n][n][n] floats, index (iz * n + iy) * n + ix; with h = 2 (1 + disp_amp) / (n - 2) and b = 1 + disp_amp + h,
+ * voxel (ix, iy, iz) is the cube [-b + ix h, -b + (ix + 1) h] x ... (one voxel of margin around the bounding
+ * sphere).  A voxel may hold surface if |f(c)| <= (1 + A k) h sqrt(3) / 2 at its centre c.  Every voxel's
+ * value is (e - sqrt(3)) h, clamped at 0, with e the exact Euclidean distance, in voxels, from its centre to
+ * the nearest such voxel's centre (three separable integer passes): two points of two voxels are at most one
+ * voxel diagonal, sqrt(3) h, nearer than their centres, so the value is a lower bound of the distance from
+ * each of the voxel's points to the surface.  (The paper stores a Chebyshev distance, which is also
+ * conservative but up to sqrt(3) smaller along diagonals.)  workspace: device, 16-byte aligned,
+ * ms_sdf_grid_workspace_size(n) bytes (two integer grids).  n in 4..1024, 0 <= disp_amp < 1.  Asynchronous on
+ * `stream` (five kernel launches: marking, three distance passes, values). */
 size_t ms_sdf_grid_workspace_size(int32_t n);
 ms_status ms_sdf_grid_build(float disp_amp, float disp_freq, int32_t n, float* grid, void* workspace,
                             size_t workspace_bytes, void* stream);
@@ -280,6 +298,12 @@ typedef struct {
 } ms_cvae_set;
 
 size_t ms_render_workspace_size(const ms_render_params* reqs, int n_requests);
+
+/* The thin-region fallback policy (Sec. 6): the minimum optical radius sigma_t r of a sphere step that a request
+ * with min_optical_radius <= 0 uses at density sigma_t.  Chosen per density as the threshold of lowest
+ * time x squared error against a brute-force reference (the displaced-sphere scene, the trained decoders),
+ * interpolated in log sigma_t between the measured densities and held constant beyond them.  Host only. */
+float ms_render_default_min_optical_radius(float sigma_t);
 
 /* image: device [height][width] doubles, accumulated: the sum over the pixel's samples (divide by spp).
  * stats: device [MS_RENDER_STATS] accumulated: [0] camera paths, [1] paths entering the object, [2] flights,
@@ -311,6 +335,21 @@ ms_status ms_render_variant_info(int i, int* decode_batch, int* trans_batch, int
 ms_status ms_render_autotune(const ms_render_params* reqs, int n, const ms_cvae_set* models, double* images,
                              unsigned long long* stats, void* workspace, size_t workspace_bytes, int repeats,
                              int* best_variant, float* ms_per_variant, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Measured peak issue rates of the execution units that bound the library's ALU-bound kernels: the
+ * denominators of the roofline fractions the benchmark reports.  The paper has no counterpart; this is a
+ * measurement helper.  ops_per_s: host [MS_PEAK_COUNT], whole-GPU operations (instructions per thread, one
+ * per lane) per second: FP32 fused multiply-add (2 flops each), the special-function unit's 2^x, log2 x,
+ * sin x and 1/sqrt x approximations, integer multiply-add, three-input logic and high-half multiply.  Each is
+ * timed with CUDA events on `stream` in a full-occupancy grid of independent dependency chains; the call waits
+ * for the stream.  scratch: device, ms_alu_peaks_scratch_bytes() bytes (each thread's result, so that nothing
+ * is optimised away).
+ * ---------------------------------------------------------------------------------------------------- */
+enum { MS_PEAK_FFMA = 0, MS_PEAK_EX2, MS_PEAK_LG2, MS_PEAK_SIN, MS_PEAK_RSQRT, MS_PEAK_IMAD, MS_PEAK_LOP3,
+       MS_PEAK_IMULHI, MS_PEAK_COUNT };
+size_t ms_alu_peaks_scratch_bytes(void);
+ms_status ms_alu_peaks(double* ops_per_s, void* scratch, size_t scratch_bytes, void* stream);
 
 #ifdef __cplusplus
 }

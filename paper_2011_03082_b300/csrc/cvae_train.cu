@@ -130,7 +130,9 @@ __device__ __forceinline__ void stage_matrix(float* __restrict__ dst, const floa
     }
 }
 
-template <int PI, int PO, int kW, int kL, bool kBF16>
+// kGrad = false: the loss alone (ms_cvae_forward): no backward pass and no staging slots in shared memory; only
+// the two loss partials of the block are written.
+template <int PI, int PO, int kW, int kL, bool kBF16, bool kGrad = true>
 __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ prm, const float* __restrict__ X,
                                                     const float* __restrict__ Cc, const float* __restrict__ EPS,
                                                     uint64_t B, uint64_t seed, uint64_t step,
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     float* row_base = sm;   // [NSLOT][SLOT]: sample s of a slot at s * R
     auto row = [&](int slot, int s) -> float* { return row_base + (size_t)slot * S::SLOT + (size_t)s * S::R; };
     __shared__ float s_rec[kSamples / 32], s_kl[kSamples / 32];
-    float* ws = sm + S::NSLOT * S::SLOT;    // padded weight matrices
+    float* ws = sm + (kGrad ? S::NSLOT * S::SLOT : 0);    // padded weight matrices
     stage_matrix<kW, S::IE>(ws + S::sE1, prm + S::E1);
     stage_matrix<kW, kW>(ws + S::sE2, prm + S::E2);
     stage_matrix<2 * kL, kW>(ws + S::sE3, prm + S::E3);
@@ -222,51 +224,53 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
 #pragma unroll
     for (int l = 0; l < kL; ++l) kl += 0.5f * (oe[l] * oe[l] + sd_e[l] * sd_e[l] - oe[kL + l] - 1.0f);
 
-    // ---------------- backward ----------------
-    float dh[kW], da2d[kW], da1d[kW], ddin[S::ID];
-    bwd_layer<kW, 2 * PO, kBF16>(ws + S::sD3, dy, dh);
-#pragma unroll
-    for (int o = 0; o < kW; ++o) da2d[o] = dh[o] * sigmoidf_fast(a2d[o]);
-    bwd_layer<kW, kW, kBF16>(ws + S::sD2, da2d, dh);
-#pragma unroll
-    for (int o = 0; o < kW; ++o) da1d[o] = dh[o] * sigmoidf_fast(a1d[o]);
-    bwd_layer<S::ID, kW, kBF16>(ws + S::sD1, da1d, ddin);
-    float doe[2 * kL];
-#pragma unroll
-    for (int l = 0; l < kL; ++l) {
-        const float dz = ddin[PI + l];
-        doe[l] = live ? dz + oe[l] * invB : 0.0f;
-        doe[kL + l] = live ? dz * eps[l] * 0.5f * sd_e[l] + 0.5f * (sd_e[l] * sd_e[l] - 1.0f) * invB : 0.0f;
-    }
-    float da2e[kW], da1e[kW];
-    bwd_layer<kW, 2 * kL, kBF16>(ws + S::sE3, doe, dh);
-#pragma unroll
-    for (int o = 0; o < kW; ++o) da2e[o] = dh[o] * sigmoidf_fast(a2e[o]);
-    bwd_layer<kW, kW, kBF16>(ws + S::sE2, da2e, dh);
-#pragma unroll
-    for (int o = 0; o < kW; ++o) da1e[o] = dh[o] * sigmoidf_fast(a1e[o]);
-
-    // ---------------- stage layer inputs and deltas ----------------
     const float m = live ? 1.0f : 0.0f;
+    if constexpr (kGrad) {
+        // ---------------- backward ----------------
+        float dh[kW], da2d[kW], da1d[kW], ddin[S::ID];
+        bwd_layer<kW, 2 * PO, kBF16>(ws + S::sD3, dy, dh);
 #pragma unroll
-    for (int k = 0; k < S::IE; ++k) row(S::IN1E, t)[k] = xin[k] * m;
+        for (int o = 0; o < kW; ++o) da2d[o] = dh[o] * sigmoidf_fast(a2d[o]);
+        bwd_layer<kW, kW, kBF16>(ws + S::sD2, da2d, dh);
 #pragma unroll
-    for (int k = 0; k < kW; ++k) {
-        row(S::H1E, t)[k] = h1e[k] * m;
-        row(S::H2E, t)[k] = h2e[k] * m;
-        row(S::H1D, t)[k] = h1d[k] * m;
-        row(S::H2D, t)[k] = h2d[k] * m;
-        row(S::DA1E, t)[k] = da1e[k];
-        row(S::DA2E, t)[k] = da2e[k];
-        row(S::DA1D, t)[k] = da1d[k];
-        row(S::DA2D, t)[k] = da2d[k];
+        for (int o = 0; o < kW; ++o) da1d[o] = dh[o] * sigmoidf_fast(a1d[o]);
+        bwd_layer<S::ID, kW, kBF16>(ws + S::sD1, da1d, ddin);
+        float doe[2 * kL];
+#pragma unroll
+        for (int l = 0; l < kL; ++l) {
+            const float dz = ddin[PI + l];
+            doe[l] = live ? dz + oe[l] * invB : 0.0f;
+            doe[kL + l] = live ? dz * eps[l] * 0.5f * sd_e[l] + 0.5f * (sd_e[l] * sd_e[l] - 1.0f) * invB : 0.0f;
+        }
+        float da2e[kW], da1e[kW];
+        bwd_layer<kW, 2 * kL, kBF16>(ws + S::sE3, doe, dh);
+#pragma unroll
+        for (int o = 0; o < kW; ++o) da2e[o] = dh[o] * sigmoidf_fast(a2e[o]);
+        bwd_layer<kW, kW, kBF16>(ws + S::sE2, da2e, dh);
+#pragma unroll
+        for (int o = 0; o < kW; ++o) da1e[o] = dh[o] * sigmoidf_fast(a1e[o]);
+
+        // ---------------- stage layer inputs and deltas ----------------
+#pragma unroll
+        for (int k = 0; k < S::IE; ++k) row(S::IN1E, t)[k] = xin[k] * m;
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            row(S::H1E, t)[k] = h1e[k] * m;
+            row(S::H2E, t)[k] = h2e[k] * m;
+            row(S::H1D, t)[k] = h1d[k] * m;
+            row(S::H2D, t)[k] = h2d[k] * m;
+            row(S::DA1E, t)[k] = da1e[k];
+            row(S::DA2E, t)[k] = da2e[k];
+            row(S::DA1D, t)[k] = da1d[k];
+            row(S::DA2D, t)[k] = da2d[k];
+        }
+#pragma unroll
+        for (int k = 0; k < S::ID; ++k) row(S::IN1D, t)[k] = din[k] * m;
+#pragma unroll
+        for (int k = 0; k < 2 * kL; ++k) row(S::DOE, t)[k] = doe[k];
+#pragma unroll
+        for (int k = 0; k < 2 * PO; ++k) row(S::DY, t)[k] = dy[k];
     }
-#pragma unroll
-    for (int k = 0; k < S::ID; ++k) row(S::IN1D, t)[k] = din[k] * m;
-#pragma unroll
-    for (int k = 0; k < 2 * kL; ++k) row(S::DOE, t)[k] = doe[k];
-#pragma unroll
-    for (int k = 0; k < 2 * PO; ++k) row(S::DY, t)[k] = dy[k];
     // loss partials (fixed-order warp and block sums)
     rec *= m;
     kl *= m;
@@ -277,138 +281,139 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     }
     if ((t & 31) == 0) { s_rec[t >> 5] = rec; s_kl[t >> 5] = kl; }
     __syncthreads();
-
-    // ---------------- block gradient: 4 x 4 register tiles, samples in order ----------------
-    // Work items: per layer, the ceil(O/4) x ceil(K/4) tiles of dW = sum_s delta_s x_s^T and the ceil(O/4) 4-wide
-    // tiles of db = sum_s delta_s.  Each parameter is summed over the block's samples in sample order (one FMA or
-    // add per sample), exactly as a one-thread-per-parameter loop would.  Tile entries past O or K read row
-    // padding and are not stored.
     float* out = partial + (size_t)blockIdx.x * (S::NP + 2);
-    auto tiles = [&](auto O_, auto K_, int dslot, int islot, int bW, int bb, int item) {
-        constexpr int O = decltype(O_)::value, K = decltype(K_)::value;
-        constexpr int TO = (O + 3) / 4, TK = (K + 3) / 4;
-        const float* dr = row(dslot, 0);
-        if (item < TO * TK) {
-            const int o0 = 4 * (item / TK), k0 = 4 * (item % TK);
-            const float* xr = row(islot, 0) + k0;
-            dr += o0;
-            float acc[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-#pragma unroll 4
-            for (int smp = 0; smp < kSamples; ++smp) {
-                const float* d = dr + smp * S::R;
-                const float* x = xr + smp * S::R;
-                const float d4[4] = {d[0], d[1], d[2], d[3]}, x4[4] = {x[0], x[1], x[2], x[3]};
+    if constexpr (kGrad) {
+        // ---------------- block gradient: 4 x 4 register tiles, samples in order ----------------
+        // Work items: per layer, the ceil(O/4) x ceil(K/4) tiles of dW = sum_s delta_s x_s^T and the ceil(O/4) 4-wide
+        // tiles of db = sum_s delta_s.  Each parameter is summed over the block's samples in sample order (one FMA or
+        // add per sample), exactly as a one-thread-per-parameter loop would.  Tile entries past O or K read row
+        // padding and are not stored.
+        auto tiles = [&](auto O_, auto K_, int dslot, int islot, int bW, int bb, int item) {
+            constexpr int O = decltype(O_)::value, K = decltype(K_)::value;
+            constexpr int TO = (O + 3) / 4, TK = (K + 3) / 4;
+            const float* dr = row(dslot, 0);
+            if (item < TO * TK) {
+                const int o0 = 4 * (item / TK), k0 = 4 * (item % TK);
+                const float* xr = row(islot, 0) + k0;
+                dr += o0;
+                float acc[4][4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(d4[i], x4[j], acc[i][j]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (o0 + i < O && k0 + j < K) out[bW + (o0 + i) * K + k0 + j] = acc[i][j];
-        } else {
-            const int o0 = 4 * (item - TO * TK);
-            dr += o0;
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
 #pragma unroll 4
-            for (int smp = 0; smp < kSamples; ++smp) {
-                const float* d = dr + smp * S::R;
+                for (int smp = 0; smp < kSamples; ++smp) {
+                    const float* d = dr + smp * S::R;
+                    const float* x = xr + smp * S::R;
+                    const float d4[4] = {d[0], d[1], d[2], d[3]}, x4[4] = {x[0], x[1], x[2], x[3]};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] += d[i];
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(d4[i], x4[j], acc[i][j]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (o0 + i < O && k0 + j < K) out[bW + (o0 + i) * K + k0 + j] = acc[i][j];
+            } else {
+                const int o0 = 4 * (item - TO * TK);
+                dr += o0;
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+                for (int smp = 0; smp < kSamples; ++smp) {
+                    const float* d = dr + smp * S::R;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] += d[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (o0 + i < O) out[bb + o0 + i] = acc[i];
             }
+        };
+        using IE = std::integral_constant<int, S::IE>;
+        using ID = std::integral_constant<int, S::ID>;
+        using W_ = std::integral_constant<int, kW>;
+        using L2 = std::integral_constant<int, 2 * kL>;
+        using P2 = std::integral_constant<int, 2 * PO>;
+        constexpr int T1 = ((kW + 3) / 4) * ((S::IE + 3) / 4) + (kW + 3) / 4;
+        constexpr int T2 = ((kW + 3) / 4) * ((kW + 3) / 4) + (kW + 3) / 4;
+        constexpr int T3 = ((2 * kL + 3) / 4) * ((kW + 3) / 4) + (2 * kL + 3) / 4;
+        constexpr int T4 = ((kW + 3) / 4) * ((S::ID + 3) / 4) + (kW + 3) / 4;
+        constexpr int T6 = ((2 * PO + 3) / 4) * ((kW + 3) / 4) + (2 * PO + 3) / 4;
+        constexpr int B1 = T1, B2 = B1 + T2, B3 = B2 + T3, B4 = B3 + T4, B5 = B4 + T2, B6 = B5 + T6;
+        // FP32: each warp forms whole layers' dW = D^T X and db = D^T 1 on the tensor cores (3xTF32, m16n8k8,
+        // the block's 128 samples as the k dimension in order); the output rows o >= O and columns k >= K read row
+        // padding and are not stored.  BF16 keeps the FFMA tiles above.
+        auto mma_grad = [&](auto O_, auto K_, int dslot, int islot, int bW, int bb) {
+            constexpr int O = decltype(O_)::value, K = decltype(K_)::value;
+            constexpr int NT = (K + 7) / 8;
+            const int lane = t & 31, g = lane >> 2, q = lane & 3;
+            float acc[NT][4], accb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (o0 + i < O) out[bb + o0 + i] = acc[i];
-        }
-    };
-    using IE = std::integral_constant<int, S::IE>;
-    using ID = std::integral_constant<int, S::ID>;
-    using W_ = std::integral_constant<int, kW>;
-    using L2 = std::integral_constant<int, 2 * kL>;
-    using P2 = std::integral_constant<int, 2 * PO>;
-    constexpr int T1 = ((kW + 3) / 4) * ((S::IE + 3) / 4) + (kW + 3) / 4;
-    constexpr int T2 = ((kW + 3) / 4) * ((kW + 3) / 4) + (kW + 3) / 4;
-    constexpr int T3 = ((2 * kL + 3) / 4) * ((kW + 3) / 4) + (2 * kL + 3) / 4;
-    constexpr int T4 = ((kW + 3) / 4) * ((S::ID + 3) / 4) + (kW + 3) / 4;
-    constexpr int T6 = ((2 * PO + 3) / 4) * ((kW + 3) / 4) + (2 * PO + 3) / 4;
-    constexpr int B1 = T1, B2 = B1 + T2, B3 = B2 + T3, B4 = B3 + T4, B5 = B4 + T2, B6 = B5 + T6;
-    // FP32: each warp forms whole layers' dW = D^T X and db = D^T 1 on the tensor cores (3xTF32, m16n8k8,
-    // the block's 128 samples as the k dimension in order); the output rows o >= O and columns k >= K read row
-    // padding and are not stored.  BF16 keeps the FFMA tiles above.
-    auto mma_grad = [&](auto O_, auto K_, int dslot, int islot, int bW, int bb) {
-        constexpr int O = decltype(O_)::value, K = decltype(K_)::value;
-        constexpr int NT = (K + 7) / 8;
-        const int lane = t & 31, g = lane >> 2, q = lane & 3;
-        float acc[NT][4], accb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-        const uint32_t one = g == 0 ? 0x3f800000u : 0u;     // B = the ones column (n = 0): the bias gradient
+            for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+            const uint32_t one = g == 0 ? 0x3f800000u : 0u;     // B = the ones column (n = 0): the bias gradient
 #pragma unroll 2
-        for (int s0 = 0; s0 < kSamples; s0 += 8) {
-            // A[o][s] = D[s0 + s][o]: (g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4)
-            const float* d0 = row(dslot, s0 + q);
-            const float* d1 = row(dslot, s0 + q + 4);
-            uint32_t ah[4], al[4];
-            split_tf32(d0[g], ah[0], al[0]);
-            split_tf32(d0[g + 8], ah[1], al[1]);
-            split_tf32(d1[g], ah[2], al[2]);
-            split_tf32(d1[g + 8], ah[3], al[3]);
-            const float* x0 = row(islot, s0 + q);
-            const float* x1 = row(islot, s0 + q + 4);
+            for (int s0 = 0; s0 < kSamples; s0 += 8) {
+                // A[o][s] = D[s0 + s][o]: (g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4)
+                const float* d0 = row(dslot, s0 + q);
+                const float* d1 = row(dslot, s0 + q + 4);
+                uint32_t ah[4], al[4];
+                split_tf32(d0[g], ah[0], al[0]);
+                split_tf32(d0[g + 8], ah[1], al[1]);
+                split_tf32(d1[g], ah[2], al[2]);
+                split_tf32(d1[g + 8], ah[3], al[3]);
+                const float* x0 = row(islot, s0 + q);
+                const float* x1 = row(islot, s0 + q + 4);
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                // B[s][k] = X[s0 + s][8 nt + k]: (q, g), (q + 4, g)
-                uint32_t bh0, bl0, bh1, bl1;
-                split_tf32(x0[8 * nt + g], bh0, bl0);
-                split_tf32(x1[8 * nt + g], bh1, bl1);
-                mma_tf32(acc[nt], al[0], al[1], al[2], al[3], bh0, bh1);
-                mma_tf32(acc[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-                mma_tf32(acc[nt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                for (int nt = 0; nt < NT; ++nt) {
+                    // B[s][k] = X[s0 + s][8 nt + k]: (q, g), (q + 4, g)
+                    uint32_t bh0, bl0, bh1, bl1;
+                    split_tf32(x0[8 * nt + g], bh0, bl0);
+                    split_tf32(x1[8 * nt + g], bh1, bl1);
+                    mma_tf32(acc[nt], al[0], al[1], al[2], al[3], bh0, bh1);
+                    mma_tf32(acc[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                    mma_tf32(acc[nt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                }
+                mma_tf32(accb, al[0], al[1], al[2], al[3], one, one);
+                mma_tf32(accb, ah[0], ah[1], ah[2], ah[3], one, one);
             }
-            mma_tf32(accb, al[0], al[1], al[2], al[3], one, one);
-            mma_tf32(accb, ah[0], ah[1], ah[2], ah[3], one, one);
-        }
-        // D[o][k] fragments: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1)
+            // D[o][k] fragments: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1)
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int o = g + (i >= 2 ? 8 : 0), k = 8 * nt + 2 * q + (i & 1);
-                if (o < O && k < K) out[bW + o * K + k] = acc[nt][i];
+                for (int i = 0; i < 4; ++i) {
+                    const int o = g + (i >= 2 ? 8 : 0), k = 8 * nt + 2 * q + (i & 1);
+                    if (o < O && k < K) out[bW + o * K + k] = acc[nt][i];
+                }
+            if (q == 0) {
+                if (g < O) out[bb + g] = accb[0];
+                if (g + 8 < O) out[bb + g + 8] = accb[2];
             }
-        if (q == 0) {
-            if (g < O) out[bb + g] = accb[0];
-            if (g + 8 < O) out[bb + g + 8] = accb[2];
-        }
-    };
-    if constexpr (!kBF16) {
-        // six layers over the block's four warps: E1 + D2, E2 + D3, E3, D1
-        const int warp = t >> 5;
-        if (warp == 0) {
-            mma_grad(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1);
-            mma_grad(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2);
-        } else if (warp == 1) {
-            mma_grad(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2);
-            mma_grad(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3);
-        } else if (warp == 2) {
-            mma_grad(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3);
+        };
+        if constexpr (!kBF16) {
+            // six layers over the block's four warps: E1 + D2, E2 + D3, E3, D1
+            const int warp = t >> 5;
+            if (warp == 0) {
+                mma_grad(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1);
+                mma_grad(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2);
+            } else if (warp == 1) {
+                mma_grad(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2);
+                mma_grad(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3);
+            } else if (warp == 2) {
+                mma_grad(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3);
+            } else {
+                mma_grad(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1);
+            }
         } else {
-            mma_grad(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1);
-        }
-    } else {
-        for (int it = t; it < B6; it += kSamples) {
-            if (it < B1) tiles(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1, it);
-            else if (it < B2) tiles(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2, it - B1);
-            else if (it < B3) tiles(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3, it - B2);
-            else if (it < B4) tiles(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1, it - B3);
-            else if (it < B5) tiles(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2, it - B4);
-            else tiles(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3, it - B5);
+            for (int it = t; it < B6; it += kSamples) {
+                if (it < B1) tiles(W_{}, IE{}, S::DA1E, S::IN1E, S::E1, S::e1, it);
+                else if (it < B2) tiles(W_{}, W_{}, S::DA2E, S::H1E, S::E2, S::e2, it - B1);
+                else if (it < B3) tiles(L2{}, W_{}, S::DOE, S::H2E, S::E3, S::e3, it - B2);
+                else if (it < B4) tiles(W_{}, ID{}, S::DA1D, S::IN1D, S::D1, S::d1, it - B3);
+                else if (it < B5) tiles(W_{}, W_{}, S::DA2D, S::H1D, S::D2, S::d2, it - B4);
+                else tiles(P2{}, W_{}, S::DY, S::H2D, S::D3, S::d3, it - B5);
+            }
         }
     }
     if (t == 0) {
@@ -419,18 +424,19 @@ __global__ void __launch_bounds__(kSamples) fwd_bwd(const float* __restrict__ pr
     }
 }
 
-// grad[p] = sum over blocks of partial[blk][p]; loss3 = (rec + kl, rec, kl) / B.  A block handles 32 consecutive
+// grad[p] = sum over blocks of partial[blk][p]; loss3 = (rec + kl, rec, kl) / B.  Entries from p_begin on (np
+// for the loss terms alone).  A block handles 32 consecutive
 // entries (one per lane); its warp w adds rows w, w + 8, w + 16, ... in that order, and the eight warp sums are
 // then added in warp order, so the result does not depend on scheduling (bit-reproducible).
 constexpr int kReduceWarps = 8;
 
 __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials(const float* __restrict__ partial, int nblk,
                                                                      int np, uint64_t B, float* __restrict__ grad,
-                                                                     float* __restrict__ loss3)
+                                                                     float* __restrict__ loss3, int p_begin)
 {
     __shared__ float s_sum[kReduceWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int p = blockIdx.x * 32 + lane;
+    const int p = p_begin + blockIdx.x * 32 + lane;
     float acc = 0.0f;
     if (p < np + 2) {
 #pragma unroll 8
@@ -522,23 +528,25 @@ __global__ void bump_step(unsigned long long* step)
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1ull;
 }
 
+using LaunchFn = cudaError_t (*)(const float*, const float*, const float*, const float*, uint64_t, uint64_t, uint64_t,
+                                 float*, cudaStream_t);
 struct Plan {
     int np = 0;
-    cudaError_t (*launch)(const float*, const float*, const float*, const float*, uint64_t, uint64_t, uint64_t,
-                          float*, cudaStream_t) = nullptr;
+    LaunchFn launch = nullptr;       // forward and backward
+    LaunchFn launch_fwd = nullptr;   // the loss alone
 };
 
-template <int PI, int PO, int W, int L, bool kBF16>
+template <int PI, int PO, int W, int L, bool kBF16, bool kGrad>
 cudaError_t launch_fb(const float* prm, const float* X, const float* C, const float* E, uint64_t B, uint64_t seed,
                       uint64_t step, float* partial, cudaStream_t s)
 {
     using S = Shape<PI, PO, W, L>;
-    const size_t smem = ((size_t)S::NSLOT * S::SLOT + S::SW) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO, W, L, kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = ((kGrad ? (size_t)S::NSLOT * S::SLOT : 0) + S::SW) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fwd_bwd<PI, PO, W, L, kBF16, kGrad>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned nblk = (unsigned)((B + kSamples - 1) / kSamples);
-    fwd_bwd<PI, PO, W, L, kBF16><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
+    fwd_bwd<PI, PO, W, L, kBF16, kGrad><<<nblk, kSamples, smem, s>>>(prm, X, C, E, B, seed, step, partial);
     return cudaGetLastError();
 }
 
@@ -554,7 +562,10 @@ Plan plan_for(const ms_cvae_shape& sh)
 #define MS_CASE(pi, po, w, l)                                                                                  \
     if (sh.p_in == pi && sh.p_out == po && sh.width == w && sh.latent == l) {                                 \
         pl.np = Shape<pi, po, w, l>::NP;                                                                      \
-        pl.launch = sh.precision == MS_BF16 ? launch_fb<pi, po, w, l, true> : launch_fb<pi, po, w, l, false>; \
+        pl.launch = sh.precision == MS_BF16 ? launch_fb<pi, po, w, l, true, true>                             \
+                                            : launch_fb<pi, po, w, l, false, true>;                           \
+        pl.launch_fwd = sh.precision == MS_BF16 ? launch_fb<pi, po, w, l, true, false>                        \
+                                                : launch_fb<pi, po, w, l, false, false>;                      \
     }
     MS_TRAIN_SHAPES(MS_CASE)
 #undef MS_CASE
@@ -618,7 +629,30 @@ extern "C" ms_status ms_cvae_forward_backward(const ms_cvae_shape* s, const floa
     const int nblk = (int)((B + kSamples - 1) / kSamples);
     MS_CUDA(pl.launch(params, x, c, eps_z, B, seed, step, partial, cs));
     const int n = pl.np + 2;
-    reduce_partials<<<(n + 31) / 32, 32 * kReduceWarps, 0, cs>>>(partial, nblk, pl.np, B, grad, loss3);
+    reduce_partials<<<(n + 31) / 32, 32 * kReduceWarps, 0, cs>>>(partial, nblk, pl.np, B, grad, loss3, 0);
+    MS_CUDA(cudaGetLastError());
+    finish_loss<<<1, 32, 0, cs>>>(loss3);
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
+}
+
+extern "C" ms_status ms_cvae_forward(const ms_cvae_shape* s, const float* params, const float* x, const float* c,
+                                     const float* eps_z, uint64_t B, uint64_t seed, uint64_t step, float* loss3,
+                                     void* workspace, size_t workspace_bytes, void* stream)
+{
+    Plan pl;
+    ms_status st = check_shape(s, "ms_cvae_forward", &pl);
+    if (st != MS_OK) return st;
+    MS_CHECK_ARG(B >= 1 && B < (1ull << 32), "ms_cvae_forward: batch must be in [1, 2^32)");
+    MS_CHECK_ARG(params && x && c && loss3, "ms_cvae_forward: null params, x, c or loss3");
+    MS_CHECK_ARG(workspace && workspace_bytes >= ms_cvae_workspace_size(s, B),
+                 "ms_cvae_forward: workspace of at least %zu bytes required", ms_cvae_workspace_size(s, B));
+    MS_CHECK_ARG(((uintptr_t)workspace & 255u) == 0, "ms_cvae_forward: workspace must be 256-byte aligned");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    float* partial = static_cast<float*>(workspace);
+    const int nblk = (int)((B + kSamples - 1) / kSamples);
+    MS_CUDA(pl.launch_fwd(params, x, c, eps_z, B, seed, step, partial, cs));
+    reduce_partials<<<1, 32 * kReduceWarps, 0, cs>>>(partial, nblk, pl.np, B, nullptr, loss3, pl.np);
     MS_CUDA(cudaGetLastError());
     finish_loss<<<1, 32, 0, cs>>>(loss3);
     MS_CUDA(cudaGetLastError());

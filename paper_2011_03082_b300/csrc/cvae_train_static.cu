@@ -13,9 +13,15 @@
 // reads (partials are written in full before the reduction, the gradient before Adam), so nothing in the
 // array has to be cleared between calls.
 //
-// In host code the array's name is only a stand-in for its device address, so the address is looked up once
-// per device with cudaGetSymbolAddress, with that device current, on the first call made on it; make that
-// first call before any stream capture.
+// In host code the array's name is only a stand-in for its device address, so the address is looked up with
+// cudaGetSymbolAddress, with the device current, on the first call made on a device, and kept together with
+// the identity of the CUDA context it belongs to.  A later call in another context of that device (after
+// cudaDeviceReset, which destroys the primary context and with it the module's memory) looks it up again.
+// Context identities come from cuCtxGetId, which never reuses an identity within a process (the driver
+// functions are reached through cudaGetDriverEntryPointByVersion, so the library does not link libcuda).
+// Make the first call on a device, and the first one after a reset, before any stream capture.
+#include <cuda.h>   // driver API types only
+
 #include <mutex>
 
 #include "ms_device.cuh"
@@ -27,8 +33,41 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_train_scratch[kStaticScratchBytes];
 
+struct Resolved {
+    unsigned long long ctx_id;   // cuCtxGetId of the context the address belongs to (0: none yet)
+    void* addr;
+};
+
 std::mutex g_lock;
-void* g_scratch_addr[kMaxDevices] = {};
+Resolved g_scratch[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identity of the calling thread's current context, or 0 when there is none (or the driver cannot say).
+unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 cudaError_t scratch_address(void** out)
 {
@@ -37,13 +76,16 @@ cudaError_t scratch_address(void** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> guard(g_lock);
-    if (g_scratch_addr[dev] == nullptr) {
+    Resolved& r = g_scratch[dev];
+    const unsigned long long id = current_context_id();
+    if (r.addr == nullptr || id == 0 || id != r.ctx_id) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_train_scratch);
+        e = cudaGetSymbolAddress(&p, g_train_scratch);   // creates the device's primary context if needed
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        r.addr = p;
+        r.ctx_id = current_context_id();
     }
-    *out = g_scratch_addr[dev];
+    *out = r.addr;
     return cudaSuccess;
 }
 

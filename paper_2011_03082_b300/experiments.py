@@ -46,14 +46,24 @@ def _render(p: dict, cset, variant=0):
     return img.cpu().numpy() / p["spp"], a.elapsed_time(b) / 1e3
 
 
-def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=256, cset=None, variant=0):
+def reference_images(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, variant=0, cset=None) -> dict:
+    """Brute-force reference images (seed 101) per density: {sigma_t: per-pixel mean image}."""
+    return {s: _render(synth.render_scene(s, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101), cset,
+                       variant)[0] for s in sigmas}
+
+
+def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=256, cset=None, variant=0, refs=None,
+               tau_min=1.0):
+    """``refs``: reference images from ``reference_images`` at the same res and ref_spp (rendered here when None).
+    ``tau_min``: the sphere tracer's minimum optical radius (0: the library's per-density default)."""
     if cset is None:
         cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
     out = []
     for s in sigmas:
         base = synth.render_scene(s, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101)
-        ref, _ = _render(base, cset, variant)
-        st_img, t_st = _render(dict(base, mode=ms.MS_SPHERE, spp=st_spp, seed=202), cset, variant)
+        ref = refs[s] if refs is not None else _render(base, cset, variant)[0]
+        st_img, t_st = _render(dict(base, mode=ms.MS_SPHERE, spp=st_spp, seed=202, min_optical_radius=tau_min),
+                               cset, variant)
         rmse_st = float(np.sqrt(np.mean((st_img - ref) ** 2)))
         ladder = []
         spp = 16
@@ -74,27 +84,29 @@ def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=2
             spp_eq = float(np.sqrt(s0 * (e0 / rmse_st) ** 2 * s1 * (e1 / rmse_st) ** 2))
             note = "interpolated"
         t_bf = per_spp_bf * spp_eq
-        out.append(dict(sigma_t=s, res=res, ref_spp=ref_spp, st_spp=st_spp, rmse_st=rmse_st, spp_bf_equal=spp_eq,
-                        t_st_s=t_st, t_bf_equal_s=t_bf, speedup=t_bf / t_st, note=note,
+        out.append(dict(sigma_t=s, res=res, ref_spp=ref_spp, st_spp=st_spp, tau_min=tau_min, rmse_st=rmse_st,
+                        spp_bf_equal=spp_eq, t_st_s=t_st, t_bf_equal_s=t_bf, speedup=t_bf / t_st, note=note,
                         ladder=[dict(spp=a, rmse=b, t_s=c) for a, b, c in ladder]))
     return out
 
 
-def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None):
+def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None, sequential=True, tune_div=64):
     """The heterogeneous batch: ``n`` requests (resolution, spp, density, g, albedo, displacement frequency
-    drawn with ``seed``; ``scale`` shrinks resolution and spp) in one persistent launch, autotuned, captured in
-    a CUDA graph and replayed; reports light paths per second, per-request completion p50 / p99 and the time
-    of the same requests rendered one launch at a time."""
+    drawn with ``seed``; ``scale`` shrinks resolution and spp) in one persistent launch, the renderer variant
+    autotuned on the same requests at 1/``tune_div`` of their spp, captured in a CUDA graph and replayed; reports
+    light paths per second, per-request completion p50 / p99 (ns counters written by the kernel when each
+    request's last path ends) and, with ``sequential``, the time of the same requests rendered one launch at a
+    time."""
     if cset is None:
         cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
-    reqs = [ms.render_params(r) for r in synth.batch_requests(seed, n, scale=scale)]
+    raw = synth.batch_requests(seed, n, scale=scale)
+    reqs = [ms.render_params(r) for r in raw]
     npx = sum(r.width * r.height for r in reqs)
     paths = sum(r.width * r.height * r.spp for r in reqs)
     imgs = torch.zeros(npx, dtype=torch.float64, device="cuda")
     st = torch.zeros(n, ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
     ws = ms.workspace(ms.ms_render_workspace_size(reqs))
-    tune = [ms.render_params(dict(synth.batch_requests(seed, n, scale=scale)[i], spp=max(1, reqs[i].spp // 16)))
-            for i in range(n)]
+    tune = [ms.render_params(dict(raw[i], spp=max(1, reqs[i].spp // tune_div))) for i in range(n)]
     variant, _ = ms.ms_render_autotune(tune, cset, imgs, st, ws=ws)
     for r in reqs:
         r.variant = variant
@@ -117,19 +129,21 @@ def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None):
         b.synchronize()
         times.append(a.elapsed_time(b) / 1e3)
     done_ms = st[:, 10].double().cpu().numpy() / 1e6
-    # the same requests, one launch each
-    one = torch.zeros(max(r.width * r.height for r in reqs), dtype=torch.float64, device="cuda")
-    ost = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for r in reqs:
-        ms.ms_render(r, cset, one, ost, ws=ws)
-    b.record()
-    b.synchronize()
     t = float(np.median(times))
-    return dict(requests=n, scale=scale, paths=paths, seconds=t, paths_per_s=paths / t, variant=variant,
-                p50_ms=float(np.percentile(done_ms, 50)), p99_ms=float(np.percentile(done_ms, 99)),
-                sequential_seconds=a.elapsed_time(b) / 1e3)
+    out = dict(requests=n, scale=scale, paths=paths, seconds=t, paths_per_s=paths / t, variant=variant,
+               p50_ms=float(np.percentile(done_ms, 50)), p99_ms=float(np.percentile(done_ms, 99)),
+               launch="one persistent ms_render_batch launch, replayed from a CUDA graph (memsets + kernel)")
+    if sequential:
+        one = torch.zeros(max(r.width * r.height for r in reqs), dtype=torch.float64, device="cuda")
+        ost = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for r in reqs:
+            ms.ms_render(r, cset, one, ost, ws=ws)
+        b.record()
+        b.synchronize()
+        out["sequential_seconds"] = a.elapsed_time(b) / 1e3
+    return out
 
 
 def _render_batch(reqs: list, cset, variant=0):
@@ -172,18 +186,37 @@ def absorption_sweep(sigma=64.0, res=256, spp=64, settings=6, cset=None, variant
 
 
 def fallback_sweep(sigma=64.0, res=128, spp=256, ref_spp=8192, tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None,
-                   variant=0):
-    """Render time and RMSE against a brute-force reference for several minimum optical radii of a sphere step."""
+                   variant=0, ref=None):
+    """Render time and RMSE against a brute-force reference for several minimum optical radii of a sphere step;
+    ``ref``: the reference image (rendered here when None).  Each row's ``cost`` = time x RMSE^2, the work
+    needed per unit of inverse squared error (lower is better)."""
     if cset is None:
         cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
     base = synth.render_scene(sigma, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101)
-    ref, _ = _render(base, cset, variant)
+    if ref is None:
+        ref, _ = _render(base, cset, variant)
     out = []
     for tm in tau_mins:
         img, t = _render(dict(base, mode=ms.MS_SPHERE, spp=spp, seed=202, min_optical_radius=tm), cset, variant)
-        out.append(dict(tau_min=tm, seconds=t, rmse=float(np.sqrt(np.mean((img - ref) ** 2)))))
+        e = float(np.sqrt(np.mean((img - ref) ** 2)))
+        out.append(dict(tau_min=tm, seconds=t, rmse=e, cost=t * e * e))
     bf, t_bf = _render(dict(base, spp=spp, seed=303), cset, variant)
-    out.append(dict(tau_min=None, mode="brute force", seconds=t_bf, rmse=float(np.sqrt(np.mean((bf - ref) ** 2)))))
+    e = float(np.sqrt(np.mean((bf - ref) ** 2)))
+    out.append(dict(tau_min=None, mode="brute force", seconds=t_bf, rmse=e, cost=t_bf * e * e))
+    return out
+
+
+def fallback_policy(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, spp=256, ref_spp=8192,
+                    tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None, variant=0, refs=None):
+    """The thin-region threshold per density (Sec. 6): for each density the sweep above, and the minimum optical
+    radius with the lowest cost (time x RMSE^2 against the brute-force reference at the same spp); beside it,
+    what the library's per-density default (min_optical_radius = 0) picks."""
+    out = []
+    for s in sigmas:
+        rows = fallback_sweep(s, res, spp, ref_spp, tau_mins, cset, variant, None if refs is None else refs[s])
+        best = min((r for r in rows if r["tau_min"] is not None), key=lambda r: r["cost"])
+        out.append(dict(sigma_t=s, best_tau_min=best["tau_min"],
+                        library_default=float(ms.lib().ms_render_default_min_optical_radius(s)), sweep=rows))
     return out
 
 
@@ -197,6 +230,7 @@ def main(argv=None):
     ap.add_argument("--scale", type=float, default=0.25)
     ap.add_argument("--absorption", action="store_true", help="run the absorption sweep instead")
     ap.add_argument("--fallback", action="store_true", help="run the fallback-threshold sweep instead")
+    ap.add_argument("--policy", action="store_true", help="the fallback-threshold sweep at every density")
     a = ap.parse_args(argv)
     if a.batched:
         print(json.dumps(batched(scale=a.scale)))
@@ -207,6 +241,11 @@ def main(argv=None):
         return
     if a.fallback:
         for r in fallback_sweep():
+            print(json.dumps(r))
+        return
+    if a.policy:
+        sigmas = tuple(float(v) for v in a.sigmas.split(","))
+        for r in fallback_policy(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, spp=a.st_spp):
             print(json.dumps(r))
         return
     sigmas = tuple(float(v) for v in a.sigmas.split(","))

@@ -23,11 +23,13 @@ MS_RENDER_STATS = 16
 
 # the C ABI's exported symbols (checked by the tests against include/ms.h)
 EXPORTS = ("ms_last_error", "ms_version", "ms_walk_workspace_size", "ms_simulate_walks", "ms_cvae_infer",
-           "ms_cvae_num_params", "ms_cvae_workspace_size", "ms_cvae_forward_backward", "ms_adam_step",
-           "ms_cvae_train_step", "ms_cvae_train_step_dev_workspace_size", "ms_cvae_train_step_dev",
-           "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records", "ms_render_workspace_size", "ms_render",
-           "ms_render_batch", "ms_render_variants", "ms_render_variant_info", "ms_render_autotune",
-           "ms_sdf_grid_workspace_size", "ms_sdf_grid_build")
+           "ms_cvae_num_params", "ms_cvae_workspace_size", "ms_cvae_forward", "ms_cvae_forward_backward",
+           "ms_adam_step", "ms_cvae_train_step", "ms_cvae_train_step_dev_workspace_size", "ms_cvae_train_step_dev",
+           "ms_cvae_static_scratch_bytes", "ms_cvae_train_step_static", "ms_training_records",
+           "ms_render_workspace_size", "ms_render", "ms_render_batch", "ms_render_default_min_optical_radius",
+           "ms_render_variants", "ms_render_variant_info", "ms_render_autotune", "ms_sdf_grid_workspace_size",
+           "ms_sdf_grid_build", "ms_alu_peaks_scratch_bytes", "ms_alu_peaks")
+PEAK_NAMES = ("ffma", "ex2", "lg2", "sin", "rsqrt", "imad", "lop3", "imulhi")
 
 
 class MsError(RuntimeError):
@@ -100,6 +102,7 @@ def lib():
         "ms_cvae_infer": ([P, P, P, U64, U64, U64, P, P, P], C.c_int),
         "ms_cvae_num_params": ([P], C.c_size_t),
         "ms_cvae_workspace_size": ([P, U64], C.c_size_t),
+        "ms_cvae_forward": ([P, P, P, P, P, U64, U64, U64, P, P, C.c_size_t, P], C.c_int),
         "ms_cvae_forward_backward": ([P, P, P, P, P, U64, U64, U64, P, P, P, C.c_size_t, P], C.c_int),
         "ms_adam_step": ([P, P, P, P, U64, U64, F, F, F, F, F, P], C.c_int),
         "ms_cvae_train_step": ([P, P, P, P, P, P, P, U64, U64, U64, F, F, P, P, C.c_size_t, P], C.c_int),
@@ -113,9 +116,12 @@ def lib():
         "ms_sdf_grid_build": ([C.c_float, C.c_float, I32, P, P, C.c_size_t, P], C.c_int),
         "ms_render": ([P, P, P, P, P, C.c_size_t, P], C.c_int),
         "ms_render_batch": ([P, C.c_int, P, P, P, P, C.c_size_t, P], C.c_int),
+        "ms_render_default_min_optical_radius": ([C.c_float], C.c_float),
         "ms_render_variants": ([], C.c_int),
         "ms_render_variant_info": ([C.c_int, P, P, P, P], C.c_int),
         "ms_render_autotune": ([P, C.c_int, P, P, P, P, C.c_size_t, C.c_int, P, P, P], C.c_int),
+        "ms_alu_peaks_scratch_bytes": ([], C.c_size_t),
+        "ms_alu_peaks": ([P, P, C.c_size_t, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         if not hasattr(L, name):
@@ -224,6 +230,13 @@ def ms_cvae_forward_backward(shape, params, x, c, B, *, eps_z=None, seed=1, step
     return _check(lib().ms_cvae_forward_backward(C.byref(shape), _ptr(params), _ptr(x), _ptr(c), _ptr(eps_z), B, seed,
                                                  step, _ptr(grad), _ptr(loss3), _ptr(ws), ws.numel(),
                                                  _stream(stream)), "ms_cvae_forward_backward")
+
+
+def ms_cvae_forward(shape, params, x, c, B, *, eps_z=None, seed=1, step=0, loss3=None, ws=None, stream=None):
+    if ws is None:
+        ws = workspace(ms_cvae_workspace_size(shape, B), params.device)
+    return _check(lib().ms_cvae_forward(C.byref(shape), _ptr(params), _ptr(x), _ptr(c), _ptr(eps_z), B, seed, step,
+                                        _ptr(loss3), _ptr(ws), ws.numel(), _stream(stream)), "ms_cvae_forward")
 
 
 def ms_adam_step(params, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
@@ -348,3 +361,15 @@ def ms_render_variant_info(i):
     vals = [C.c_int() for _ in range(4)]
     _check(lib().ms_render_variant_info(i, *[C.byref(v) for v in vals]), "ms_render_variant_info")
     return dict(zip(("decode_batch", "trans_batch", "steps", "min_blocks"), (v.value for v in vals)))
+
+
+# ------------------------------------------------------------------------------------------------ peaks
+
+def ms_alu_peaks(device=None, stream=None) -> dict:
+    """Measured whole-GPU issue rates (operations per second) of FFMA, the special-function unit (ex2, lg2, sin,
+    rsqrt) and integer multiply-add, logic and high multiply; waits for the stream."""
+    n = int(lib().ms_alu_peaks_scratch_bytes())
+    ws = workspace(n, device)
+    out = (C.c_double * len(PEAK_NAMES))()
+    _check(lib().ms_alu_peaks(out, _ptr(ws), ws.numel(), _stream(stream)), "ms_alu_peaks")
+    return dict(zip(PEAK_NAMES, list(out)))

@@ -11,7 +11,7 @@
 3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder), each
    model's shape (p_in, p_out, latent, width: the final settings of Table 1) and the training log.
 
-Run as ``python -m paper_2011_03082_b300.pipeline [--walks N] [--steps S] [--out PATH]``.
+Run as ``python -m paper_2011_03082_b300.pipeline [--walks N] [--steps S] [--out PATH] [--precision bf16]``.
 """
 from __future__ import annotations
 
@@ -46,11 +46,12 @@ def generate_records(n_walks: int, seed: int = 1, device="cuda") -> dict:
 
 
 def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch: int, lr: float, seed: int,
-              log_every: int = 100):
+              log_every: int = 100, precision: int = ms.MS_FP32):
     """Train one CVAE: one training step (device-side batch sampling, forward, backward, deterministic
-    reduction, Adam with its step counter on the device) is captured in a CUDA graph and replayed."""
+    reduction, Adam with its step counter on the device) is captured in a CUDA graph and replayed.
+    ``precision``: MS_FP32, or MS_BF16 (BF16 products with FP32 accumulation and FP32 master weights)."""
     p_in, p_out, latent, width = synth.MODEL_SHAPES[name]
-    shape = ms.cvae_shape(p_in, p_out, latent, width)
+    shape = ms.cvae_shape(p_in, p_out, latent, width, precision=precision)
     dev = c.device
     params = torch.from_numpy(synth.xavier_cvae(seed, p_in, p_out, latent, width)).to(dev)
     m = torch.zeros_like(params)
@@ -75,12 +76,13 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
     return params, log
 
 
-def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every=100) -> dict:
+def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every=100,
+          precision: int = ms.MS_FP32) -> dict:
     models = {}
     for i, name in enumerate(MODELS):
         ck, xk = RECORD_KEYS[name]
         params, log = train_one(name, records[ck], records[xk], steps=steps, batch=batch, lr=lr,
-                                seed=seed + 17 * i, log_every=log_every)
+                                seed=seed + 17 * i, log_every=log_every, precision=precision)
         models[name] = dict(params=params.cpu().numpy(), log=log)
     return models
 
@@ -136,17 +138,21 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default=str(DEFAULT_WEIGHTS))
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
+                    help="training arithmetic (bf16: BF16 products, FP32 accumulation and master weights)")
     a = ap.parse_args(argv)
+    prec = ms.MS_BF16 if a.precision == "bf16" else ms.MS_FP32
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     recs = generate_records(a.walks, a.seed)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed)
+    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=prec)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     c = recs["counters"].cpu().tolist()
-    meta = dict(walks=a.walks, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, walk_seconds=t1 - t0,
+    meta = dict(walks=a.walks, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=a.precision,
+                walk_seconds=t1 - t0,
                 train_seconds=t2 - t1, walk_counters=c,
                 final_loss={k: v["log"][-1][1] for k, v in models.items()})
     save(a.out, models, meta)

@@ -9,6 +9,9 @@
   brute     the same render in brute-force mode
   render512 / brute512   512x512 px x 64 spp at sigma_t 128 (sphere tracing / brute force)
   render512g             render512 with sphere radii also from a 128^3 voxel grid of conservative distances
+  batch128 / batch256    the benchmark's launch (one ms_render_batch of sigma_t 16, 32, 64, 128, trained
+                         decoders) at 128x128 or 256x256 px x 16 spp: small cases of the benchmark launch for
+                         multi-pass ncu captures (DRAM bytes per launch scale with the images' pixels)
 Each case runs ``--repeat`` times (default 2) and prints the CUDA-event time of the last run.
 """
 from __future__ import annotations
@@ -82,12 +85,31 @@ def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0, grid_n=0):
     return run
 
 
+def case_batch(res, spp=16, sigmas=(16.0, 32.0, 64.0, 128.0)):
+    """The benchmark's four-density batch at a reduced size, default renderer variant."""
+    models = pipeline.load()
+    cset = ms.cvae_set(pipeline.device_decoders(models))
+    reqs = [ms.render_params(synth.render_scene(s, width=res, height=res, spp=spp, mode=ms.MS_SPHERE))
+            for s in sigmas]
+    img = torch.zeros(len(reqs) * res * res, dtype=torch.float64, device="cuda")
+    st = torch.zeros(len(reqs), ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+    ws = ms.workspace(ms.ms_render_workspace_size(reqs))
+
+    def run():
+        img.zero_()
+        st.zero_()
+        ms.ms_render_batch(reqs, cset, img, st, ws=ws)
+    run.stats = st
+    return run
+
+
 CASES = {"walk": case_walk, "walk24": case_walk24, "decoder": case_decoder, "train": case_train,
          "decoder16": lambda: case_decoder(precision=ms.MS_FP16),
          "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE),
          "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
          "render512g": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0, grid_n=128),
-         "brute512": lambda: case_render(ms.MS_BRUTE, 512, 64, 128.0)}
+         "brute512": lambda: case_render(ms.MS_BRUTE, 512, 64, 128.0),
+         "batch128": lambda: case_batch(128), "batch256": lambda: case_batch(256)}
 
 
 def main(argv=None):

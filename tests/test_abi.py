@@ -31,3 +31,16 @@ def test_host_only_queries():
     shape = ms.cvae_shape(7, 6)
     assert ms.ms_cvae_num_params(shape) == (16 * 13 + 16 + 256 + 16 + 8 * 16 + 8) + (16 * 11 + 16 + 256 + 16 + 12 * 16 + 12)
     assert ms.ms_cvae_workspace_size(shape, 65536) > 0
+
+
+def test_fallback_policy_is_a_host_function_of_the_density():
+    """The per-density thin-region threshold (ms_render_default_min_optical_radius) is positive, held constant
+    beyond the measured densities, and between two neighbouring knots lies between their values."""
+    f = lambda s: float(ms.lib().ms_render_default_min_optical_radius(s))
+    knots = [16.0, 32.0, 64.0, 128.0]
+    vals = [f(s) for s in knots]
+    assert all(v > 0 for v in vals)
+    assert f(1.0) == vals[0] and f(1e6) == vals[-1]
+    for (a, va), (b, vb) in zip(zip(knots, vals), zip(knots[1:], vals[1:])):
+        mid = f((a * b) ** 0.5)
+        assert min(va, vb) - 1e-6 <= mid <= max(va, vb) + 1e-6
