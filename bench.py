@@ -416,7 +416,7 @@ def main(argv=None):
                            "image_rms": float(torch.sqrt(torch.mean(img_fp32.double() ** 2)).item()) / spp}
 
     # ---------------- equal-RMSE comparison with brute force and the fallback policy (after the timed region) --
-    equal = policy = batch = None
+    equal = policy = batch = breakdown = None
     if rank == 0 and world == 1 and not args.no_equal_rmse:
         from paper_2011_03082_b300 import experiments
         refs = experiments.reference_images(SIGMAS, args.eq_res, args.eq_ref_spp, variant, cset)
@@ -437,6 +437,7 @@ def main(argv=None):
                    "library_default": r["library_default"],
                    "sweep": [{k: v for k, v in x.items() if k != "mode"} for x in r["sweep"]]} for r in pol]
         del refs
+        breakdown = experiments.time_breakdown((64.0, 128.0), res=W, spp=64, cset=cset)
     if rank == 0 and world == 1 and not args.no_batched:
         from paper_2011_03082_b300 import experiments
         b = experiments.batched(seed=5, n=64, scale=args.batch_scale, repeats=1, cset=cset, sequential=False)
@@ -460,7 +461,7 @@ def main(argv=None):
                            "autotune_ms": [round(t, 2) for t in variant_ms]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clocks, "entering_paths_per_s": entering, "brute_force": brute,
-                "decoder_precision": precision, "equal_rmse": equal,
+                "decoder_precision": precision, "equal_rmse": equal, "time_breakdown": breakdown,
                 "fallback_policy": policy, "batched_64": batch, "step_ms": step_ms}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -266,6 +266,11 @@ typedef struct {
     const float* sdf_grid;      /* NULL, or device [n][n][n] from ms_sdf_grid_build(disp_amp, disp_freq, n):
                                    a sphere step's radius is then the larger of the distance bound and
                                    the value of the grid voxel holding the collision point             */
+    int32_t phase_timers;       /* 0 normally.  1 (first request of a launch): run an instrumented kernel
+                                   of the default variant that also counts shadow-ray march steps in
+                                   stats[11] and adds each warp's clock cycles by round kind to the first
+                                   request's stats[12..15] (march, decoder, transition, refill) — a time
+                                   breakdown; FP32 decoders only; slightly slower                       */
 } ms_render_params;
 
 /* The voxel grid of conservative distances that sizes sphere steps (Sec. 3: the bounding volume is voxelised
@@ -310,7 +315,9 @@ float ms_render_default_min_optical_radius(float sigma_t);
  * [3] sphere steps, [4] brute-force events, [5] absorbed, [6] truncated paths or dropped estimates,
  * [7] next-event estimates, [8] SDF evaluations (march steps, each with f's derivative along the ray, and
  * sphere radii at collisions), [9] march steps in the boundary band, [10] completion time
- * of the request in ns after the launch's first block started (written, not accumulated), [11..15] zero.
+ * of the request in ns after the launch's first block started (written, not accumulated), [11..15] zero
+ * (with phase_timers: [11] shadow-ray march steps, [12..15] of the first request the warps' cycles in march,
+ * decoder, transition and refill rounds).
  * models: host struct with device weight pointers (ignored in MS_BRUTE).  workspace:
  * ms_render_workspace_size() bytes (sample ticket, start time, finished-path counters).  One persistent
  * launch; asynchronous; capturable in a CUDA graph (a memset and a kernel). */

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict
     __shared__ __align__(16) unsigned char wsm[mmadec::smem_bytes(8, NTH)];
     __shared__ float stage[kMmaThreads / 32][mmadec::kStageFloats];
     __shared__ float rows[kMmaThreads][41];   // [0,16) inputs, [16,24) eps, [24,40) outputs
-    mmadec::stage_weights<kBF16, NTH>(wsm, wts, p_in + latent, p_out);
+    mmadec::stage_weights<kBF16, NTH, kSplit == 3>(wsm, wts, p_in + latent, p_out);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* my = rows[threadIdx.x];
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma_fixed(const float* __re
     constexpr int NT3 = mmadec::n_tiles_out(P);
     __shared__ __align__(16) unsigned char wsm[mmadec::smem_bytes(P, NTH)];
     __shared__ float stage[kMmaThreads / 32][mmadec::kStageFloats];
-    mmadec::stage_weights<kBF16, NTH>(wsm, wts, PI + L, P);
+    mmadec::stage_weights<kBF16, NTH, kSplit == 3>(wsm, wts, PI + L, P);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t n_chunks = (n + 31) / 32;

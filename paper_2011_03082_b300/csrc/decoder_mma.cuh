@@ -15,6 +15,18 @@
 // kSplit = 2 splits the activations only (inputs and hidden layers carried as head + tail, weights rounded
 // once to half precision), so the error is that of the rounded weights; kSplit = 1 is plain half precision.
 // Half is FP16 (kBF16 = false) or BF16.  Accumulation is FP32 throughout.
+//
+// Softplus in base 2: every decoder evaluates its hidden layers on pre-activations scaled by log2(e),
+// a' = a log2(e), where sp(a) = ln(2) sp2(a') with sp2(a') = max(a', 0) + log2(1 + 2^-|a'|): each hidden unit
+// then costs 2^x, log2 and three additions, without the two scalings that sp(a) = max(a, 0) + ln(1 + e^-|a|)
+// needs on the special-function unit.  The scalings are folded in where they cost nothing: the first two
+// layers' biases are staged times log2(e); the first hidden layer's ln(2) cancels the second layer's log2(e),
+// so the second layer's weights stay as they are.  The first layer's log2(e) and the last hidden layer's ln(2)
+// are folded into the first and third layers' weights with kSplit = 3 (weights split into head and tail, so
+// the scaled weights are exact to about 22 bits); with the half-precision weights of kSplit <= 2 the scaled
+// weights would round differently from the weights themselves, so there the input row is multiplied by
+// log2(e) before it is split and the last hidden layer's outputs by ln(2) (FP32 values, carried as head and
+// tail).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -89,10 +101,16 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint3
 // Block-wide: packed float weights W1[w][k_in] b1 W2[w][w] b2 W3[2p][w] b3 (w = 8 NTH) -> fragment layout at
 // `dst`.  For 8-column tile j and lane (g = lane / 4, t = lane % 4) the B operand holds rows k = 2t, 2t+1 (b0)
 // and 2t+8, 2t+9 (b1) of column n = 8j + g, i.e. W[n][k] (zero for k >= K); stored as
-// {b0 head, b1 head, b0 tail, b1 tail}.
-template <bool kBF16, int NTH = 2>
+// {b0 head, b1 head, b0 tail, b1 tail}.  The scalings of the base-2 Softplus (see above): biases of the first
+// two layers times log2(e) always; with kScaleW (kSplit = 3) also the first layer's weights times log2(e) and
+// the third layer's times ln(2).
+constexpr float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+
+template <bool kBF16, int NTH = 2, bool kScaleW = false>
 __device__ void stage_weights(unsigned char* dst, const float* __restrict__ g, int k_in, int p_out)
 {
+    const float wscale[3] = {kScaleW ? kLog2e : 1.0f, 1.0f, kScaleW ? kLn2 : 1.0f};
+    const float bscale[3] = {kLog2e, kLog2e, 1.0f};
     constexpr int w = 8 * NTH;
     const int nt3 = n_tiles_out(p_out);
     uint4* frag = reinterpret_cast<uint4*>(dst);
@@ -109,7 +127,7 @@ __device__ void stage_weights(unsigned char* dst, const float* __restrict__ g, i
         const int j = tile - T0[layer];
         const int n = 8 * j + (lane >> 2), t = lane & 3;
         auto w = [&](int k) -> float {
-            return (n < N[layer] && k < K[layer]) ? W[layer][n * K[layer] + k] : 0.0f;
+            return (n < N[layer] && k < K[layer]) ? wscale[layer] * W[layer][n * K[layer] + k] : 0.0f;
         };
         float v[4] = {w(2 * t), w(2 * t + 1), w(2 * t + 8), w(2 * t + 9)};
         uint32_t h0, l0, h1, l1;
@@ -124,8 +142,8 @@ __device__ void stage_weights(unsigned char* dst, const float* __restrict__ g, i
         frag[e] = make_uint4(h0, h1, l0, l1);
     }
     for (int e = threadIdx.x; e < 2 * w + 8 * nt3; e += blockDim.x) {
-        if (e < w) bias[e] = Bv[0][e];
-        else if (e < 2 * w) bias[e] = Bv[1][e - w];
+        if (e < w) bias[e] = bscale[0] * Bv[0][e];
+        else if (e < 2 * w) bias[e] = bscale[1] * Bv[1][e - w];
         else bias[e] = (e - 2 * w) < 2 * p_out ? Bv[2][e - 2 * w] : 0.0f;
     }
 }
@@ -151,19 +169,30 @@ __device__ __forceinline__ void layer(const uint32_t (&ah)[MT][4], const uint32_
     }
 }
 
-// Softplus of an 8 NTH-wide hidden layer, re-packed as the next layer's A fragments (head and tail); with
-// NTH = 1 the upper k half (columns 8..15) is zero.
-template <int kSplit, bool kBF16, int NTH = 2, int MT = 2>
+// sp2(a) = max(a, 0) + log2(1 + 2^-|a|): Softplus in base 2 on the special-function unit's 2^x and log2.
+__device__ __forceinline__ float softplus2(float a)
+{
+    float e, l;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-fabsf(a)));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.0f + e));
+    return fmaxf(a, 0.0f) + l;
+}
+
+// Softplus (base 2, on the scaled pre-activations) of an 8 NTH-wide hidden layer, re-packed as the next
+// layer's A fragments (head and tail); with NTH = 1 the upper k half (columns 8..15) is zero.  kOutScale: the
+// last hidden layer with half-precision weights, whose outputs are multiplied by ln(2) (see above).
+template <int kSplit, bool kBF16, int NTH = 2, int MT = 2, bool kOutScale = false>
 __device__ __forceinline__ void hidden_to_a(const float (&acc)[MT][NTH][4], uint32_t (&ah)[MT][4],
                                             uint32_t (&al)[MT][4])
 {
+    auto sp = [](float a) -> float { return kOutScale ? kLn2 * softplus2(a) : softplus2(a); };
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt) {
         float s[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            s[i] = softplus(acc[mt][0][i]);
-            s[4 + i] = NTH == 2 ? softplus(acc[mt][NTH - 1][i]) : 0.0f;
+            s[i] = sp(acc[mt][0][i]);
+            s[4 + i] = NTH == 2 ? sp(acc[mt][NTH - 1][i]) : 0.0f;
         }
         if (kSplit >= 2) {
             split2<kBF16>(s[0], s[1], ah[mt][0], al[mt][0]);
@@ -188,8 +217,9 @@ __device__ __forceinline__ void warp_mlp(const unsigned char* __restrict__ wsm, 
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint4* frag = reinterpret_cast<const uint4*>(wsm);
     const float* bias = reinterpret_cast<const float*>(wsm + (2 * NTH + NT3) * 32 * 16);
+    constexpr float kIn = kSplit == 3 ? 1.0f : kLog2e;     // the first layer's log2(e), on the input row
 #pragma unroll
-    for (int j = 0; j < 16; ++j) stage[lane * kStageStride + j] = x[j];
+    for (int j = 0; j < 16; ++j) stage[lane * kStageStride + j] = kIn * x[j];
     __syncwarp();
     uint32_t ah[2][4], al[2][4];
 #pragma unroll
@@ -206,7 +236,7 @@ __device__ __forceinline__ void warp_mlp(const unsigned char* __restrict__ wsm, 
     layer<NTH, kSplit, kBF16>(ah, al, frag, bias, lane, h);
     hidden_to_a<kSplit, kBF16, NTH>(h, ah, al);
     layer<NTH, kSplit, kBF16>(ah, al, frag + NTH * 32, bias + 8 * NTH, lane, h);
-    hidden_to_a<kSplit, kBF16, NTH>(h, ah, al);
+    hidden_to_a<kSplit, kBF16, NTH, 2, kSplit != 3>(h, ah, al);
     float o[2][NT3][4];
     layer<NT3, kSplit, kBF16>(ah, al, frag + 2 * NTH * 32, bias + 16 * NTH, lane, o);
 #pragma unroll
@@ -241,9 +271,10 @@ __device__ __forceinline__ void warp_mlp_rows16(const unsigned char* __restrict_
     const uint4* frag = reinterpret_cast<const uint4*>(wsm);
     const float* bias = reinterpret_cast<const float*>(wsm + (2 * NTH + NT3) * 32 * 16);
     constexpr int kCols = KIN <= 8 ? 8 : 16;
+    constexpr float kIn = kSplit == 3 ? 1.0f : kLog2e;     // the first layer's log2(e), on the input row
     if (active) {
 #pragma unroll
-        for (int j = 0; j < kCols; ++j) stage[row * kStageStride + j] = x[j];
+        for (int j = 0; j < kCols; ++j) stage[row * kStageStride + j] = kIn * x[j];
     }
     __syncwarp();
     uint32_t ah[1][4], al[1][4];
@@ -264,7 +295,7 @@ __device__ __forceinline__ void warp_mlp_rows16(const unsigned char* __restrict_
     layer<NTH, kSplit, kBF16, 1>(ah, al, frag, bias, lane, h);
     hidden_to_a<kSplit, kBF16, NTH, 1>(h, ah, al);
     layer<NTH, kSplit, kBF16, 1>(ah, al, frag + NTH * 32, bias + 8 * NTH, lane, h);
-    hidden_to_a<kSplit, kBF16, NTH, 1>(h, ah, al);
+    hidden_to_a<kSplit, kBF16, NTH, 1, kSplit != 3>(h, ah, al);
     float o[1][NT3][4];
     layer<NT3, kSplit, kBF16, 1>(ah, al, frag + 2 * NTH * 32, bias + 16 * NTH, lane, o);
 #pragma unroll

@@ -17,6 +17,9 @@ struct Variant {
             s, m},
 static const Variant kVariants[] = {MS_RENDER_VARIANTS(MS_RENDER_ENTRY)};
 #undef MS_RENDER_ENTRY
+// The instrumented instantiations (phase timers) of the default variant.
+static const void* const kTimedFP32 = (const void*)render_kernel<10, 12, 24, 3, kDecFP32, true>;
+static const void* const kTimedBrute = (const void*)render_kernel<10, 12, 24, 3, kDecNone, true>;
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
 static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const char* fn)
@@ -140,7 +143,13 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
     MS_CUDA(cudaMemsetAsync(workspace, 0, (2 + kMaxReq) * sizeof(unsigned long long), s));
     MS_CUDA(cudaMemsetAsync(b.t_start, 0xff, sizeof(unsigned long long), s));
     const Variant& v = kVariants[reqs[0].variant];
-    const void* kfn = !any_sphere ? v.fn_brute
+    if (reqs[0].phase_timers) {
+        MS_CHECK_ARG(!any_sphere || precision == MS_FP32, "%s: phase timers need FP32 decoders", fn);
+        MS_CHECK_ARG(kVariants[0].decode_batch == 10 && kVariants[0].trans_batch == 12 && kVariants[0].steps == 24,
+                     "%s: the instrumented kernel is not the default variant's", fn);
+    }
+    const void* kfn = reqs[0].phase_timers ? (any_sphere ? kTimedFP32 : kTimedBrute)
+                      : !any_sphere ? v.fn_brute
                       : precision == MS_FP16 ? variant_kernel_fp16(reqs[0].variant)
                       : precision == MS_BF16 ? variant_kernel_bf16(reqs[0].variant)
                                               : v.fn;

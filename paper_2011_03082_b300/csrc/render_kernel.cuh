@@ -246,7 +246,12 @@ enum Event : int { kEvHit = 0, kEvReenter, kEvEscape, kEvCap, kEvExit, kEvCollid
 //             per tile), FP32 accumulation: the error is that of the rounded weights.
 enum : int { kDecNone = 0, kDecFP32 = 1, kDecFP16 = 2, kDecBF16 = 3 };
 
-template <int kDecodeBatch, int kTransBatch, int kSteps, int kMinBlocks, int kDec>
+//
+// kTimers: an instrumented instantiation for the time breakdown (ms_render_params.phase_timers): each warp
+// accumulates clock64 cycles by round kind, added to the first request's stats[12..15] (march, decoder,
+// transition, refill rounds, summed over warps), and march steps of shadow rays are counted in each request's
+// stats[11].  The timed kernels are the kTimers = false instantiations, which carry none of this.
+template <int kDecodeBatch, int kTransBatch, int kSteps, int kMinBlocks, int kDec, bool kTimers = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __grid_constant__ Batch B)
 {
     constexpr bool kLearned = kDec != kDecNone;
@@ -265,18 +270,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     float* stage = s_stage[tid >> 5];
     float* draws = s_draws[kLearned ? tid >> 5 : 0];
     if constexpr (learned) {
-        mmadec::stage_weights<kHalfBF16, 1>(wl, B.wL, 2 + kLatL, 1);
-        mmadec::stage_weights<kHalfBF16, 2>(wpth, B.wP, 3 + kLatP, 3);
-        mmadec::stage_weights<kHalfBF16, 2>(wev, B.wE, 7 + kLatE, 6);
+        mmadec::stage_weights<kHalfBF16, 1, kSplit == 3>(wl, B.wL, 2 + kLatL, 1);
+        mmadec::stage_weights<kHalfBF16, 2, kSplit == 3>(wpth, B.wP, 3 + kLatP, 3);
+        mmadec::stage_weights<kHalfBF16, 2, kSplit == 3>(wev, B.wE, 7 + kLatE, 6);
     }
     for (int k = tid; k < kMaxReq * kStats; k += kThreads) s_stats[k] = 0ull;
     if (tid == 0) atomicMin(B.t_start, global_ns());
     __syncthreads();
 
     // counters of the lane's current path (flushed into its request's shared counters when the path ends)
-    unsigned cnt[kUsedStats];
+    constexpr int kCnt = kTimers ? kUsedStats + 1 : kUsedStats;   // + shadow-march steps (stats[11])
+    unsigned cnt[kCnt];
 #pragma unroll
-    for (int j = 0; j < kUsedStats; ++j) cnt[j] = 0u;
+    for (int j = 0; j < kCnt; ++j) cnt[j] = 0u;
+    unsigned long long phase_cycles[4] = {0ull, 0ull, 0ull, 0ull};   // kTimers: march, decoder, transition, refill
+    long long t_prev = kTimers ? clock64() : 0;
+    int last_phase = -1;
 
     // ---- the lane's path ----
     int st = kIdle, req = 0, ev = 0;
@@ -304,8 +313,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         if (atomicAdd(&B.done[req], 1ull) + 1ull == total_r)
             atomicExch(&B.stats[req * kStats + 10], global_ns() - *((volatile unsigned long long*)B.t_start));
 #pragma unroll
-        for (int j = 0; j < kUsedStats; ++j) {
-            if (cnt[j]) atomicAdd(&s_stats[req * kStats + j], (unsigned long long)cnt[j]);
+        for (int j = 0; j < kCnt; ++j) {
+            if (cnt[j]) atomicAdd(&s_stats[req * kStats + (j < kUsedStats ? j : 11)], (unsigned long long)cnt[j]);
             cnt[j] = 0u;
         }
         st = kIdle;
@@ -325,10 +334,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     };
 
     for (;;) {
+        if constexpr (kTimers) {
+            const long long now = clock64();
+            if (last_phase >= 0) phase_cycles[last_phase] += (unsigned long long)(now - t_prev);
+            t_prev = now;
+        }
         unsigned idle = __ballot_sync(0xffffffffu, st == kIdle);
         unsigned marching = __ballot_sync(0xffffffffu, st >= kCamera && st <= kShadow);
         // ---------------- refill round: new camera samples for idle lanes ----------------
         if (idle && !drained && (__popc(idle) >= kRefillBatch || __popc(marching) < 16)) {
+            last_phase = 3;
             const int leader = __ffs(idle) - 1;
             unsigned long long t0 = 0;
             if (lane == leader) t0 = atomicAdd(B.ticket, (unsigned long long)__popc(idle));
@@ -363,6 +378,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
 
         if (learned && parked && (__popc(parked) >= kDecodeBatch || n_active + __popc(pending) < kDecodeBatch)) {
             // ================= decoder round: the three learned samplers for the parked lanes =================
+            last_phase = 1;
             // The first 16 parked lanes (by lane index) are compacted into the 16 rows of one tensor-core tile;
             // the MLPs run on that tile (in the decoders' precision, kDec), and lanes parked beyond it wait for the
             // next round.  Everything else per path stays in the lane's registers.
@@ -475,6 +491,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
 
         if (pending && (__popc(pending) >= kTransBatch || n_active < 16)) {
             // ================= transition round: what follows each finished march =================
+            last_phase = 2;
             if (st == kPending) {
                 const Req& q = B.r[req];
                 bool need_flight = false, finish = false;   // one end_path call site for the whole round
@@ -561,6 +578,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         }
 
         // ================= kSteps signed-distance steps of every marching lane =================
+        last_phase = 0;
         // One body for every kind of march (selects, no per-kind branches), so lanes in different kinds of
         // march stay converged; only boundary crossings, which are rare, branch.
 #pragma unroll 1
@@ -581,6 +599,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             float rp, irp, R0, gd;
             const float f = sdf_parts_grad(geo, r, md, &rp, &irp, &R0, &gd);
             cnt[8] += 1u;
+            if constexpr (kTimers) cnt[kCnt - 1] += shadow ? 1u : 0u;
             const float hs = in_medium ? -f : f, h1 = in_medium ? -gd : gd;   // the marched side's distance
             const float dl = hs * geo.inv_lip;
             // boundary band: the point is on the surface; the ray crosses there if it moves to the other side,
@@ -639,6 +658,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     }
 
     // ---------------- block counters -> global ----------------
+    if constexpr (kTimers) {
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(&s_stats[12 + k], phase_cycles[k]);
+    }
     __syncthreads();
     for (int k = tid; k < B.n * kStats; k += kThreads)
         if (s_stats[k]) atomicAdd(&B.stats[k], s_stats[k]);

@@ -206,6 +206,40 @@ def fallback_sweep(sigma=64.0, res=128, spp=256, ref_spp=8192, tau_mins=(0.5, 1.
     return out
 
 
+def time_breakdown(sigmas=(64.0, 128.0), res=512, spp=64, cset=None):
+    """Where each method's time goes, per density: the instrumented render kernel (phase_timers) reports the
+    warps' cycles by round kind (march, decoder, transition, refill) and counts the march steps of shadow rays
+    apart from the path's own marches (camera, flight, re-entry).  The march cycles are split between the two in
+    proportion to their steps (every march step runs the same loop body).  Counts are per entering path."""
+    if cset is None:
+        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    out = []
+    for s in sigmas:
+        for mode, name in ((ms.MS_SPHERE, "sphere tracing"), (ms.MS_BRUTE, "brute force")):
+            p = synth.render_scene(s, width=res, height=res, spp=spp, mode=mode, seed=1)
+            rp = ms.render_params(dict(p, phase_timers=1))
+            img = torch.zeros(res * res, dtype=torch.float64, device="cuda")
+            st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+            ws = ms.workspace(ms.ms_render_workspace_size([rp]))
+            ms.ms_render(rp, cset if mode == ms.MS_SPHERE else None, img, st, ws=ws)
+            st = st.cpu().numpy().astype(np.float64)
+            cyc = st[12:16]
+            tot = max(cyc.sum(), 1.0)
+            radius = st[3] + st[4] if mode == ms.MS_SPHERE else 0.0
+            march_steps = st[8] - radius
+            shadow = st[11]
+            ent = max(st[1], 1.0)
+            share = dict(march_own=cyc[0] / tot * (march_steps - shadow) / max(march_steps, 1.0),
+                         march_shadow=cyc[0] / tot * shadow / max(march_steps, 1.0),
+                         decoder=cyc[1] / tot, transition=cyc[2] / tot, refill=cyc[3] / tot)
+            out.append(dict(sigma_t=s, method=name, res=res, spp=spp, time_share=share,
+                            per_entering_path=dict(flights=st[2] / ent, sphere_steps=st[3] / ent,
+                                                   brute_events=st[4] / ent, nee=st[7] / ent,
+                                                   march_steps_own=(march_steps - shadow) / ent,
+                                                   march_steps_shadow=shadow / ent)))
+    return out
+
+
 def fallback_policy(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, spp=256, ref_spp=8192,
                     tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None, variant=0, refs=None):
     """The thin-region threshold per density (Sec. 6): for each density the sweep above, and the minimum optical

@@ -9,9 +9,10 @@
   brute     the same render in brute-force mode
   render512 / brute512   512x512 px x 64 spp at sigma_t 128 (sphere tracing / brute force)
   render512g             render512 with sphere radii also from a 128^3 voxel grid of conservative distances
-  batch128 / batch256    the benchmark's launch (one ms_render_batch of sigma_t 16, 32, 64, 128, trained
-                         decoders) at 128x128 or 256x256 px x 16 spp: small cases of the benchmark launch for
-                         multi-pass ncu captures (DRAM bytes per launch scale with the images' pixels)
+  batch128 / batch256 / batch384 / batch512
+                         the benchmark's launch (one ms_render_batch of sigma_t 16, 32, 64, 128, trained
+                         decoders) at 128^2 .. 512^2 px x 16 spp, with L2 flushed before the launch (256 MB
+                         write) as in the benchmark: small cases of the benchmark launch for ncu captures
 Each case runs ``--repeat`` times (default 2) and prints the CUDA-event time of the last run.
 """
 from __future__ import annotations
@@ -95,9 +96,12 @@ def case_batch(res, spp=16, sigmas=(16.0, 32.0, 64.0, 128.0)):
     st = torch.zeros(len(reqs), ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
     ws = ms.workspace(ms.ms_render_workspace_size(reqs))
 
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
     def run():
         img.zero_()
         st.zero_()
+        flush.fill_(1)
         ms.ms_render_batch(reqs, cset, img, st, ws=ws)
     run.stats = st
     return run
@@ -109,7 +113,8 @@ CASES = {"walk": case_walk, "walk24": case_walk24, "decoder": case_decoder, "tra
          "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
          "render512g": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0, grid_n=128),
          "brute512": lambda: case_render(ms.MS_BRUTE, 512, 64, 128.0),
-         "batch128": lambda: case_batch(128), "batch256": lambda: case_batch(256)}
+         "batch128": lambda: case_batch(128), "batch256": lambda: case_batch(256),
+         "batch384": lambda: case_batch(384), "batch512": lambda: case_batch(512)}
 
 
 def main(argv=None):

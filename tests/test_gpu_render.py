@@ -262,3 +262,19 @@ def test_full_size_batch_sampled_pixels_match_oracle(orc):
         coincide += int(same.sum())
         total += pix.size
     assert coincide >= 0.95 * total, (coincide, total)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_phase_timers_instrumentation_traces_the_same_paths(mode):
+    """The instrumented kernel (phase_timers) traces the same paths as the timed one (same counters, image equal up
+    to the order of the per-pixel additions), counts shadow-ray march steps (stats[11], fewer than all march
+    steps) and reports positive warp cycles for the round kinds that ran (stats[12..15])."""
+    models = _models() if mode == 1 else None
+    p = synth.render_scene(64.0, width=24, height=24, spp=8, mode=mode, seed=6)
+    img, st = gpu_render(p, models)
+    img_t, st_t = gpu_render(dict(p, phase_timers=1), models)
+    assert np.array_equal(st[:10], st_t[:10]) and np.all(st[11:] == 0)
+    assert np.allclose(img, img_t, rtol=1e-6, atol=1e-12)
+    assert 0 < st_t[11] < st_t[8]
+    assert st_t[12] > 0 and st_t[14] > 0 and st_t[15] > 0
+    assert (st_t[13] > 0) == (mode == 1)
