@@ -61,10 +61,19 @@ __device__ __forceinline__ void sincos_turns_fast(float u, float* s, float* c)
     *c = -cs;
 }
 
+// Square root on the special-function unit's approximation (relative error about 2^-23; no IEEE rounding and
+// none of the correctly rounded square root's special-case branch).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Box-Muller: two standard normals from two 24-bit uniforms.
 __device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb)
 {
-    const float r = sqrtf(-2.0f * __logf(1.0f - u24(wa)));
+    const float r = sqrt_approx(-2.0f * __logf(1.0f - u24(wa)));
     float s, c;
     sincos_turns_fast(u24(wb), &s, &c);
     return make_float2(r * c, r * s);

@@ -51,8 +51,11 @@ static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const
         }
         q.tan_half = (float)std::tan(0.5 * (double)p.fov_y_deg * 3.14159265358979323846 / 180.0);
         q.aspect = (float)p.width / (float)p.height;
+        q.two_over_w = 2.0f / (float)p.width;
+        q.two_over_h = 2.0f / (float)p.height;
         q.I = p.light_I;
         q.sigma = p.sigma_t;
+        q.inv_sigma = 1.0f / p.sigma_t;
         q.g = p.g;
         q.phi = p.albedo;
         q.log_phi = p.albedo > 0.0f ? std::log(p.albedo) : -INFINITY;

@@ -42,9 +42,9 @@ constexpr int kMaxMarch = 1024;     // steps per march; running out ends the pat
 constexpr float kNMax = 16777216.0f;
 
 struct Req {
-    float cam[3], at[3], tan_half, aspect;
+    float cam[3], at[3], tan_half, aspect, two_over_w, two_over_h;
     float light[3], I;
-    float sigma, g, phi, log_phi, A, k, lip, inv_lip, rb2;
+    float sigma, inv_sigma, g, phi, log_phi, A, k, lip, inv_lip, rb2;
     float tau_min, tau_max;
     const float* grid;               // voxel grid of conservative distances, or null
     int32_t grid_n;
@@ -175,7 +175,7 @@ __device__ __forceinline__ float sdf_parts_grad(const Geo& q, V p, V w, float* r
 __device__ __forceinline__ float hg_pdf(float cosang, float g)
 {
     const float den = 1.0f + g * g - 2.0f * g * cosang;
-    return (1.0f - g * g) * 0.0795774715459476679f * rsqrtf(den) / den;
+    return (1.0f - g * g) * 0.0795774715459476679f * __fdividef(rsqrtf(den), den);
 }
 
 __device__ __forceinline__ float hg_cosine(float u, float g)
@@ -188,7 +188,7 @@ __device__ __forceinline__ float hg_cosine(float u, float g)
 __device__ __forceinline__ void onb(V w, V* t1, V* t2)
 {
     const float sign = w.z >= 0.0f ? 1.0f : -1.0f;
-    const float a = -1.0f / (sign + w.z);
+    const float a = __fdividef(-1.0f, sign + w.z);      // |sign + w.z| in [1, 2]
     const float b = w.x * w.y * a;
     *t1 = v3(1.0f + sign * w.x * w.x * a, sign * b, -sign * w.x);
     *t2 = v3(b, sign + w.y * w.y * a, -w.y);
@@ -198,7 +198,7 @@ __device__ __forceinline__ V scatter_dir(V w, float mu, float u)
 {
     V t1, t2;
     onb(w, &t1, &t2);
-    const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+    const float st = sqrt_approx(fmaxf(0.0f, 1.0f - mu * mu));
     float sp, cp;
     sincos_turns_fast(u, &sp, &cp);
     return unit(t1 * (st * cp) + t2 * (st * sp) + w * mu);
@@ -210,8 +210,8 @@ __device__ __forceinline__ void camera_ray(const Req& q, int px, int py, float j
     const V fw = unit(v3(q.at[0], q.at[1], q.at[2]) - cp);
     const V rt = unit(cross(fw, v3(0.0f, 1.0f, 0.0f)));
     const V up = cross(rt, fw);
-    const float sx = (2.0f * ((float)px + jx) / (float)q.W - 1.0f) * q.tan_half * q.aspect;
-    const float sy = (1.0f - 2.0f * ((float)py + jy) / (float)q.H) * q.tan_half;
+    const float sx = (((float)px + jx) * q.two_over_w - 1.0f) * q.tan_half * q.aspect;
+    const float sy = (1.0f - ((float)py + jy) * q.two_over_h) * q.tan_half;
     *o = cp;
     *d = unit(fw + rt * sx + up * sy);
 }
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         const Req& q = B.r[req];
         mo = nX;
         const V dl = v3(q.light[0], q.light[1], q.light[2]) - nX;
-        ml = sqrtf(dot(dl, dl));
-        md = dl * (1.0f / ml);
+        ml = sqrt_approx(dot(dl, dl));
+        md = dl * __fdividef(1.0f, ml);
         mt = 0.0f;
         din = 0.0f;
         inside = true;
@@ -354,8 +354,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 req = find_req(B, t);
                 const Req& q = B.r[req];
                 const uint64_t local = t - q.samples_begin;
-                id_hi = (uint32_t)(local / q.spp);
-                id_lo = (uint32_t)(q.sample_offset + local % q.spp);
+                if ((local >> 32) == 0) {                         // the usual case: 32-bit division
+                    id_hi = (uint32_t)local / q.spp;
+                    id_lo = (uint32_t)q.sample_offset + ((uint32_t)local - id_hi * q.spp);
+                } else {
+                    id_hi = (uint32_t)(local / q.spp);
+                    id_lo = (uint32_t)(q.sample_offset + local % q.spp);
+                }
                 const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
                 const Words j = rs.at(0u, 8u);
                 camera_ray(q, (int)(id_hi % (uint32_t)q.W), (int)(id_hi / (uint32_t)q.W), u24(j.w0), u24(j.w1),
@@ -452,14 +457,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
 #pragma unroll
                 for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * nrm(kEE + k);
                 const float phiN = __expf(N * qq.log_phi);
-                const float lam = qq.phi < 1.0f ? qq.phi * (1.0f - phiN) / (1.0f - qq.phi) : N;
+                const float lam = qq.phi < 1.0f ? __fdividef(qq.phi * (1.0f - phiN), 1.0f - qq.phi) : N;
                 // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
                 V t1, t2;
                 onb(w, &t1, &t2);
                 float sn, cs;
                 sincos_turns_fast(nrm(25), &sn, &cs);
-                const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-                const float nn = sqrtf(fmaxf(0.0f, 1.0f - ab2));
+                const float stt = sqrt_approx(fmaxf(0.0f, 1.0f - ct * ct));
+                const float nn = sqrt_approx(fmaxf(0.0f, 1.0f - ab2));
                 V vs[4] = {v3(stt, 0.0f, ct), v3(be * ct + nn * stt, al, -be * stt + nn * ct), v3(e[0], e[1], e[2]),
                            v3(e[3], e[4], e[5])};
                 const float xn2 = dot(vs[2], vs[2]);
@@ -501,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                         cnt[6] += 1u;
                     } else {
                         const float rho = hg_pdf(dot(nW, md), q.g);
-                        acc += nwt * rho * __expf(-q.sigma * din) * q.I / (ml * ml);
+                        acc += __fdividef(nwt * rho * __expf(-q.sigma * din) * q.I, ml * ml);
                     }
                     finish = end_after;
                     need_flight = !end_after;
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                             dc = fmaxf(dc, __ldg(q.grid + ((size_t)iz * q.grid_n + iy) * q.grid_n + ix));
                         }
                         cnt[8] += 1u;
-                        rad = fminf(dc, q.tau_max / q.sigma);
+                        rad = fminf(dc, q.tau_max * q.inv_sigma);
                         tau = q.sigma * rad;
                         if (tau >= q.tau_min) {
                             sphere = true;
@@ -561,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                         cnt[2] += 1u;
                         const Stream rs(q.seed, ((uint64_t)id_hi << 32) | id_lo);
                         const Words u = rs.at(seg, 0u);
-                        ml = -__logf(1.0f - u24(u.w0)) / q.sigma;
+                        ml = -__logf(1.0f - u24(u.w0)) * q.inv_sigma;
                         u1 = u24(u.w1);
                         u2 = u24(u.w2);
                         u3 = u24(u.w3);
