@@ -10,8 +10,8 @@
 //    log, a sin/cos pair, square roots — no memory traffic except when a photon finishes;
 //  * histograms live in shared memory (integer atomics, order independent) and are added to the global
 //    64-bit counters once per block, so results do not depend on the launch shape.
-// The arithmetic is written once against a precision policy: `F32` (24-bit uniforms, hardware
-// approximations) and `F64` (53-bit uniforms, the correctly rounded operations of ms_detmath.cuh in the same
+// The arithmetic is written once against a precision policy: `F32` (24-bit uniforms, the special-function
+// unit's approximations for log, sin/cos, reciprocal and square roots) and `F64` (53-bit uniforms, the correctly rounded operations of ms_detmath.cuh in the same
 // order as any other implementation of these steps; its translation unit is built without FMA contraction).
 #pragma once
 
@@ -48,7 +48,7 @@ struct F32 {
     static __device__ __forceinline__ real log(real x) { return __logf(x); }
     static __device__ __forceinline__ void sincos_turns(real u, real* s, real* c) { sincos_turns_fast(u, s, c); }
     static __device__ __forceinline__ real atan2(real y, real x) { return atan2f(y, x); }
-    static __device__ __forceinline__ real sqrt(real x) { return sqrtf(x); }
+    static __device__ __forceinline__ real sqrt(real x) { return sqrt_approx(x); }
     static __device__ __forceinline__ real div(real a, real b) { return __fdividef(a, b); }
     static __device__ __forceinline__ real inv_norm(real d) { return rsqrtf(d); }
     static constexpr bool kDivideToNormalise = false;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(Job J)
         }
         V3<Pol> x{(real)0, (real)0, (real)0};
         if (done < 0) {
-            const real l = -Pol::log((real)1 - u[0]) / ph.sig;
+            const real l = Pol::div(-Pol::log((real)1 - u[0]), ph.sig);
             const real b = dot<Pol>(ph.p, ph.w);
             const real c = dot<Pol>(ph.p, ph.p) - (real)1;
             real disc = b * b - c;
