@@ -43,6 +43,7 @@
 #define R_EPS        1e-4      /* distance from the boundary treated as on it */
 #define R_MAX_MARCH  1024      /* sphere-tracing steps per march; a march that runs out ends the path */
 #define R_N_MAX      16777216.0
+#define R_TAU_CUT    30.0      /* a shadow ray stops once its optical depth inside the medium exceeds this */
 
 typedef struct {
     int32_t p_in, latent, width, p_out;
@@ -257,8 +258,10 @@ static int march_outside(const scene* S, ov3 p, ov3 w, ov3* q)
 }
 
 /* Length of the straight segment X -> x_L that lies inside the medium (Sec. 4.3, d_t); -1 when the step
- * cap runs out (the estimate is then dropped).  A boundary crossing switches the side at the same point. */
-static double inside_length(const scene* S, ov3 X, ov3 xl)
+ * cap runs out (the estimate is then dropped).  A boundary crossing switches the side at the same point.  The
+ * march stops once the inside length exceeds din_cut (returning it): the transmittance exp(-sigma_t d_t) is
+ * then below exp(-sigma_t din_cut), and whatever follows can only make it smaller. */
+static double inside_length(const scene* S, ov3 X, ov3 xl, double din_cut)
 {
     ov3 dl = sub(xl, X);
     double D = sqrt(dot(dl, dl));
@@ -266,7 +269,7 @@ static double inside_length(const scene* S, ov3 X, ov3 xl)
     double t = 0.0, din = 0.0;
     int inside = 1;
     for (int it = 0; it < S->max_march; ++it) {
-        if (t >= D)
+        if (t >= D || din > din_cut)
             return din;
         ov3 r = add(X, mul(w, t));
         if (!inside && dot(r, r) > S->rb2 && dot(r, w) >= 0.0)
@@ -408,7 +411,9 @@ static double nee(const scene* S, const om_render_params* P, ov3 X, ov3 W, doubl
     double d2 = dot(dl, dl);
     ov3 wl = mul(dl, 1.0 / sqrt(d2));
     double rho = hg_pdf(dot(W, wl), P->g);
-    double din = inside_length(S, X, xl);
+    /* a shadow ray whose optical depth passes R_TAU_CUT is not marched further: its transmittance is below
+     * exp(-R_TAU_CUT) (about 1e-13) of the unshadowed term, far below single precision and Monte Carlo noise */
+    double din = inside_length(S, X, xl, R_TAU_CUT / P->sigma_t);
     if (din < 0.0) {
         st[6] += 1;
         return 0.0;
@@ -838,5 +843,5 @@ double om_march_step(double A, double k, const double* p, const double* w)
 double om_inside_length(double A, double k, const double* X, const double* xl)
 {
     scene S = { A, k, 1.0 + A * k, (1.0 + A + 1e-3) * (1.0 + A + 1e-3), NULL, 0, 0.0, 0.0, 0, R_MAX_MARCH };
-    return inside_length(&S, v3(X[0], X[1], X[2]), v3(xl[0], xl[1], xl[2]));
+    return inside_length(&S, v3(X[0], X[1], X[2]), v3(xl[0], xl[1], xl[2]), INFINITY);
 }

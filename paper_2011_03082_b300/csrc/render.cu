@@ -56,6 +56,7 @@ static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const
         q.I = p.light_I;
         q.sigma = p.sigma_t;
         q.inv_sigma = 1.0f / p.sigma_t;
+        q.din_cut = kTauCut / p.sigma_t;
         q.g = p.g;
         q.phi = p.albedo;
         q.log_phi = p.albedo > 0.0f ? std::log(p.albedo) : -INFINITY;

@@ -40,11 +40,12 @@ constexpr int kStats = MS_RENDER_STATS;
 constexpr float kEps = 1e-4f;       // distance from the boundary treated as on it
 constexpr int kMaxMarch = 1024;     // steps per march; running out ends the path (or drops the estimate)
 constexpr float kNMax = 16777216.0f;
+constexpr float kTauCut = 30.0f;    // a shadow ray stops once its optical depth inside the medium exceeds this
 
 struct Req {
     float cam[3], at[3], tan_half, aspect, two_over_w, two_over_h;
     float light[3], I;
-    float sigma, inv_sigma, g, phi, log_phi, A, k, lip, inv_lip, rb2;
+    float sigma, inv_sigma, din_cut, g, phi, log_phi, A, k, lip, inv_lip, rb2;
     float tau_min, tau_max;
     const float* grid;               // voxel grid of conservative distances, or null
     int32_t grid_n;
@@ -95,7 +96,7 @@ __device__ __forceinline__ V unit(V a) { return a * rsqrtf(dot(a, a)); }
 
 // The constants of the march held in registers for the lane's current request.
 struct Geo {
-    float A, k, inv_lip, rb2;
+    float A, k, inv_lip, rb2, din_cut;
 };
 
 // ---- the displaced sphere f(p) = |p| - R(p), R(p) = 1 + A sin(kx) sin(ky) sin(kz) (negative inside) ----
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     float mt = 0.0f, ml = 0.0f, din = 0.0f;
     int mstep = 0;
     bool inside = true, capped = false;
-    Geo geo{0.0f, 0.0f, 1.0f, 1.0f};
+    Geo geo{0.0f, 0.0f, 1.0f, 1.0f, 0.0f};
     bool drained = false;                       // warp-uniform: camera tickets exhausted
 
     auto end_path = [&]() {
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 mt = 0.0f;
                 mstep = 0;
                 st = kCamera;
-                geo = Geo{q.A, q.k, q.inv_lip, q.rb2};
+                geo = Geo{q.A, q.k, q.inv_lip, q.rb2, q.din_cut};
                 cnt[0] += 1u;
             }
             continue;
@@ -651,7 +652,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             const float adv = reach ? lim - mt : d;
             if (shadow && inside) din += adv;
             mt += adv;
-            if (reach) {
+            // a shadow ray whose optical depth has passed kTauCut ends here: its transmittance is below
+            // exp(-kTauCut) (about 1e-13) of the unshadowed term, and the rest of the segment can only lower it
+            if (reach || (shadow && din > geo.din_cut)) {
                 ev = flight ? kEvCollide : kEvShadowDone;
                 st = kPending;
             } else if (mstep >= kMaxMarch) {
