@@ -266,6 +266,11 @@ typedef struct {
     const float* sdf_grid;      /* NULL, or device [n][n][n] from ms_sdf_grid_build(disp_amp, disp_freq, n):
                                    a sphere step's radius is then the larger of the distance bound and
                                    the value of the grid voxel holding the collision point             */
+    int32_t exact_n1;           /* 0: LengthGen gives N (the paper's form).  1: a sphere step takes N = 1 with
+                                   its exact probability exp(-tau) — the first free path from the centre
+                                   leaves the sphere (Sec. 3.1) — using the uniform of the tag 4 words'
+                                   low bytes, and LengthGen, trained on the N >= 2 records, gives N >= 2
+                                   otherwise; for models trained that way                                */
     int32_t phase_timers;       /* 0 normally.  1 (first request of a launch): run an instrumented kernel
                                    of the default variant that also counts shadow-ray march steps in
                                    stats[11] and adds each warp's clock cycles by round kind to the first

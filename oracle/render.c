@@ -30,7 +30,8 @@
  *   tags 2..7: Box-Muller normals n[0..23], tag t words (w0,w1) -> n[4(t-2)], n[4(t-2)+1], (w2,w3) -> next two;
  *       used in order: LengthGen z then eps, PathGen z then eps, EventGen z then eps; the low bytes of words
  *       0..2, which the uniforms leave unused, give ((w0 & 0xff) << 16 | (w1 & 0xff) << 8 | (w2 & 0xff)) 2^-24:
- *       from tag 2 the absorption test's uniform, from tag 3 the rotation angle psi's
+ *       from tag 2 the absorption test's uniform, from tag 3 the rotation angle psi's, from tag 4 the
+ *       exact N = 1 test's (exact_n1)
  *   tag 8 at step 0: pixel jitter.
  * Uniforms are (w >> 8) * 2^-24 (24-bit), identical to the single-precision kernels' stream.
  */
@@ -61,6 +62,8 @@ typedef struct {
     int32_t sdf_grid_n;        /* 0, or n: sphere radii also from an n^3 voxel grid of conservative distances */
     int32_t march_mode;        /* 0 the largest of the three conservative steps, 1 the Lipschitz step alone */
     int32_t max_march;         /* steps per march, 0 for the default R_MAX_MARCH */
+    int32_t exact_n1;          /* 1: N = 1 drawn with its exact probability exp(-tau), LengthGen gives N >= 2 */
+    int32_t pad_;
     double min_optical_radius, max_optical_radius;
     uint64_t seed, sample_offset;
     const double* sdf_grid;    /* sdf_grid_n^3 voxel values (index (iz n + iy) n + ix) over [-b, b]^3, voxel side
@@ -300,12 +303,12 @@ static void words(const stream* s, uint32_t step, uint32_t tag, uint32_t w[4])
 }
 static double u24(uint32_t w) { return (double)(w >> 8) * 0x1.0p-24; }
 
-static void normals(const stream* s, uint32_t step, double n[24], double extra[2])
+static void normals(const stream* s, uint32_t step, double n[24], double extra[3])
 {
     for (uint32_t t = 2; t < 8; ++t) {
         uint32_t w[4];
         words(s, step, t, w);
-        if (t < 4)
+        if (t < 5)
             extra[t - 2] = (double)(((w[0] & 0xffu) << 16) | ((w[1] & 0xffu) << 8) | (w[2] & 0xffu)) * 0x1.0p-24;
         for (int pair = 0; pair < 2; ++pair) {
             double ua = u24(w[2 * pair]), ub = u24(w[2 * pair + 1]);
@@ -521,7 +524,7 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
             if (tau >= P->min_optical_radius) {
                 /* ---- sphere-tracing step: the three models of Eq. 3 at optical radius tau ---- */
                 st[3] += 1;
-                double n[24], ua[2];
+                double n[24], ua[3];
                 normals(&rs, seg, n, ua);
                 double N, ct, al, be, ab2, xe[6];
                 if (P->mode == 2) {
@@ -540,8 +543,14 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                     double cL[2] = { ltau, g }, yN;
                     decoder_sample(&D[0], cL, n + zL, n + eL, &yN);
                     N = floor(exp(yN) + 0.5);
-                    if (!(N >= 1.0)) N = 1.0;
+                    /* exact_n1: a step leaves the sphere after its first event (at the centre) exactly when the
+                     * first free path exceeds the radius, with probability exp(-tau) (Sec. 3.1); that mass is
+                     * drawn as such and LengthGen, trained on the N >= 2 records, gives the rest */
+                    double n_min = P->exact_n1 ? 2.0 : 1.0;
+                    if (!(N >= n_min)) N = n_min;
                     if (N > R_N_MAX) N = R_N_MAX;
+                    if (P->exact_n1 && ua[2] < exp(-tau))
+                        N = 1.0;
                     double lnN = log(N);
                     double cP[3] = { ltau, g, lnN }, xp[3];
                     decoder_sample(&D[1], cP, n + zP, n + eP, xp);

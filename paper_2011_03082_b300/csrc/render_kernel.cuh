@@ -50,7 +50,7 @@ struct Req {
     const float* grid;               // voxel grid of conservative distances, or null
     int32_t grid_n;
     float grid_b, grid_inv_h;
-    int32_t W, H, mode;
+    int32_t W, H, mode, exact_n1;
     uint32_t spp, max_segments;
     uint64_t seed, sample_offset, image_offset, samples_begin;
 };
@@ -228,7 +228,7 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
 }
 
 constexpr int kUsedStats = 10;
-constexpr int kDraws = 26 * 16;      // a decoder round's draws: value v of row r at [v * 16 + r]
+constexpr int kDraws = 27 * 16;      // a decoder round's draws: value v of row r at [v * 16 + r]
 constexpr int kDrawKeys = 0;         // staging-tile offset of the draw keys (5 words per row) in a decoder round
 static_assert(kDrawKeys + 5 * 16 <= mmadec::kStageFloats, "decoder-round draw keys exceed the staging tile");
 
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             const int rank = __popc(parked & ((1u << lane) - 1u));
             const bool mine = st == kDecode && rank < 16;
             const Req& qq = B.r[req];
-            // The step's draws (tags 2..7: 24 normals; the low bytes of words 0..2 of tags 2 and 3, unused by
-            // the normals, give the absorption and azimuth uniforms) are the same Philox blocks as drawn lane
+            // The step's draws (tags 2..7: 24 normals; the low bytes of words 0..2 of tags 2, 3 and 4, unused by
+            // the normals, give the absorption, azimuth and exact-N = 1 uniforms) are the same Philox blocks as drawn lane
             // by lane, but the 6 blocks of each of the nsel selected paths are spread over all 32 lanes and
             // handed over through shared memory: value v of row r at draws[v * 16 + r].
             const int nsel = min(16, __popc(parked));
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 const float2 a = box_muller(wd.w0, wd.w1), b = box_muller(wd.w2, wd.w3);
                 float* o = draws + 4 * c * 16 + r;
                 o[0] = a.x; o[16] = a.y; o[32] = b.x; o[48] = b.y;
-                if (c < 2)
+                if (c < 3)
                     draws[(24 + c) * 16 + r] =
                         (float)(((wd.w0 & 0xffu) << 16) | ((wd.w1 & 0xffu) << 8) | (wd.w2 & 0xffu)) * 0x1.0p-24f;
             }
@@ -433,7 +433,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             mmadec::warp_mlp_rows16<1, kSplit, kHalfBF16, 1, 2 + kLatL, 2>(wl, stage, xin, yL, rank, mine);
             const float yN = yL[0] + __expf(0.5f * yL[1]) * nrm(kEL);
             float N = floorf(__expf(yN) + 0.5f);
-            N = fminf(fmaxf(N, 1.0f), kNMax);
+            N = fminf(fmaxf(N, mine && qq.exact_n1 ? 2.0f : 1.0f), kNMax);
+            // exact_n1: N = 1 (the first free path from the centre leaves the sphere) drawn with its exact
+            // probability exp(-tau), LengthGen (trained on the N >= 2 records) giving the rest
+            if (mine && qq.exact_n1 && nrm(26) < __expf(-tau)) N = 1.0f;
             const float lnN = mine ? __logf(N) : 0.0f;
             // PathGen: (cos theta, alpha, beta)
             float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, nrm(kZP), nrm(kZP + 1), nrm(kZP + 2), nrm(kZP + 3),

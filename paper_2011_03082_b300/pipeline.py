@@ -11,6 +11,10 @@
 3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder), each
    model's shape (p_in, p_out, latent, width: the final settings of Table 1) and the training log.
 
+With ``--exact-n1`` LengthGen is trained on the records with N >= 2 only: a renderer using such a set draws
+N = 1 with its exact probability exp(-tau) (the first free path from the centre leaves the sphere, Sec. 3.1)
+and samples N >= 2 from LengthGen (``render_options``).  The paper's form trains LengthGen on every record.
+
 Run as ``python -m paper_2011_03082_b300.pipeline [--walks N] [--steps S] [--out PATH] [--precision bf16]``.
 """
 from __future__ import annotations
@@ -77,14 +81,24 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
 
 
 def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every=100,
-          precision: int = ms.MS_FP32) -> dict:
+          precision: int = ms.MS_FP32, exact_n1: bool = False) -> dict:
     models = {}
     for i, name in enumerate(MODELS):
         ck, xk = RECORD_KEYS[name]
-        params, log = train_one(name, records[ck], records[xk], steps=steps, batch=batch, lr=lr,
-                                seed=seed + 17 * i, log_every=log_every, precision=precision)
+        c, x = records[ck], records[xk]
+        if name == "length" and exact_n1:
+            # the records with N >= 2: the dequantised y = ln(N - 1/2 + u) is >= ln(3/2) exactly for those
+            keep = x[:, 0] >= float(np.log(1.5))
+            c, x = c[keep].contiguous(), x[keep].contiguous()
+        params, log = train_one(name, c, x, steps=steps, batch=batch, lr=lr, seed=seed + 17 * i,
+                                log_every=log_every, precision=precision)
         models[name] = dict(params=params.cpu().numpy(), log=log)
     return models
+
+
+def render_options(models: dict) -> dict:
+    """Render-request fields that a model set needs: ``exact_n1`` when its LengthGen was trained on N >= 2."""
+    return dict(exact_n1=int(bool(models.get("meta", {}).get("exact_n1", False))))
 
 
 def decoder_part(name: str, params: np.ndarray) -> np.ndarray:
@@ -140,6 +154,8 @@ def main(argv=None):
     ap.add_argument("--out", default=str(DEFAULT_WEIGHTS))
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
                     help="training arithmetic (bf16: BF16 products, FP32 accumulation and master weights)")
+    ap.add_argument("--exact-n1", action="store_true",
+                    help="train LengthGen on the N >= 2 records (N = 1 is then drawn exactly, exp(-tau))")
     a = ap.parse_args(argv)
     prec = ms.MS_BF16 if a.precision == "bf16" else ms.MS_FP32
     torch.cuda.synchronize()
@@ -147,11 +163,12 @@ def main(argv=None):
     recs = generate_records(a.walks, a.seed)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=prec)
+    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=prec, exact_n1=a.exact_n1)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     c = recs["counters"].cpu().tolist()
     meta = dict(walks=a.walks, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=a.precision,
+                exact_n1=bool(a.exact_n1),
                 walk_seconds=t1 - t0,
                 train_seconds=t2 - t1, walk_counters=c,
                 final_loss={k: v["log"][-1][1] for k, v in models.items()})

@@ -202,3 +202,28 @@ def test_renderer_rejects_mixed_or_unknown_decoder_precision(trained):
     cs.path.precision = ms.MS_FP64
     with pytest.raises(ms.MsError, match="precision"):
         gpu_render(p, cs)
+
+
+def test_exact_n1_render_matches_oracle(orc):
+    """exact_n1 (a sphere step takes N = 1 with its exact probability exp(-tau), LengthGen trained on the N >= 2
+    records gives N >= 2): the renderer against the oracle with the same rule and the same model set
+    (weights/cvae_set_n1.npz), same acceptance as the other trained cases (sigma_t 16 and 64)."""
+    models = pipeline.load(pipeline.DEFAULT_WEIGHTS.with_name("cvae_set_n1.npz"))
+    opt = pipeline.render_options(models)
+    assert opt == dict(exact_n1=1)
+    dec = {k: pipeline.decoder_part(k, models[k]["params"]) for k in pipeline.MODELS}
+    cs = ms.cvae_set({k: (torch.from_numpy(dec[k]).cuda(), *synth.MODEL_SHAPES[k]) for k in pipeline.MODELS})
+    decs = [(dec[k].astype(np.float64), *synth.MODEL_SHAPES[k]) for k in pipeline.MODELS]
+    for sigma in (16.0, 64.0):
+        p1 = dict(synth.render_scene(sigma, width=32, height=32, spp=16, mode=1, seed=1), **opt)
+        p2 = dict(p1, seed=2)
+        o1, _, _ = orc.render(p1, decs)
+        o2, s2, _ = orc.render(p2, decs)
+        g2, gs = gpu_render(p2, cs)
+        tol = 2.0 * sigma * (1.0 + p1["disp_amp"] * p1["disp_freq"]) * EPS
+        same = np.abs(g2 - o2) <= tol * np.abs(o2) + 1e-9
+        assert same.mean() >= 0.98, (sigma, same.mean())
+        noise = rmse(o2, o1)
+        assert abs(rmse(g2, o1) / noise - 1.0) <= 0.01, (sigma, rmse(g2, o1), noise)
+        for k in (1, 2, 3, 4, 5, 7):
+            assert abs(int(gs[k]) - int(s2[k])) <= 0.01 * max(s2[k], 100), (sigma, k, gs[k], s2[k])
