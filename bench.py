@@ -3,7 +3,9 @@
 Workload (one step): the displaced-sphere object 0.1 sin(6x) sin(6y) sin(6z) lit by a point light, rendered at
 512 x 512 pixels with 256 samples per pixel at the four densities sigma_t in {16, 32, 64, 128} (density
 doubling, g = 0.8, albedo 0.999), with the three decoders trained by ``paper_2011_03082_b300.pipeline`` —
-the four images in one persistent ``ms_render_batch`` launch.  ``value`` counts camera paths (light paths)
+the four images in one persistent ``ms_render_batch`` launch.  The decoders are the model set
+``pipeline.RENDER_SET`` (trained for the exact N = 1 step and centre event; ``--models paper`` for the set in the
+paper's form).  ``value`` counts camera paths (light paths)
 per second over all ranks.  The brute-force tracer is timed on the same workload for context.
 
 ``python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]``; under torchrun every rank renders
@@ -133,7 +135,7 @@ def recorded_traffic(pixels: int):
 
 # --------------------------------------------------------------------------------------------- CPU oracle
 
-def oracle_paths_per_second(models_np, budget_s: float, sigmas=SIGMAS, mode=1):
+def oracle_paths_per_second(models_np, budget_s: float, sigmas=SIGMAS, mode=1, opts=None):
     """Time the oracle renderer (as it stands) on a bounded sample of the workload: every density, a square
     image and spp sized so that the whole sample takes about ``budget_s`` seconds on all host cores."""
     import oracle
@@ -145,7 +147,8 @@ def oracle_paths_per_second(models_np, budget_s: float, sigmas=SIGMAS, mode=1):
         paths, threads = 0, 0
         t0 = time.perf_counter()
         for s in sigmas:
-            _, st, threads = oracle.render(synth.render_scene(s, width=side, height=side, spp=spp, mode=mode), decs)
+            _, st, threads = oracle.render(dict(synth.render_scene(s, width=side, height=side, spp=spp, mode=mode),
+                                                **(opts or {})), decs)
             paths += int(st[0])
         return paths, time.perf_counter() - t0, threads
 
@@ -169,15 +172,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2011_03082_b300 import pipeline
-    models = pipeline.load()
+    models = pipeline.load_set(args.models or pipeline.RENDER_SET)
+    opts = pipeline.render_options(models)
     dec = {k: pipeline.decoder_part(k, models[k]["params"]) for k in pipeline.MODELS}
     # each step is a bounded sample; the budget keeps the whole run within a few minutes
     budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_paths_per_second(dec, budget * 0.25)
+        oracle_paths_per_second(dec, budget * 0.25, opts=opts)
     vals, samples, cores = [], [], 0
     for _ in range(args.steps):
-        r = oracle_paths_per_second(dec, budget)
+        r = oracle_paths_per_second(dec, budget, opts=opts)
         vals.append(r["value"])
         samples.append(r["sample"])
         cores = r["cores"]
@@ -211,6 +215,8 @@ def main(argv=None):
     ap.add_argument("--eq-ref-spp", type=int, default=16384, help="spp of its brute-force reference")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="resolution and spp scale of the 64 requests")
     ap.add_argument("--variant", type=int, default=None, help="renderer variant to use instead of autotuning")
+    ap.add_argument("--models", default=None, help="model set (paper_2011_03082_b300.pipeline.MODEL_SETS); "
+                                                   "pipeline.RENDER_SET when not given")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -227,14 +233,16 @@ def main(argv=None):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    models = pipeline.load()
+    set_name = args.models or pipeline.RENDER_SET
+    models = pipeline.load_set(set_name)
+    opts = pipeline.render_options(models)
     dm = pipeline.device_decoders(models, dev)
     cset = ms.cvae_set(dm)
 
     W = H = args.width
     spp = args.spp
-    reqs = [synth.render_scene(s, width=W, height=H, spp=spp, mode=ms.MS_SPHERE, seed=1,
-                               sample_offset=rank * spp) for s in SIGMAS]
+    reqs = [dict(synth.render_scene(s, width=W, height=H, spp=spp, mode=ms.MS_SPHERE, seed=1,
+                                    sample_offset=rank * spp), **opts) for s in SIGMAS]
     preqs = [ms.render_params(r) for r in reqs]
     npx = W * H * len(reqs)
     images = torch.zeros(npx, dtype=torch.float64, device=dev)
@@ -419,9 +427,9 @@ def main(argv=None):
         from paper_2011_03082_b300 import experiments
         refs = experiments.reference_images(SIGMAS, args.eq_res, args.eq_ref_spp, variant, cset)
         rows = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
-                                      variant=variant, refs=refs, tau_min=1.0)
+                                      variant=variant, refs=refs, tau_min=1.0, opts=opts)
         rows_auto = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
-                                           variant=variant, refs=refs, tau_min=0.0)
+                                           variant=variant, refs=refs, tau_min=0.0, opts=opts)
         keys = ("sigma_t", "tau_min", "rmse_st", "spp_bf_equal", "t_st_s", "t_bf_equal_s", "speedup", "note")
         equal = {"res": args.eq_res, "ref_spp": args.eq_ref_spp, "st_spp": spp,
                  "per_sigma": [{k: r[k] for k in keys} for r in rows],
@@ -430,22 +438,23 @@ def main(argv=None):
                                                        ms.lib().ms_render_default_min_optical_radius(r["sigma_t"])))
                                               for r in rows_auto]}
         pol = experiments.fallback_policy(SIGMAS, res=args.eq_res, spp=spp, ref_spp=args.eq_ref_spp, cset=cset,
-                                          variant=variant, refs=refs)
+                                          variant=variant, refs=refs, opts=opts)
         policy = [{"sigma_t": r["sigma_t"], "best_tau_min": r["best_tau_min"],
                    "library_default": r["library_default"],
                    "sweep": [{k: v for k, v in x.items() if k != "mode"} for x in r["sweep"]]} for r in pol]
         del refs
-        breakdown = experiments.time_breakdown((64.0, 128.0), res=W, spp=64, cset=cset)
+        breakdown = experiments.time_breakdown((64.0, 128.0), res=W, spp=64, cset=cset, opts=opts)
     if rank == 0 and world == 1 and not args.no_batched:
         from paper_2011_03082_b300 import experiments
-        b = experiments.batched(seed=5, n=64, scale=args.batch_scale, repeats=1, cset=cset, sequential=False)
+        b = experiments.batched(seed=5, n=64, scale=args.batch_scale, repeats=1, cset=cset, sequential=False,
+                                opts=opts)
         batch = {k: b[k] for k in ("requests", "scale", "paths", "seconds", "paths_per_s", "variant", "p50_ms",
                                    "p99_ms", "launch")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         dec_np = {k: pipeline.decoder_part(k, models[k]["params"]) for k in pipeline.MODELS}
-        cpu = oracle_paths_per_second(dec_np, args.cpu_budget)
+        cpu = oracle_paths_per_second(dec_np, args.cpu_budget, opts=opts)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -457,6 +466,8 @@ def main(argv=None):
                            else "single GPU", "stats_per_request": per_req,
                            "kernel_variant": dict(index=variant, **ms.ms_render_variant_info(variant)),
                            "autotune_ms": [round(t, 2) for t in variant_ms]},
+                "model_set": {"name": set_name, "file": "paper_2011_03082_b300/weights/" + pipeline.MODEL_SETS[set_name],
+                              "render_options": opts},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clocks, "entering_paths_per_s": entering, "brute_force": brute,
                 "decoder_precision": precision, "equal_rmse": equal, "time_breakdown": breakdown,

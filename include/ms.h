@@ -269,13 +269,23 @@ typedef struct {
     int32_t exact_n1;           /* 0: LengthGen gives N (the paper's form).  1: a sphere step takes N = 1 with
                                    its exact probability exp(-tau) — the first free path from the centre
                                    leaves the sphere (Sec. 3.1) — using the uniform of the tag 4 words'
-                                   low bytes, and LengthGen, trained on the N >= 2 records, gives N >= 2
-                                   otherwise; for models trained that way                                */
+                                   low bytes, and such a step is exact as a whole: the path leaves
+                                   radially along the centre event's HG scattering of the incoming
+                                   direction (cos theta from the tag 6 words' low bytes, alpha = beta = 0)
+                                   and that event is the representative one.  Otherwise the models give
+                                   the step, with N >= 2; for models trained on the N >= 2 records       */
     int32_t phase_timers;       /* 0 normally.  1 (first request of a launch): run an instrumented kernel
                                    of the default variant that also counts shadow-ray march steps in
                                    stats[11] and adds each warp's clock cycles by round kind to the first
                                    request's stats[12..15] (march, decoder, transition, refill) — a time
                                    breakdown; FP32 decoders only; slightly slower                       */
+    int32_t exact_centre;       /* 0: EventGen gives the representative event (the paper's form).  1: the
+                                   representative event is the step's first event — at the centre, with
+                                   the incoming direction — with its exact probability phi / Lambda (the
+                                   weight phi^k / Lambda of k = 1, Sec. 4.3; always when N = 1), using the
+                                   uniform of the tag 5 words' low bytes, and EventGen, trained on the
+                                   records whose representative event is a later one, gives it otherwise;
+                                   for models trained that way                                          */
 } ms_render_params;
 
 /* The voxel grid of conservative distances that sizes sphere steps (Sec. 3: the bounding volume is voxelised

@@ -64,7 +64,7 @@ class RenderParams(C.Structure):
                 ("sigma_t", C.c_double), ("g", C.c_double), ("albedo", C.c_double),
                 ("disp_amp", C.c_double), ("disp_freq", C.c_double),
                 ("mode", C.c_int32), ("sdf_grid_n", C.c_int32), ("march_mode", C.c_int32),
-                ("max_march", C.c_int32), ("exact_n1", C.c_int32), ("pad_", C.c_int32),
+                ("max_march", C.c_int32), ("exact_n1", C.c_int32), ("exact_centre", C.c_int32),
                 ("min_optical_radius", C.c_double), ("max_optical_radius", C.c_double),
                 ("seed", C.c_uint64), ("sample_offset", C.c_uint64), ("sdf_grid", C.c_void_p)]
 

@@ -31,7 +31,8 @@
  *       used in order: LengthGen z then eps, PathGen z then eps, EventGen z then eps; the low bytes of words
  *       0..2, which the uniforms leave unused, give ((w0 & 0xff) << 16 | (w1 & 0xff) << 8 | (w2 & 0xff)) 2^-24:
  *       from tag 2 the absorption test's uniform, from tag 3 the rotation angle psi's, from tag 4 the
- *       exact N = 1 test's (exact_n1)
+ *       exact N = 1 test's (exact_n1), from tag 5 the centre-event test's (exact_centre), from tag 6 the
+ *       HG cosine of an exact N = 1 step's exit (exact_n1)
  *   tag 8 at step 0: pixel jitter.
  * Uniforms are (w >> 8) * 2^-24 (24-bit), identical to the single-precision kernels' stream.
  */
@@ -62,8 +63,10 @@ typedef struct {
     int32_t sdf_grid_n;        /* 0, or n: sphere radii also from an n^3 voxel grid of conservative distances */
     int32_t march_mode;        /* 0 the largest of the three conservative steps, 1 the Lipschitz step alone */
     int32_t max_march;         /* steps per march, 0 for the default R_MAX_MARCH */
-    int32_t exact_n1;          /* 1: N = 1 drawn with its exact probability exp(-tau), LengthGen gives N >= 2 */
-    int32_t pad_;
+    int32_t exact_n1;          /* 1: the N = 1 step drawn exactly (probability exp(-tau), exit along the first
+                                  event's HG direction, event at the centre), the models give N >= 2 */
+    int32_t exact_centre;      /* 1: the representative event is the first one (the centre, incoming direction)
+                                  with its exact probability phi / Lambda, EventGen gives the later ones */
     double min_optical_radius, max_optical_radius;
     uint64_t seed, sample_offset;
     const double* sdf_grid;    /* sdf_grid_n^3 voxel values (index (iz n + iy) n + ix) over [-b, b]^3, voxel side
@@ -303,12 +306,12 @@ static void words(const stream* s, uint32_t step, uint32_t tag, uint32_t w[4])
 }
 static double u24(uint32_t w) { return (double)(w >> 8) * 0x1.0p-24; }
 
-static void normals(const stream* s, uint32_t step, double n[24], double extra[3])
+static void normals(const stream* s, uint32_t step, double n[24], double extra[5])
 {
     for (uint32_t t = 2; t < 8; ++t) {
         uint32_t w[4];
         words(s, step, t, w);
-        if (t < 5)
+        if (t < 7)
             extra[t - 2] = (double)(((w[0] & 0xffu) << 16) | ((w[1] & 0xffu) << 8) | (w[2] & 0xffu)) * 0x1.0p-24;
         for (int pair = 0; pair < 2; ++pair) {
             double ua = u24(w[2 * pair]), ub = u24(w[2 * pair + 1]);
@@ -524,7 +527,7 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
             if (tau >= P->min_optical_radius) {
                 /* ---- sphere-tracing step: the three models of Eq. 3 at optical radius tau ---- */
                 st[3] += 1;
-                double n[24], ua[3];
+                double n[24], ua[5];
                 normals(&rs, seg, n, ua);
                 double N, ct, al, be, ab2, xe[6];
                 if (P->mode == 2) {
@@ -545,7 +548,10 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                     N = floor(exp(yN) + 0.5);
                     /* exact_n1: a step leaves the sphere after its first event (at the centre) exactly when the
                      * first free path exceeds the radius, with probability exp(-tau) (Sec. 3.1); that mass is
-                     * drawn as such and LengthGen, trained on the N >= 2 records, gives the rest */
+                     * drawn as such and LengthGen, trained on the N >= 2 records, gives the rest.  Such a step
+                     * is then exact as a whole: the path leaves radially along the event's HG scattering of the
+                     * incoming direction, so x~ = w~ = (sin theta, 0, cos theta) with cos theta the HG cosine
+                     * and alpha = beta = 0, and its one event, the centre, is the representative one */
                     double n_min = P->exact_n1 ? 2.0 : 1.0;
                     if (!(N >= n_min)) N = n_min;
                     if (N > R_N_MAX) N = R_N_MAX;
@@ -564,9 +570,22 @@ static double trace_path(const render_job* J, const scene* S, int px, int py, ui
                     }
                     double cE[7] = { ltau, g, phi, ct, al, be, lnN };
                     decoder_sample(&D[2], cE, n + zE, n + eE, xe);
+                    if (P->exact_n1 && N <= 1.0) {
+                        ct = hg_cosine(ua[4], g);
+                        al = 0.0; be = 0.0; ab2 = 0.0;
+                    }
                 }
                 double phiN = pow(phi, N);
                 double lam = (phi < 1.0) ? phi * (1.0 - phiN) / (1.0 - phi) : N;
+                /* exact_centre: the first event sits at the centre c with the incoming direction w, and Sec. 4.3
+                 * picks it as the representative event with probability phi / Lambda^(N) (k = 1); that atom,
+                 * which a Gaussian decoder cannot form, is drawn as such, and EventGen, trained on the records
+                 * whose representative event is a later one, gives the rest */
+                int centre = N <= 1.0 ? (P->exact_n1 || P->exact_centre) : (P->exact_centre && ua[3] < phi / lam);
+                if (P->mode == 1 && centre) {
+                    xe[0] = 0.0; xe[1] = 0.0; xe[2] = 0.0;
+                    xe[3] = 0.0; xe[4] = 0.0; xe[5] = 1.0;
+                }
                 if (g_plant == 1)
                     lam = lam + 1.0;
 

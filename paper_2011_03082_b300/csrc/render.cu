@@ -86,6 +86,7 @@ static ms_status fill_batch(const ms_render_params* reqs, int n, Batch* b, const
         q.H = p.height;
         q.mode = p.mode;
         q.exact_n1 = p.exact_n1 != 0;
+        q.exact_centre = p.exact_centre != 0;
         q.spp = p.spp;
         q.max_segments = p.max_segments;
         q.seed = p.seed;

@@ -50,7 +50,7 @@ struct Req {
     const float* grid;               // voxel grid of conservative distances, or null
     int32_t grid_n;
     float grid_b, grid_inv_h;
-    int32_t W, H, mode, exact_n1;
+    int32_t W, H, mode, exact_n1, exact_centre;
     uint32_t spp, max_segments;
     uint64_t seed, sample_offset, image_offset, samples_begin;
 };
@@ -228,7 +228,7 @@ __device__ __forceinline__ int find_req(const Batch& B, uint64_t t)
 }
 
 constexpr int kUsedStats = 10;
-constexpr int kDraws = 27 * 16;      // a decoder round's draws: value v of row r at [v * 16 + r]
+constexpr int kDraws = 29 * 16;      // a decoder round's draws: value v of row r at [v * 16 + r]
 constexpr int kDrawKeys = 0;         // staging-tile offset of the draw keys (5 words per row) in a decoder round
 static_assert(kDrawKeys + 5 * 16 <= mmadec::kStageFloats, "decoder-round draw keys exceed the staging tile");
 
@@ -391,10 +391,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             const int rank = __popc(parked & ((1u << lane) - 1u));
             const bool mine = st == kDecode && rank < 16;
             const Req& qq = B.r[req];
-            // The step's draws (tags 2..7: 24 normals; the low bytes of words 0..2 of tags 2, 3 and 4, unused by
-            // the normals, give the absorption, azimuth and exact-N = 1 uniforms) are the same Philox blocks as drawn lane
-            // by lane, but the 6 blocks of each of the nsel selected paths are spread over all 32 lanes and
-            // handed over through shared memory: value v of row r at draws[v * 16 + r].
+            // The step's draws (tags 2..7: 24 normals; the low bytes of words 0..2 of tags 2..6, unused by the
+            // normals, give the absorption, azimuth, exact-N = 1, centre-event and N = 1 exit uniforms) are the
+            // same Philox blocks as drawn lane by lane, but the 6 blocks of each of the nsel selected paths are
+            // spread over all 32 lanes and handed over through shared memory: value v of row r at
+            // draws[v * 16 + r].
             const int nsel = min(16, __popc(parked));
             uint32_t* keys = reinterpret_cast<uint32_t*>(stage) + kDrawKeys;
             if (mine) {
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 const float2 a = box_muller(wd.w0, wd.w1), b = box_muller(wd.w2, wd.w3);
                 float* o = draws + 4 * c * 16 + r;
                 o[0] = a.x; o[16] = a.y; o[32] = b.x; o[48] = b.y;
-                if (c < 3)
+                if (c < 5)
                     draws[(24 + c) * 16 + r] =
                         (float)(((wd.w0 & 0xffu) << 16) | ((wd.w1 & 0xffu) << 8) | (wd.w2 & 0xffu)) * 0x1.0p-24f;
             }
@@ -435,15 +436,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             float N = floorf(__expf(yN) + 0.5f);
             N = fminf(fmaxf(N, mine && qq.exact_n1 ? 2.0f : 1.0f), kNMax);
             // exact_n1: N = 1 (the first free path from the centre leaves the sphere) drawn with its exact
-            // probability exp(-tau), LengthGen (trained on the N >= 2 records) giving the rest
+            // probability exp(-tau), LengthGen (trained on the N >= 2 records) giving the rest; such a step is
+            // exact as a whole (exit along the centre event's HG direction, that event the representative one)
             if (mine && qq.exact_n1 && nrm(26) < __expf(-tau)) N = 1.0f;
+            const bool one = mine && qq.exact_n1 && N <= 1.0f;
             const float lnN = mine ? __logf(N) : 0.0f;
             // PathGen: (cos theta, alpha, beta)
             float xp[16] = {ltau, mine ? qq.g : 0.0f, lnN, nrm(kZP), nrm(kZP + 1), nrm(kZP + 2), nrm(kZP + 3),
                             nrm(kZP + 4)};
             float yP[8];
             mmadec::warp_mlp_rows16<1, kSplit, kHalfBF16, 2, 3 + kLatP, 6>(wpth, stage, xp, yP, rank, mine);
-            const float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * nrm(kEP)));
+            float ct = fminf(1.0f, fmaxf(-1.0f, yP[0] + __expf(0.5f * yP[3]) * nrm(kEP)));
             float al = yP[1] + __expf(0.5f * yP[4]) * nrm(kEP + 1);
             float be = yP[2] + __expf(0.5f * yP[5]) * nrm(kEP + 2);
             float ab2 = al * al + be * be;
@@ -460,8 +463,21 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
                 float e[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) e[k] = yE[k] + __expf(0.5f * yE[6 + k]) * nrm(kEE + k);
+                if (one) {
+                    ct = hg_cosine(nrm(28), qq.g);
+                    al = be = ab2 = 0.0f;
+                }
                 const float phiN = __expf(N * qq.log_phi);
                 const float lam = qq.phi < 1.0f ? __fdividef(qq.phi * (1.0f - phiN), 1.0f - qq.phi) : N;
+                // exact_centre: the first event (the centre, incoming direction) is the representative one with
+                // probability phi / Lambda (Sec. 4.3, k = 1), drawn as such; EventGen gives the later ones
+                // (and exact_n1's N = 1 step takes the centre too)
+                if (N <= 1.0f ? (qq.exact_n1 || qq.exact_centre)
+                              : (qq.exact_centre && nrm(27) < __fdividef(qq.phi, lam))) {
+                    e[0] = e[1] = e[2] = 0.0f;
+                    e[3] = e[4] = 0.0f;
+                    e[5] = 1.0f;
+                }
                 // Eq. 4 and Sec. 4.1: CVAE frame -> world via R^CVAE R_psi, scaled by r
                 V t1, t2;
                 onb(w, &t1, &t2);

@@ -11,6 +11,9 @@ For each density (the density-doubling protocol of Fig. 1 and Sec. 5.2, syntheti
 The sphere tracer is biased (its samplers are learned approximations): when its error is above the brute-force
 error of the smallest ladder run, the speed-up is bounded above by that run, and the result says so.
 
+Every study renders with a model set and the request fields it needs (``pipeline.render_set``): by default
+``pipeline.RENDER_SET``; pass ``cset`` and ``opts`` to use another.
+
 ``python -m paper_2011_03082_b300.experiments [--res 128] [--ref-spp 8192] [--st-spp 256]``, and
 ``python -m paper_2011_03082_b300.experiments --batched [--scale 0.25]`` for the 64-request batch.
 
@@ -33,6 +36,13 @@ import torch
 from . import ms, pipeline, synth
 
 
+def _model_set(cset, opts):
+    """The (cvae_set, request fields) to render with: the default set when ``cset`` is None."""
+    if cset is None:
+        return pipeline.render_set()
+    return cset, dict(opts or {})
+
+
 def _render(p: dict, cset, variant=0):
     img = torch.zeros(p["width"] * p["height"], dtype=torch.float64, device="cuda")
     st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
@@ -53,14 +63,13 @@ def reference_images(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, va
 
 
 def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=256, cset=None, variant=0, refs=None,
-               tau_min=1.0):
+               tau_min=1.0, opts=None):
     """``refs``: reference images from ``reference_images`` at the same res and ref_spp (rendered here when None).
     ``tau_min``: the sphere tracer's minimum optical radius (0: the library's per-density default)."""
-    if cset is None:
-        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    cset, opts = _model_set(cset, opts)
     out = []
     for s in sigmas:
-        base = synth.render_scene(s, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101)
+        base = dict(synth.render_scene(s, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101), **opts)
         ref = refs[s] if refs is not None else _render(base, cset, variant)[0]
         st_img, t_st = _render(dict(base, mode=ms.MS_SPHERE, spp=st_spp, seed=202, min_optical_radius=tau_min),
                                cset, variant)
@@ -90,16 +99,15 @@ def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=2
     return out
 
 
-def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None, sequential=True, tune_div=64):
+def batched(seed=5, n=64, scale=0.25, repeats=3, cset=None, sequential=True, tune_div=64, opts=None):
     """The heterogeneous batch: ``n`` requests (resolution, spp, density, g, albedo, displacement frequency
     drawn with ``seed``; ``scale`` shrinks resolution and spp) in one persistent launch, the renderer variant
     autotuned on the same requests at 1/``tune_div`` of their spp, captured in a CUDA graph and replayed; reports
     light paths per second, per-request completion p50 / p99 (ns counters written by the kernel when each
     request's last path ends) and, with ``sequential``, the time of the same requests rendered one launch at a
     time."""
-    if cset is None:
-        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
-    raw = synth.batch_requests(seed, n, scale=scale)
+    cset, opts = _model_set(cset, opts)
+    raw = [dict(r, **opts) for r in synth.batch_requests(seed, n, scale=scale)]
     reqs = [ms.render_params(r) for r in raw]
     npx = sum(r.width * r.height for r in reqs)
     paths = sum(r.width * r.height * r.spp for r in reqs)
@@ -164,17 +172,16 @@ def _render_batch(reqs: list, cset, variant=0):
     return img.cpu().numpy(), st.cpu().numpy(), a.elapsed_time(b) / 1e3
 
 
-def absorption_sweep(sigma=64.0, res=256, spp=64, settings=6, cset=None, variant=0):
+def absorption_sweep(sigma=64.0, res=256, spp=64, settings=6, cset=None, variant=0, opts=None):
     """Render time of both methods against absorption: RGB absorption (2e-3, 2e-4, 2e-3) x 2^i, i < settings."""
-    if cset is None:
-        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    cset, opts = _model_set(cset, opts)
     out = []
     for i in range(settings):
         absorb = [a * 2.0 ** i for a in (2e-3, 2e-4, 2e-3)]
         row = dict(absorption_rgb=absorb)
         for mode, name in ((ms.MS_SPHERE, "sphere"), (ms.MS_BRUTE, "brute")):
-            reqs = [synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode, seed=7, albedo=1.0 - a)
-                    for a in absorb]
+            reqs = [dict(synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode, seed=7, albedo=1.0 - a),
+                         **opts) for a in absorb]
             img, st, t = _render_batch(reqs, cset, variant)
             paths = 3 * res * res * spp
             row[name] = dict(seconds=t, paths_per_s=paths / t, mean_rgb=[float(img[k * res * res:(k + 1) * res * res].mean()
@@ -186,13 +193,12 @@ def absorption_sweep(sigma=64.0, res=256, spp=64, settings=6, cset=None, variant
 
 
 def fallback_sweep(sigma=64.0, res=128, spp=256, ref_spp=8192, tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None,
-                   variant=0, ref=None):
+                   variant=0, ref=None, opts=None):
     """Render time and RMSE against a brute-force reference for several minimum optical radii of a sphere step;
     ``ref``: the reference image (rendered here when None).  Each row's ``cost`` = time x RMSE^2, the work
     needed per unit of inverse squared error (lower is better)."""
-    if cset is None:
-        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
-    base = synth.render_scene(sigma, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101)
+    cset, opts = _model_set(cset, opts)
+    base = dict(synth.render_scene(sigma, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101), **opts)
     if ref is None:
         ref, _ = _render(base, cset, variant)
     out = []
@@ -206,17 +212,16 @@ def fallback_sweep(sigma=64.0, res=128, spp=256, ref_spp=8192, tau_mins=(0.5, 1.
     return out
 
 
-def time_breakdown(sigmas=(64.0, 128.0), res=512, spp=64, cset=None):
+def time_breakdown(sigmas=(64.0, 128.0), res=512, spp=64, cset=None, opts=None):
     """Where each method's time goes, per density: the instrumented render kernel (phase_timers) reports the
     warps' cycles by round kind (march, decoder, transition, refill) and counts the march steps of shadow rays
     apart from the path's own marches (camera, flight, re-entry).  The march cycles are split between the two in
     proportion to their steps (every march step runs the same loop body).  Counts are per entering path."""
-    if cset is None:
-        cset = ms.cvae_set(pipeline.device_decoders(pipeline.load()))
+    cset, opts = _model_set(cset, opts)
     out = []
     for s in sigmas:
         for mode, name in ((ms.MS_SPHERE, "sphere tracing"), (ms.MS_BRUTE, "brute force")):
-            p = synth.render_scene(s, width=res, height=res, spp=spp, mode=mode, seed=1)
+            p = dict(synth.render_scene(s, width=res, height=res, spp=spp, mode=mode, seed=1), **opts)
             rp = ms.render_params(dict(p, phase_timers=1))
             img = torch.zeros(res * res, dtype=torch.float64, device="cuda")
             st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
@@ -241,13 +246,15 @@ def time_breakdown(sigmas=(64.0, 128.0), res=512, spp=64, cset=None):
 
 
 def fallback_policy(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, spp=256, ref_spp=8192,
-                    tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None, variant=0, refs=None):
+                    tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None, variant=0, refs=None, opts=None):
     """The thin-region threshold per density (Sec. 6): for each density the sweep above, and the minimum optical
     radius with the lowest cost (time x RMSE^2 against the brute-force reference at the same spp); beside it,
     what the library's per-density default (min_optical_radius = 0) picks."""
+    cset, opts = _model_set(cset, opts)
     out = []
     for s in sigmas:
-        rows = fallback_sweep(s, res, spp, ref_spp, tau_mins, cset, variant, None if refs is None else refs[s])
+        rows = fallback_sweep(s, res, spp, ref_spp, tau_mins, cset, variant, None if refs is None else refs[s],
+                              opts=opts)
         best = min((r for r in rows if r["tau_min"] is not None), key=lambda r: r["cost"])
         out.append(dict(sigma_t=s, best_tau_min=best["tau_min"],
                         library_default=float(ms.lib().ms_render_default_min_optical_radius(s)), sweep=rows))
@@ -265,25 +272,28 @@ def main(argv=None):
     ap.add_argument("--absorption", action="store_true", help="run the absorption sweep instead")
     ap.add_argument("--fallback", action="store_true", help="run the fallback-threshold sweep instead")
     ap.add_argument("--policy", action="store_true", help="the fallback-threshold sweep at every density")
+    ap.add_argument("--models", default=pipeline.RENDER_SET, choices=sorted(pipeline.MODEL_SETS),
+                    help="the model set to render with")
     a = ap.parse_args(argv)
+    cset, opts = pipeline.render_set(a.models)
     if a.batched:
-        print(json.dumps(batched(scale=a.scale)))
+        print(json.dumps(batched(scale=a.scale, cset=cset, opts=opts)))
         return
     if a.absorption:
-        for r in absorption_sweep():
+        for r in absorption_sweep(cset=cset, opts=opts):
             print(json.dumps(r))
         return
     if a.fallback:
-        for r in fallback_sweep():
+        for r in fallback_sweep(cset=cset, opts=opts):
             print(json.dumps(r))
         return
     if a.policy:
         sigmas = tuple(float(v) for v in a.sigmas.split(","))
-        for r in fallback_policy(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, spp=a.st_spp):
+        for r in fallback_policy(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, spp=a.st_spp, cset=cset, opts=opts):
             print(json.dumps(r))
         return
     sigmas = tuple(float(v) for v in a.sigmas.split(","))
-    for r in equal_rmse(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp):
+    for r in equal_rmse(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp, cset=cset, opts=opts):
         print(json.dumps(r))
 
 

@@ -76,7 +76,7 @@ class RenderParams(C.Structure):
                 ("min_optical_radius", C.c_float), ("max_optical_radius", C.c_float),
                 ("seed", C.c_uint64), ("sample_offset", C.c_uint64), ("variant", C.c_int32),
                 ("sdf_grid_n", C.c_int32), ("sdf_grid", C.c_void_p), ("exact_n1", C.c_int32),
-                ("phase_timers", C.c_int32)]
+                ("phase_timers", C.c_int32), ("exact_centre", C.c_int32)]
 
 
 class CvaeSet(C.Structure):

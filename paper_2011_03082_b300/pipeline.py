@@ -11,9 +11,19 @@
 3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder), each
    model's shape (p_in, p_out, latent, width: the final settings of Table 1) and the training log.
 
-With ``--exact-n1`` LengthGen is trained on the records with N >= 2 only: a renderer using such a set draws
-N = 1 with its exact probability exp(-tau) (the first free path from the centre leaves the sphere, Sec. 3.1)
-and samples N >= 2 from LengthGen (``render_options``).  The paper's form trains LengthGen on every record.
+With ``--exact-n1`` the three models are trained on the records with N >= 2 only: a renderer using such a set
+draws N = 1 with its exact probability exp(-tau) (the first free path from the centre leaves the sphere,
+Sec. 3.1) and then the whole step exactly (the path leaves radially along the centre event's HG scattering of
+the incoming direction, so alpha = beta = 0: a point mass of PathGen's output that a Gaussian decoder cannot
+form; the centre is the representative event), and samples N >= 2 steps from the models (``render_options``).
+The paper's form trains every model on every record.
+
+With ``--exact-centre`` EventGen is trained on the records whose representative event is not the first one:
+the first event sits at the centre with the incoming direction, and the weights phi^k / Lambda of Sec. 4.3
+pick it with probability phi / Lambda (every record with N = 1, about 1/N of the others), a point mass of
+(X~, W~) = (0, 0, 0, 0, 0, 1) that a Gaussian decoder cannot form: fitting it drives the decoder's variances
+towards zero and pulls the continuous part of the law toward the centre.  A renderer using such a set draws
+the centre event with its exact probability and samples the later events from EventGen.
 
 Run as ``python -m paper_2011_03082_b300.pipeline [--walks N] [--steps S] [--out PATH] [--precision bf16]``.
 """
@@ -30,7 +40,12 @@ import torch
 from . import ms, synth
 
 FORMAT = 2
-DEFAULT_WEIGHTS = Path(__file__).resolve().parent / "weights" / "cvae_set.npz"
+WEIGHTS_DIR = Path(__file__).resolve().parent / "weights"
+DEFAULT_WEIGHTS = WEIGHTS_DIR / "cvae_set.npz"
+# committed model sets: the paper's form (every model trained on every record), the same in BF16 training
+# arithmetic, and the set trained for the exact N = 1 step and centre event (--exact-n1 --exact-centre)
+MODEL_SETS = {"paper": "cvae_set.npz", "bf16": "cvae_set_bf16.npz", "atoms": "cvae_set_atoms.npz"}
+RENDER_SET = "atoms"        # the set the experiments and the benchmark render with
 MODELS = ("length", "path", "event")
 RECORD_KEYS = {"length": ("cL", "xL"), "path": ("cP", "xP"), "event": ("cE", "xE")}
 
@@ -81,14 +96,19 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
 
 
 def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every=100,
-          precision: int = ms.MS_FP32, exact_n1: bool = False) -> dict:
+          precision: int = ms.MS_FP32, exact_n1: bool = False, exact_centre: bool = False) -> dict:
     models = {}
     for i, name in enumerate(MODELS):
         ck, xk = RECORD_KEYS[name]
         c, x = records[ck], records[xk]
-        if name == "length" and exact_n1:
-            # the records with N >= 2: the dequantised y = ln(N - 1/2 + u) is >= ln(3/2) exactly for those
-            keep = x[:, 0] >= float(np.log(1.5))
+        if exact_n1:
+            # the records with N >= 2: LengthGen's dequantised y = ln(N - 1/2 + u) is >= ln(3/2) exactly for
+            # those; PathGen's and EventGen's conditions hold ln N (>= ln 2 = 0.69 for those, 0 for N = 1)
+            keep = x[:, 0] >= float(np.log(1.5)) if name == "length" else c[:, -1] > 0.5
+            c, x = c[keep].contiguous(), x[keep].contiguous()
+        if name == "event" and exact_centre:
+            # the records whose representative event is a later one: the first event's X~ is exactly zero
+            keep = (x[:, :3] != 0.0).any(dim=1)
             c, x = c[keep].contiguous(), x[keep].contiguous()
         params, log = train_one(name, c, x, steps=steps, batch=batch, lr=lr, seed=seed + 17 * i,
                                 log_every=log_every, precision=precision)
@@ -97,8 +117,27 @@ def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every
 
 
 def render_options(models: dict) -> dict:
-    """Render-request fields that a model set needs: ``exact_n1`` when its LengthGen was trained on N >= 2."""
-    return dict(exact_n1=int(bool(models.get("meta", {}).get("exact_n1", False))))
+    """Render-request fields that a model set needs: ``exact_n1`` when its LengthGen was trained on N >= 2,
+    ``exact_centre`` when its EventGen was trained without the records whose representative event is the first."""
+    meta = models.get("meta", {})
+    return dict(exact_n1=int(bool(meta.get("exact_n1", False))),
+                exact_centre=int(bool(meta.get("exact_centre", False))))
+
+
+def load_set(name: str) -> dict:
+    """A committed model set by name (``MODEL_SETS``)."""
+    return load(WEIGHTS_DIR / MODEL_SETS[name])
+
+
+def render_set(models=None, device="cuda", precision=None):
+    """(the ms.cvae_set of a model set's decoders on ``device``, the render-request fields the set needs).
+    ``models``: a loaded set, a name of ``MODEL_SETS``, or None for ``RENDER_SET``; ``precision``: the decoders'
+    arithmetic (ms.MS_FP32 when None)."""
+    if models is None or isinstance(models, str):
+        models = load_set(models or RENDER_SET)
+    dm = device_decoders(models, device)
+    cset = ms.cvae_set(dm) if precision is None else ms.cvae_set(dm, precision=precision)
+    return cset, render_options(models)
 
 
 def decoder_part(name: str, params: np.ndarray) -> np.ndarray:
@@ -155,7 +194,9 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
                     help="training arithmetic (bf16: BF16 products, FP32 accumulation and master weights)")
     ap.add_argument("--exact-n1", action="store_true",
-                    help="train LengthGen on the N >= 2 records (N = 1 is then drawn exactly, exp(-tau))")
+                    help="train the models on the N >= 2 records (the N = 1 step is then drawn exactly)")
+    ap.add_argument("--exact-centre", action="store_true",
+                    help="train EventGen without the centre-event records (that event is then drawn exactly)")
     a = ap.parse_args(argv)
     prec = ms.MS_BF16 if a.precision == "bf16" else ms.MS_FP32
     torch.cuda.synchronize()
@@ -163,12 +204,13 @@ def main(argv=None):
     recs = generate_records(a.walks, a.seed)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=prec, exact_n1=a.exact_n1)
+    models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=prec, exact_n1=a.exact_n1,
+                   exact_centre=a.exact_centre)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     c = recs["counters"].cpu().tolist()
     meta = dict(walks=a.walks, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=a.precision,
-                exact_n1=bool(a.exact_n1),
+                exact_n1=bool(a.exact_n1), exact_centre=bool(a.exact_centre),
                 walk_seconds=t1 - t0,
                 train_seconds=t2 - t1, walk_counters=c,
                 final_loss={k: v["log"][-1][1] for k, v in models.items()})

@@ -64,10 +64,10 @@ def case_train(B=65536):
 
 
 def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0, grid_n=0):
-    """One render; the returned callable exposes the per-request counters as ``.stats``."""
-    models = pipeline.load()
-    cset = ms.cvae_set(pipeline.device_decoders(models))
-    scene = synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode)
+    """One render with the benchmark's model set; the returned callable exposes the per-request counters as
+    ``.stats``."""
+    cset, opts = pipeline.render_set()
+    scene = dict(synth.render_scene(sigma, width=res, height=res, spp=spp, mode=mode), **opts)
     grid = None
     if grid_n:
         grid = ms.ms_sdf_grid_build(scene["disp_amp"], scene["disp_freq"], grid_n)
@@ -86,10 +86,9 @@ def case_render(mode=ms.MS_SPHERE, res=128, spp=16, sigma=64.0, grid_n=0):
 
 
 def case_batch(res, spp=16, sigmas=(16.0, 32.0, 64.0, 128.0)):
-    """The benchmark's four-density batch at a reduced size, default renderer variant."""
-    models = pipeline.load()
-    cset = ms.cvae_set(pipeline.device_decoders(models))
-    reqs = [ms.render_params(synth.render_scene(s, width=res, height=res, spp=spp, mode=ms.MS_SPHERE))
+    """The benchmark's four-density batch (and model set) at a reduced size, default renderer variant."""
+    cset, opts = pipeline.render_set()
+    reqs = [ms.render_params(dict(synth.render_scene(s, width=res, height=res, spp=spp, mode=ms.MS_SPHERE), **opts))
             for s in sigmas]
     img = torch.zeros(len(reqs) * res * res, dtype=torch.float64, device="cuda")
     st = torch.zeros(len(reqs), ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")

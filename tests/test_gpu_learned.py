@@ -5,7 +5,8 @@
   KS statistic between decoder samples and oracle walks, for N (LengthGen) and for cos theta given the walk's
   N (PathGen), compared between the trained and the untrained (Glorot) weights.
 * Rendering: a sphere-traced image with the trained decoders is much closer to a brute-force reference than
-  the same render with untrained decoders.
+  the same render with untrained decoders; and with the set trained for the exact N = 1 step and centre event
+  (both drawn exactly) the image mean matches brute force, where the paper-form set is several percent dark.
 The absolute KS values are reported, not bounded: the paper prints no numbers for them (figures only)."""
 import numpy as np
 import pytest
@@ -105,3 +106,25 @@ def test_trained_sphere_tracing_is_close_to_brute_force():
     e_tr = float(np.sqrt(np.mean((tr - ref) ** 2)))
     e_un = float(np.sqrt(np.mean((un - ref) ** 2)))
     assert e_tr < 0.5 * e_un, (e_tr, e_un)
+
+
+@pytest.mark.parametrize("sigma", [64.0, 128.0])
+def test_exact_point_masses_remove_the_learned_bias(sigma):
+    """The model set trained for the exact N = 1 step and centre event, rendered with both drawn exactly, against
+    the paper-form set (every model trained on every record): image mean over 128 x 128 px at 1,024 spp against
+    a 4,096-spp brute-force reference of the benchmark scene.  The paper form is more than 3% too dark (the
+    Gaussian decoders' fit to the two point masses degenerates); the exact form is within 1.5%."""
+    def mean(models, mode, spp, seed):
+        cs, opt = pipeline.render_set(models)
+        p = dict(synth.render_scene(sigma, width=128, height=128, spp=spp, mode=mode, seed=seed), **opt)
+        img = torch.zeros(128 * 128, dtype=torch.float64, device="cuda")
+        st = torch.zeros(ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+        ms.ms_render(ms.render_params(p), cs if mode == ms.MS_SPHERE else None, img, st)
+        torch.cuda.synchronize()
+        return float(img.sum().item()) / spp
+
+    ref = mean("paper", ms.MS_BRUTE, 4096, seed=7)
+    r_paper = mean("paper", ms.MS_SPHERE, 1024, seed=8) / ref
+    r_atoms = mean("atoms", ms.MS_SPHERE, 1024, seed=8) / ref
+    assert r_paper < 0.97, (r_paper, r_atoms)
+    assert abs(r_atoms - 1.0) < 0.015, (r_paper, r_atoms)

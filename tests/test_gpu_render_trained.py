@@ -7,7 +7,9 @@ their realistic N and Lambda, unlike the untrained decoders of test_gpu_render.p
   * g -0.7 (backward scattering), 0 and 5e-5 (the isotropic branch of the HG sampler, |g| < 1e-4);
   * densities 256 and 512, and a sphere radius capped by the largest optical radius (tau_max 16 at sigma_t 64);
   * a heterogeneous batch shaped like the 64-request workload (resolution, spp, density, g, albedo and
-    displacement frequency drawn per request), checked per request at sampled pixels.
+    displacement frequency drawn per request), checked per request at sampled pixels;
+  * the exact N = 1 step and centre event (exact_n1, exact_centre; alone and together) with the set trained
+    for them (``weights/cvae_set_atoms.npz``).
 Acceptance (oracle images O1 with seed 1 and O2 with seed 2, GPU image G2 with seed 2) — the single-precision
 GPU path follows the FP64 oracle's paths except where a floating-point decision flips, which gives another
 sample of the same distribution:
@@ -204,22 +206,33 @@ def test_renderer_rejects_mixed_or_unknown_decoder_precision(trained):
         gpu_render(p, cs)
 
 
-def test_exact_n1_render_matches_oracle(orc):
-    """exact_n1 (a sphere step takes N = 1 with its exact probability exp(-tau), LengthGen trained on the N >= 2
-    records gives N >= 2): the renderer against the oracle with the same rule and the same model set
-    (weights/cvae_set_n1.npz), same acceptance as the other trained cases (sigma_t 16 and 64)."""
-    models = pipeline.load(pipeline.DEFAULT_WEIGHTS.with_name("cvae_set_n1.npz"))
-    opt = pipeline.render_options(models)
-    assert opt == dict(exact_n1=1)
+@pytest.fixture(scope="module")
+def atoms():
+    models = pipeline.load_set("atoms")
     dec = {k: pipeline.decoder_part(k, models[k]["params"]) for k in pipeline.MODELS}
     cs = ms.cvae_set({k: (torch.from_numpy(dec[k]).cuda(), *synth.MODEL_SHAPES[k]) for k in pipeline.MODELS})
-    decs = [(dec[k].astype(np.float64), *synth.MODEL_SHAPES[k]) for k in pipeline.MODELS]
+    return dict(models=models, cset=cs, decs=[(dec[k].astype(np.float64), *synth.MODEL_SHAPES[k])
+                                              for k in pipeline.MODELS])
+
+
+def test_atoms_set_needs_its_options(atoms):
+    assert pipeline.render_options(atoms["models"]) == dict(exact_n1=1, exact_centre=1)
+
+
+@pytest.mark.parametrize("exact_n1,exact_centre", [(1, 1), (1, 0), (0, 1)])
+def test_exact_atoms_render_matches_oracle(orc, atoms, exact_n1, exact_centre):
+    """The exact N = 1 step (exact_n1: N = 1 with probability exp(-tau), then the exit along the centre event's
+    HG direction, alpha = beta = 0, and the centre as the representative event) and the exact centre event
+    (exact_centre: the first event with probability phi / Lambda), each alone and together: the renderer against
+    the oracle with the same rules and the same decoders (the set trained for both), same acceptance as the other
+    trained cases (sigma_t 16 and 64)."""
+    opt = dict(exact_n1=exact_n1, exact_centre=exact_centre)
     for sigma in (16.0, 64.0):
         p1 = dict(synth.render_scene(sigma, width=32, height=32, spp=16, mode=1, seed=1), **opt)
         p2 = dict(p1, seed=2)
-        o1, _, _ = orc.render(p1, decs)
-        o2, s2, _ = orc.render(p2, decs)
-        g2, gs = gpu_render(p2, cs)
+        o1, _, _ = orc.render(p1, atoms["decs"])
+        o2, s2, _ = orc.render(p2, atoms["decs"])
+        g2, gs = gpu_render(p2, atoms["cset"])
         tol = 2.0 * sigma * (1.0 + p1["disp_amp"] * p1["disp_freq"]) * EPS
         same = np.abs(g2 - o2) <= tol * np.abs(o2) + 1e-9
         assert same.mean() >= 0.98, (sigma, same.mean())

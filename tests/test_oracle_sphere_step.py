@@ -11,6 +11,12 @@
 * The Lambda-weighted representative NEE is unbiased (Sec. 4.3, Eq. 5): on the same walks, Lambda^(N) times
   the representative event's term has the mean of the per-event NEE sum; with the paper's printed
   sum over i = 0..N (N + 1 terms) it does not.
+* The centre event (exact_centre): in a training record the representative event is the first one — at the
+  sphere's centre, with the incoming direction — exactly when its position is the centre, and given N that
+  happens with probability phi / Lambda^(N) (Sec. 4.3, k = 1), the probability the renderer draws it with.
+* The N = 1 step (exact_n1): with probability exp(-tau) the first free path leaves the sphere; such a record
+  exits radially (exit direction = exit position, so alpha = beta = 0) along one HG scattering of the incoming
+  direction, and its representative event is the centre: what the renderer draws for that step.
 * The march (sphere tracing, Hart 1996): a plain Lipschitz-only march (step |f| / (1 + A k)) finds the same
   boundary crossings as the three-bound march, up to the boundary band, and renders the same image.
 """
@@ -117,6 +123,55 @@ def test_lambda_weighted_representative_nee_is_unbiased(orc, tau, g, phi, power)
         d_paper = (lam + 1.0) * term - r["nee_sum"]
         z_paper = d_paper.mean() / (d_paper.std(ddof=1) / np.sqrt(n))
         assert z_paper > 8.0, z_paper
+
+
+@pytest.mark.parametrize("tau,g,phi,power", [(2.0, 0.8, 0.9, True), (6.0, -0.5, 0.97, True),
+                                             (3.0, 0.0, 1.0, False)])
+def test_centre_event_probability(orc, tau, g, phi, power):
+    """The representative event is the first one exactly when it sits at the centre (0, 0, 0), and then its
+    direction is the incoming (0, 0, 1); later events never sit at the centre.  Given N, the first event is
+    picked with probability phi / Lambda^(N), Lambda^(N) = phi (1 - phi^N) / (1 - phi) (N at phi = 1): the count
+    over 200,000 walks against the sum of those probabilities (|z| <= 4).  Taking the uniform 1 / N instead (a
+    plausible slip: the walks' events are equally likely only at phi = 1) fails the same count (|z| > 8)."""
+    n = 200_000
+    r = orc.walk_nee(9, n, tau, g, phi, np.array([0.3, 1.2, 1.5]))
+    N = r["n_events"].astype(np.float64)
+    first = r["rep_index"] == 1
+    at_centre = np.all(r["rep_pos"] == 0.0, axis=1)
+    assert np.array_equal(first, at_centre)
+    assert np.all(r["rep_dir"][first] == np.array([0.0, 0.0, 1.0]))
+    lam = N if phi == 1.0 else phi * (1.0 - phi ** N) / (1.0 - phi)
+
+    def z_of(p):
+        return (first.sum() - p.sum()) / np.sqrt(np.sum(p * (1.0 - p)) + 1e-300)
+
+    assert abs(z_of(phi / lam)) <= 4.0, z_of(phi / lam)
+    if power:
+        assert abs(z_of(1.0 / N)) > 8.0, z_of(1.0 / N)
+
+
+@pytest.mark.parametrize("tau,g", [(0.7, 0.8), (1.5, -0.5), (1.0, 0.0)])
+def test_single_event_step_is_exact(orc, tau, g):
+    """A record with N = 1 has probability exp(-tau) (binomial |z| <= 4); its exit direction equals its exit
+    position (alpha = beta = 0 in the model frame), cos theta = x_z follows the HG law of cosines with
+    parameter g (KS against the closed-form CDF F(mu) = (1 - g^2) / (2g) [(1 + g^2 - 2 g mu)^(-1/2) - 1 / (1 + g)],
+    uniform at g = 0), and its representative event is the centre with the incoming direction (0, 0, 1)."""
+    from scipy import stats
+    n, phi = 200_000, 0.95
+    r = orc.walk(31, n, dict(optical_radius=tau, g=g, albedo=phi, dir_in=(0.0, 0.0, 1.0), isotropic_start=0,
+                             first_event_at_origin=1), reservoir_mode=2)
+    one = r["n_events"] == 1
+    p1 = np.exp(-tau)
+    assert abs(one.sum() - n * p1) <= 4.0 * np.sqrt(n * p1 * (1.0 - p1))
+    x, w = r["exit_pos"][one], r["exit_dir"][one]
+    assert np.max(np.abs(x - w)) < 1e-12
+    assert np.all(r["rep_index"][one] == 1)
+    assert np.all(r["rep_pos"][one] == 0.0) and np.all(r["rep_dir"][one] == np.array([0.0, 0.0, 1.0]))
+    if g == 0.0:
+        cdf = lambda mu: (mu + 1.0) / 2.0
+    else:
+        cdf = lambda mu: (1.0 - g * g) / (2.0 * g) * (1.0 / np.sqrt(1.0 + g * g - 2.0 * g * mu) - 1.0 / (1.0 + g))
+    assert stats.kstest(x[:, 2], cdf).pvalue > 1e-3
 
 
 def _f(A, k, q):
