@@ -608,6 +608,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         // march stay converged; only boundary crossings, which are rare, branch.
 #pragma unroll 1
         for (int step = 0; step < kSteps; ++step) {
+            // the round ends early once no lane marches (its marches are short: a few steps on average)
+            if (!__any_sync(0xffffffffu, st >= kCamera && st <= kShadow)) break;
             if (st < kCamera || st > kShadow) continue;
             const V r = mo + md * mt;
             const bool shadow = st == kShadow, flight = st == kFlight;
