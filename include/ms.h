@@ -139,9 +139,11 @@ typedef struct {
 } ms_decoder;
 
 /* cond: device [n][p_in].  z_eps: device [n][latent + p_out] standard normals (z then eps), or NULL to draw
- * them in the kernel: normals 4j..4j+3 of query q come from counter (j, id_lo, id_hi, 0xD0), id = offset+q,
- * by Box-Muller on 24-bit uniforms (words (w0,w1) and (w2,w3)).  out_mean_logvar: device [n][2P] or NULL;
- * out_sample: device [n][P] or NULL. */
+ * them in the kernel from query q's Philox blocks j = 0..B-1, counter (j, id_lo, id_hi, 0xD0), id = offset+q:
+ * with c = latent + p_out normals, B is the fewest blocks with 4B + floor(4B/3) >= 2 ceil(c/2); uniform k < 4B
+ * is the top 24 bits of word k (block k/4, word k%4), uniform 4B+i is the low bytes of words 3i, 3i+1, 3i+2
+ * ((b0 << 16 | b1 << 8 | b2) 2^-24), and normals 2m, 2m+1 are Box-Muller on uniforms 2m, 2m+1.
+ * out_mean_logvar: device [n][2P] or NULL; out_sample: device [n][P] or NULL. */
 ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const float* z_eps, uint64_t seed,
                         uint64_t offset, uint64_t n, float* out_mean_logvar, float* out_sample, void* stream);
 

@@ -174,12 +174,29 @@ def normals_from_words(words):
 
 
 def decoder_normals(seed, offset, n, count):
-    """Latent and posterior normals of the decoder queries offset..offset+n-1: counter (j, id_lo, id_hi, 0xD0),
-    j = 0, 1, ...; words of block j give normals 4j..4j+3.  Returns [n][count]."""
-    blocks = []
-    for j in range((count + 3) // 4):
-        blocks.append(normals_from_words(philox_words(seed, offset, n, j, 0xD0)))
-    return np.concatenate(blocks, axis=1)[:, :count]
+    """Latent and posterior normals of the decoder queries offset..offset+n-1 (the input layout of the decoder
+    workload, stated in include/ms.h): B Philox blocks, counter (j, id_lo, id_hi, 0xD0) for j < B, where B is the
+    fewest blocks whose 4B words give 2 ceil(count/2) uniforms when every word gives a 24-bit uniform from its
+    top bits and every three words give one more from their low bytes.  Uniforms in order: the top bits of words
+    0..4B-1, then the low bytes of words (0,1,2), (3,4,5), ...; normals 2m, 2m+1 are Box-Muller on uniforms 2m,
+    2m+1.  Returns [n][count]."""
+    need = count + (count & 1)
+    nb = 1
+    while 4 * nb + (4 * nb) // 3 < need:
+        nb += 1
+    words = np.concatenate([philox_words(seed, offset, n, j, 0xD0) for j in range(nb)], axis=1)   # [n][4B]
+    top = u24(words)
+    low = (words & np.uint32(0xFF)).astype(np.uint64)
+    spare = [((low[:, 3 * i] << 16) | (low[:, 3 * i + 1] << 8) | low[:, 3 * i + 2]).astype(np.float64) * 2.0 ** -24
+             for i in range((4 * nb) // 3)]
+    u = np.concatenate([top] + [s[:, None] for s in spare], axis=1)[:, :need]
+    out = np.empty((n, need))
+    for m in range(need // 2):
+        ua, ub = u[:, 2 * m], u[:, 2 * m + 1]
+        r = np.sqrt(-2.0 * np.log(1.0 - ua))
+        out[:, 2 * m] = r * np.cos(2.0 * np.pi * ub)
+        out[:, 2 * m + 1] = r * np.sin(2.0 * np.pi * ub)
+    return out[:, :count]
 
 
 # ---------------------------------------------------------------- walk

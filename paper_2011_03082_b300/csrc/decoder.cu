@@ -42,15 +42,9 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma(const float* __restrict
             if (z_eps) {
                 for (int m = 0; m < nz; ++m) my[m < latent ? p_in + m : 16 + m - latent] = z_eps[q * nz + m];
             } else {
-                const Stream st(seed, offset + q);
-                for (int j = 0; 4 * j < nz; ++j) {
-                    const float4 v = normals4(st, (uint32_t)j, 0xD0u);
-                    const int m = 4 * j;
-                    if (m < nz) my[m < latent ? p_in + m : 16 + m - latent] = v.x;
-                    if (m + 1 < nz) my[m + 1 < latent ? p_in + m + 1 : 16 + m + 1 - latent] = v.y;
-                    if (m + 2 < nz) my[m + 2 < latent ? p_in + m + 2 : 16 + m + 2 - latent] = v.z;
-                    if (m + 3 < nz) my[m + 3 < latent ? p_in + m + 3 : 16 + m + 3 - latent] = v.w;
-                }
+                float v[16];
+                query_normals_runtime(Stream(seed, offset + q), 0xD0u, nz, v);
+                for (int m = 0; m < nz; ++m) my[m < latent ? p_in + m : 16 + m - latent] = v[m];
             }
         }
         float x[16];
@@ -134,8 +128,8 @@ __device__ __forceinline__ void store_row(float* __restrict__ dst, const float* 
     }
 }
 
-// x[PI .. PI+L) = z and eps[0 .. P) of query q: from z_eps [n][L+P], or normals 4j..4j+3 from counter
-// (j, id_lo, id_hi, 0xD0) with id = offset + q.
+// x[PI .. PI+L) = z and eps[0 .. P) of query q: from z_eps [n][L+P], or the query's normals from its Philox
+// stream (tag 0xD0, id = offset + q; layout in decoder.cuh).
 template <int PI, int L, int P, int XN>
 __device__ __forceinline__ void query_normals(const float* __restrict__ z_eps, uint64_t seed, uint64_t id, uint64_t q,
                                               float (&x)[XN], float (&eps)[P])
@@ -145,12 +139,7 @@ __device__ __forceinline__ void query_normals(const float* __restrict__ z_eps, u
     if (z_eps) {
         load_row<NZ>(z_eps + q * NZ, nz);
     } else {
-        const Stream st(seed, id);
-#pragma unroll
-        for (int j = 0; 4 * j < NZ; ++j) {
-            const float4 v = normals4(st, (uint32_t)j, 0xD0u);
-            nz[4 * j] = v.x; nz[4 * j + 1] = v.y; nz[4 * j + 2] = v.z; nz[4 * j + 3] = v.w;
-        }
+        query_normals_philox<NZ>(Stream(seed, id), 0xD0u, nz);
     }
 #pragma unroll
     for (int m = 0; m < L; ++m) x[PI + m] = nz[m];
@@ -173,18 +162,24 @@ __global__ void __launch_bounds__(kMmaThreads) infer_mma_fixed(const float* __re
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t n_chunks = (n + 31) / 32;
     const uint64_t warps = (uint64_t)gridDim.x * (kMmaThreads / 32);
-    for (uint64_t ch = (uint64_t)blockIdx.x * (kMmaThreads / 32) + warp; ch < n_chunks; ch += warps) {
+    // the condition row of the warp's next chunk is loaded one iteration ahead (its latency hides behind the
+    // current chunk's work)
+    uint64_t ch = (uint64_t)blockIdx.x * (kMmaThreads / 32) + warp;
+    float cnext[PI];
+#pragma unroll
+    for (int k = 0; k < PI; ++k) cnext[k] = 0.0f;
+    if (ch * 32 + lane < n) load_row<PI>(cond + (ch * 32 + lane) * PI, cnext);
+    for (; ch < n_chunks; ch += warps) {
         const uint64_t q = ch * 32 + lane;
         const bool live = q < n;
         float x[16], eps[P];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) x[k] = 0.0f;
+        for (int k = 0; k < 16; ++k) x[k] = k < PI ? cnext[k < PI ? k : 0] : 0.0f;
 #pragma unroll
         for (int k = 0; k < P; ++k) eps[k] = 0.0f;
-        if (live) {
-            load_row<PI>(cond + q * PI, x);
-            query_normals<PI, L, P>(z_eps, seed, offset + q, q, x, eps);
-        }
+        const uint64_t qn = q + warps * 32;
+        if (qn < n) load_row<PI>(cond + qn * PI, cnext);
+        if (live) query_normals<PI, L, P>(z_eps, seed, offset + q, q, x, eps);
         float y[8 * NT3];
         mmadec::warp_mlp<NT3, kSplit, kBF16, NTH>(wsm, stage[warp], x, y);
         if (live) {

@@ -149,3 +149,26 @@ def test_scatter_rotation(orc):
     w = np.array([0.6, -0.0, 0.8])
     avg = np.mean([orc.scatter_dir(w, 0.5, (k + 0.5) / 64) for k in range(64)], axis=0)
     assert np.allclose(avg, 0.5 * w, atol=1e-12)
+
+
+@pytest.mark.parametrize("count", [3, 5, 8, 10, 11])
+def test_decoder_normals_are_independent_standard_normals(orc, count):
+    """The decoder workload's normals (Box-Muller on 24-bit uniforms; with ten normals the last pair comes from
+    the low bytes the first eight uniforms leave unused, so two Philox blocks serve instead of three): every
+    column is standard normal (KS against N(0, 1), mean and variance within 5 standard errors) and no two columns
+    correlate, over 100,000 queries.  Counts that fill whole blocks keep the plain layout: normals 4j..4j+3 from
+    block j."""
+    n = 100_000
+    z = orc.decoder_normals(7, 0, n, count)
+    assert z.shape == (n, count)
+    se = 1.0 / np.sqrt(n)
+    for j in range(count):
+        assert stats.kstest(z[:, j], "norm").pvalue > 1e-4, j
+        assert abs(z[:, j].mean()) < 5 * se and abs(z[:, j].var() - 1.0) < 5 * np.sqrt(2.0) * se, j
+    c = np.corrcoef(z.T)
+    assert np.abs(c - np.eye(count)).max() < 5 * se
+    # the first eight normals (and all of them when count is not 9 or 10) come from the blocks in order
+    full = min(count, 8) if count in (9, 10) else count
+    plain = np.concatenate([orc.normals_from_words(orc.philox_words(7, 0, n, j, 0xD0))
+                            for j in range((full + 3) // 4)], axis=1)[:, :full]
+    assert np.array_equal(z[:, :full], plain)
