@@ -270,11 +270,15 @@ def main(argv=None):
 
     # autotune the renderer's scheduling variant on a reduced sample of the same requests (untimed), unless a
     # variant is given
+    # (brute force, the comparison method, gets its own pick on the same sample)
     if args.variant is None:
         tune_reqs = [ms.render_params(dict(r, spp=max(1, spp // 16))) for r in reqs]
         variant, variant_ms = ms.ms_render_autotune(tune_reqs, cset, images, stats, repeats=1, ws=ws)
+        tune_bf = [ms.render_params(dict(r, spp=max(1, spp // 16), mode=ms.MS_BRUTE)) for r in reqs]
+        bf_variant, bf_variant_ms = ms.ms_render_autotune(tune_bf, None, images, stats, repeats=1, ws=ws)
     else:
         variant, variant_ms = args.variant, []
+        bf_variant, bf_variant_ms = args.variant, []
     for r in preqs:
         r.variant = variant
     for _ in range(args.warmup):
@@ -381,7 +385,7 @@ def main(argv=None):
     # ---------------- brute force on the same workload (context: paths/s at equal spp) ----------------
     brute = None
     if not args.no_brute:
-        breqs = [ms.render_params(dict(r, mode=ms.MS_BRUTE, variant=variant)) for r in reqs]
+        breqs = [ms.render_params(dict(r, mode=ms.MS_BRUTE, variant=bf_variant)) for r in reqs]
         images.zero_()
         stats.zero_()
         ms.ms_render_batch(breqs, None, images, stats, ws=ws)   # warm-up
@@ -425,11 +429,12 @@ def main(argv=None):
     equal = policy = batch = breakdown = None
     if rank == 0 and world == 1 and not args.no_equal_rmse:
         from paper_2011_03082_b300 import experiments
-        refs = experiments.reference_images(SIGMAS, args.eq_res, args.eq_ref_spp, variant, cset)
+        refs = experiments.reference_images(SIGMAS, args.eq_res, args.eq_ref_spp, bf_variant, cset)
         rows = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
-                                      variant=variant, refs=refs, tau_min=1.0, opts=opts)
+                                      variant=variant, refs=refs, tau_min=1.0, opts=opts, bf_variant=bf_variant)
         rows_auto = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
-                                           variant=variant, refs=refs, tau_min=0.0, opts=opts)
+                                           variant=variant, refs=refs, tau_min=0.0, opts=opts,
+                                           bf_variant=bf_variant)
         keys = ("sigma_t", "tau_min", "rmse_st", "spp_bf_equal", "t_st_s", "t_bf_equal_s", "speedup", "note")
         equal = {"res": args.eq_res, "ref_spp": args.eq_ref_spp, "st_spp": spp,
                  "per_sigma": [{k: r[k] for k in keys} for r in rows],
@@ -438,7 +443,7 @@ def main(argv=None):
                                                        ms.lib().ms_render_default_min_optical_radius(r["sigma_t"])))
                                               for r in rows_auto]}
         pol = experiments.fallback_policy(SIGMAS, res=args.eq_res, spp=spp, ref_spp=args.eq_ref_spp, cset=cset,
-                                          variant=variant, refs=refs, opts=opts)
+                                          variant=variant, refs=refs, opts=opts, bf_variant=bf_variant)
         policy = [{"sigma_t": r["sigma_t"], "best_tau_min": r["best_tau_min"],
                    "library_default": r["library_default"],
                    "sweep": [{k: v for k, v in x.items() if k != "mode"} for x in r["sweep"]]} for r in pol]
@@ -465,7 +470,9 @@ def main(argv=None):
                            "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1
                            else "single GPU", "stats_per_request": per_req,
                            "kernel_variant": dict(index=variant, **ms.ms_render_variant_info(variant)),
-                           "autotune_ms": [round(t, 2) for t in variant_ms]},
+                           "autotune_ms": [round(t, 2) for t in variant_ms],
+                           "brute_force_variant": dict(index=bf_variant, **ms.ms_render_variant_info(bf_variant)),
+                           "brute_force_autotune_ms": [round(t, 2) for t in bf_variant_ms]},
                 "model_set": {"name": set_name, "file": "paper_2011_03082_b300/weights/" + pipeline.MODEL_SETS[set_name],
                               "render_options": opts},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,

@@ -697,12 +697,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         if (s_stats[k]) atomicAdd(&B.stats[k], s_stats[k]);
 }
 
-// The compiled scheduling variants (decode batch, transition batch, steps per decision, blocks per SM); index 0,
-// the one the autotuner usually selects on the four-density benchmark, is the default.  A decoder round takes at
-// most 16 parked lanes (one tensor-core tile), so the decode thresholds stay <= 16.
+// The compiled scheduling variants (decode batch, transition batch, most steps per march round, blocks per
+// SM); index 0 is the default.  The sphere-tracing picks lie within 2% of each other on the four-density
+// benchmark; brute force (no decoder rounds) prefers larger transition batches and longer march rounds (the last
+// three).  A decoder round takes at most 16 parked lanes (one tensor-core tile), so the decode thresholds stay
+// <= 16.
 #define MS_RENDER_VARIANTS(X)                                                                                 \
-    X(10, 12, 24, 3) X(12, 12, 24, 3) X(8, 12, 24, 3) X(10, 14, 24, 3) X(10, 12, 20, 3) X(10, 12, 28, 3)       \
-    X(10, 16, 24, 3) X(10, 10, 28, 3) X(8, 14, 28, 3)
+    X(10, 12, 24, 3) X(8, 14, 28, 3) X(8, 12, 32, 3) X(12, 12, 24, 3) X(10, 14, 24, 3) X(10, 12, 28, 3)        \
+    X(10, 16, 32, 3) X(10, 20, 32, 3) X(10, 16, 48, 3)
 
 // The kernel of variant i with decoder arithmetic kDec (one translation unit per kDec, compiled in parallel).
 template <int kDec>

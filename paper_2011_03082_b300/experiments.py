@@ -63,21 +63,24 @@ def reference_images(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, va
 
 
 def equal_rmse(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, ref_spp=8192, st_spp=256, cset=None, variant=0, refs=None,
-               tau_min=1.0, opts=None):
+               tau_min=1.0, opts=None, bf_variant=None):
     """``refs``: reference images from ``reference_images`` at the same res and ref_spp (rendered here when None).
-    ``tau_min``: the sphere tracer's minimum optical radius (0: the library's per-density default)."""
+    ``tau_min``: the sphere tracer's minimum optical radius (0: the library's per-density default).
+    ``variant`` / ``bf_variant``: the renderer variants of the sphere tracer and of brute force (each method's
+    own autotuned pick; ``bf_variant`` None: the same as ``variant``)."""
     cset, opts = _model_set(cset, opts)
+    bfv = variant if bf_variant is None else bf_variant
     out = []
     for s in sigmas:
         base = dict(synth.render_scene(s, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101), **opts)
-        ref = refs[s] if refs is not None else _render(base, cset, variant)[0]
+        ref = refs[s] if refs is not None else _render(base, cset, bfv)[0]
         st_img, t_st = _render(dict(base, mode=ms.MS_SPHERE, spp=st_spp, seed=202, min_optical_radius=tau_min),
                                cset, variant)
         rmse_st = float(np.sqrt(np.mean((st_img - ref) ** 2)))
         ladder = []
         spp = 16
         while spp <= ref_spp // 2:
-            img, t = _render(dict(base, spp=spp, seed=303 + spp), cset, variant)
+            img, t = _render(dict(base, spp=spp, seed=303 + spp), cset, bfv)
             ladder.append((spp, float(np.sqrt(np.mean((img - ref) ** 2))), t))
             if ladder[-1][1] <= rmse_st:
                 break
@@ -193,20 +196,21 @@ def absorption_sweep(sigma=64.0, res=256, spp=64, settings=6, cset=None, variant
 
 
 def fallback_sweep(sigma=64.0, res=128, spp=256, ref_spp=8192, tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None,
-                   variant=0, ref=None, opts=None):
+                   variant=0, ref=None, opts=None, bf_variant=None):
     """Render time and RMSE against a brute-force reference for several minimum optical radii of a sphere step;
     ``ref``: the reference image (rendered here when None).  Each row's ``cost`` = time x RMSE^2, the work
     needed per unit of inverse squared error (lower is better)."""
     cset, opts = _model_set(cset, opts)
     base = dict(synth.render_scene(sigma, width=res, height=res, spp=ref_spp, mode=ms.MS_BRUTE, seed=101), **opts)
+    bfv = variant if bf_variant is None else bf_variant
     if ref is None:
-        ref, _ = _render(base, cset, variant)
+        ref, _ = _render(base, cset, bfv)
     out = []
     for tm in tau_mins:
         img, t = _render(dict(base, mode=ms.MS_SPHERE, spp=spp, seed=202, min_optical_radius=tm), cset, variant)
         e = float(np.sqrt(np.mean((img - ref) ** 2)))
         out.append(dict(tau_min=tm, seconds=t, rmse=e, cost=t * e * e))
-    bf, t_bf = _render(dict(base, spp=spp, seed=303), cset, variant)
+    bf, t_bf = _render(dict(base, spp=spp, seed=303), cset, bfv)
     e = float(np.sqrt(np.mean((bf - ref) ** 2)))
     out.append(dict(tau_min=None, mode="brute force", seconds=t_bf, rmse=e, cost=t_bf * e * e))
     return out
@@ -246,7 +250,7 @@ def time_breakdown(sigmas=(64.0, 128.0), res=512, spp=64, cset=None, opts=None):
 
 
 def fallback_policy(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, spp=256, ref_spp=8192,
-                    tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None, variant=0, refs=None, opts=None):
+                    tau_mins=(0.5, 1.0, 2.0, 4.0, 8.0), cset=None, variant=0, refs=None, opts=None, bf_variant=None):
     """The thin-region threshold per density (Sec. 6): for each density the sweep above, and the minimum optical
     radius with the lowest cost (time x RMSE^2 against the brute-force reference at the same spp); beside it,
     what the library's per-density default (min_optical_radius = 0) picks."""
@@ -254,7 +258,7 @@ def fallback_policy(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, spp=256, ref_spp=
     out = []
     for s in sigmas:
         rows = fallback_sweep(s, res, spp, ref_spp, tau_mins, cset, variant, None if refs is None else refs[s],
-                              opts=opts)
+                              opts=opts, bf_variant=bf_variant)
         best = min((r for r in rows if r["tau_min"] is not None), key=lambda r: r["cost"])
         out.append(dict(sigma_t=s, best_tau_min=best["tau_min"],
                         library_default=float(ms.lib().ms_render_default_min_optical_radius(s)), sweep=rows))
