@@ -616,6 +616,7 @@ extern "C" ms_status ms_cvae_forward_backward(const ms_cvae_shape* s, const floa
                                               uint64_t step, float* grad, float* loss3, void* workspace,
                                               size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_cvae_forward_backward");
     Plan pl;
     ms_status st = check_shape(s, "ms_cvae_forward_backward", &pl);
     if (st != MS_OK) return st;
@@ -640,6 +641,7 @@ extern "C" ms_status ms_cvae_forward(const ms_cvae_shape* s, const float* params
                                      const float* eps_z, uint64_t B, uint64_t seed, uint64_t step, float* loss3,
                                      void* workspace, size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_cvae_forward");
     Plan pl;
     ms_status st = check_shape(s, "ms_cvae_forward", &pl);
     if (st != MS_OK) return st;
@@ -662,6 +664,7 @@ extern "C" ms_status ms_cvae_forward(const ms_cvae_shape* s, const float* params
 extern "C" ms_status ms_adam_step(float* params, float* m, float* v, const float* grad, uint64_t n, uint64_t t,
                                   float lr, float beta1, float beta2, float eps, float weight_decay, void* stream)
 {
+    MS_NVTX("ms_adam_step");
     MS_CHECK_ARG(params && m && v && grad, "ms_adam_step: null array");
     MS_CHECK_ARG(t >= 1, "ms_adam_step: step t must be >= 1");
     if (n == 0) return MS_OK;
@@ -678,6 +681,7 @@ extern "C" ms_status ms_cvae_train_step(const ms_cvae_shape* s, float* params, f
                                         float lr, float weight_decay, float* loss3, void* workspace,
                                         size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_cvae_train_step");
     Plan pl;
     ms_status st = check_shape(s, "ms_cvae_train_step", &pl);
     if (st != MS_OK) return st;
@@ -713,6 +717,7 @@ extern "C" ms_status ms_cvae_train_step_dev(const ms_cvae_shape* s, float* param
                                             uint64_t seed, unsigned long long* step, float lr, float weight_decay,
                                             float* loss3, void* workspace, size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_cvae_train_step_dev");
     Plan pl;
     ms_status st = check_shape(s, "ms_cvae_train_step_dev", &pl);
     if (st != MS_OK) return st;

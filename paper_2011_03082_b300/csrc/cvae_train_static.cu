@@ -98,6 +98,7 @@ extern "C" ms_status ms_cvae_train_step_static(const ms_cvae_shape* s, float* pa
                                                uint64_t seed, uint64_t step, float lr, float weight_decay,
                                                float* loss3, void* stream)
 {
+    MS_NVTX("ms_cvae_train_step_static");
     MS_CHECK_ARG(s != nullptr, "ms_cvae_train_step_static: null shape");
     const size_t need = ms_cvae_workspace_size(s, B);
     MS_CHECK_ARG(need <= kStaticScratchBytes,

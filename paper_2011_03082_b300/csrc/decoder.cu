@@ -243,6 +243,7 @@ extern "C" ms_status ms_cvae_infer(const ms_decoder* d, const float* cond, const
                                    uint64_t offset, uint64_t n, float* out_mean_logvar, float* out_sample,
                                    void* stream)
 {
+    MS_NVTX("ms_cvae_infer");
     MS_CHECK_ARG(d != nullptr && d->weights != nullptr, "ms_cvae_infer: null decoder or weights");
     MS_CHECK_ARG(d->width == 8 || d->width == 16, "ms_cvae_infer: width must be 8 or 16 (got %d)", d->width);
     MS_CHECK_ARG(d->p_in >= 1 && d->latent >= 1 && d->latent <= 8 && d->p_in + d->latent <= 16,

@@ -99,6 +99,22 @@ __device__ __forceinline__ unsigned long long warp_ticket(unsigned long long* co
 }  // namespace ms
 
 // ---------------------------------------------------------------------------------------------------------
+// Tracing: every compute entry point of the C ABI opens an NVTX range named after itself for its duration on the
+// host (what it validates and enqueues), so profilers can attribute launches to ABI calls (for example
+// `ncu --nvtx --nvtx-include "ms_render/"`).  NVTX is header-only: without a profiler attached the range calls
+// return at once.
+#include <nvtx3/nvToolsExt.h>
+namespace ms {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace ms
+#define MS_NVTX(name) ::ms::NvtxRange ms_nvtx_range_(name)
+
+// ---------------------------------------------------------------------------------------------------------
 // Host-side status plumbing (defined in capi.cu).
 namespace ms {
 ms_status set_error(ms_status st, const char* fmt, ...);

@@ -82,6 +82,7 @@ extern "C" size_t ms_alu_peaks_scratch_bytes(void)
 
 extern "C" ms_status ms_alu_peaks(double* ops_per_s, void* scratch, size_t scratch_bytes, void* stream)
 {
+    MS_NVTX("ms_alu_peaks");
     using namespace ms::peaks;
     MS_CHECK_ARG(ops_per_s != nullptr, "ms_alu_peaks: null output");
     const size_t need = ms_alu_peaks_scratch_bytes();

@@ -53,6 +53,7 @@ extern "C" ms_status ms_training_records(uint64_t n, const int32_t* n_events, co
                                          const ms_medium* media, int32_t per_photon_media, uint64_t seed, float* cL,
                                          float* xL, float* cP, float* xP, float* cE, float* xE, void* stream)
 {
+    MS_NVTX("ms_training_records");
     MS_CHECK_ARG(n_events && exit_pos && exit_dir && rep_pos && rep_dir && media,
                  "ms_training_records: null input");
     MS_CHECK_ARG(cL && xL && cP && xP && cE && xE, "ms_training_records: null output");

@@ -173,6 +173,7 @@ static ms_status render_launch(const ms_render_params* reqs, int n, const ms_cva
 extern "C" ms_status ms_render(const ms_render_params* p, const ms_cvae_set* models, double* image,
                                unsigned long long* stats, void* workspace, size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_render");
     return render_launch(p, 1, models, image, stats, workspace, workspace_bytes, stream, "ms_render");
 }
 
@@ -180,6 +181,7 @@ extern "C" ms_status ms_render_batch(const ms_render_params* reqs, int n, const 
                                      unsigned long long* stats, void* workspace, size_t workspace_bytes,
                                      void* stream)
 {
+    MS_NVTX("ms_render_batch");
     return render_launch(reqs, n, models, images, stats, workspace, workspace_bytes, stream, "ms_render_batch");
 }
 
@@ -199,6 +201,7 @@ extern "C" ms_status ms_render_autotune(const ms_render_params* reqs, int n, con
                                         unsigned long long* stats, void* workspace, size_t workspace_bytes,
                                         int repeats, int* best_variant, float* ms_per_variant, void* stream)
 {
+    MS_NVTX("ms_render_autotune");
     MS_CHECK_ARG(reqs != nullptr && n >= 1 && n <= kMaxReq && best_variant != nullptr,
                  "ms_render_autotune: need 1..%d requests and best_variant", kMaxReq);
     MS_CHECK_ARG(repeats >= 1, "ms_render_autotune: repeats must be >= 1");

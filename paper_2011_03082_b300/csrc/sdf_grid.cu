@@ -67,6 +67,7 @@ extern "C" size_t ms_sdf_grid_workspace_size(int32_t n)
 extern "C" ms_status ms_sdf_grid_build(float disp_amp, float disp_freq, int32_t n, float* grid, void* workspace,
                                        size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_sdf_grid_build");
     MS_CHECK_ARG(grid != nullptr, "ms_sdf_grid_build: null grid");
     MS_CHECK_ARG(n >= 4 && n <= 1024, "ms_sdf_grid_build: n must be in 4..1024");
     MS_CHECK_ARG(disp_amp >= 0.0f && disp_amp < 1.0f && disp_freq >= 0.0f,

@@ -18,6 +18,7 @@ extern "C" size_t ms_walk_workspace_size(const ms_walk_params* p)
 extern "C" ms_status ms_simulate_walks(const ms_walk_params* p, const ms_walk_out* out, void* workspace,
                                        size_t workspace_bytes, void* stream)
 {
+    MS_NVTX("ms_simulate_walks");
     MS_CHECK_ARG(p != nullptr && out != nullptr, "ms_simulate_walks: null params or outputs");
     MS_CHECK_ARG(p->media != nullptr, "ms_simulate_walks: media is null");
     MS_CHECK_ARG(p->max_events >= 1, "ms_simulate_walks: max_events must be >= 1");
