@@ -10,6 +10,10 @@
    (``ms_cvae_train_step_dev``).
 3. ``save`` / ``load``: a versioned ``.npz`` with the packed float32 parameters (encoder then decoder), each
    model's shape (p_in, p_out, latent, width: the final settings of Table 1) and the training log.
+4. Checkpoint and resume (``--checkpoint-dir``, ``--checkpoint-every``): each model's full training state
+   (master weights, Adam moments, step, draw key) is written every few steps with a CRC (``checkpoint.py``); a
+   run started again with the same directory continues each model from its last checkpoint and ends with the
+   same parameters, bit for bit, as a run that was never interrupted.
 
 With ``--exact-n1`` the three models are trained on the records with N >= 2 only: a renderer using such a set
 draws N = 1 with its exact probability exp(-tau) (the first free path from the centre leaves the sphere,
@@ -37,6 +41,7 @@ from pathlib import Path
 import numpy as np
 import torch
 
+from . import checkpoint as ckpt
 from . import ms, synth
 
 FORMAT = 2
@@ -65,10 +70,14 @@ def generate_records(n_walks: int, seed: int = 1, device="cuda") -> dict:
 
 
 def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch: int, lr: float, seed: int,
-              log_every: int = 100, precision: int = ms.MS_FP32):
+              log_every: int = 100, precision: int = ms.MS_FP32, checkpoint=None, checkpoint_every: int = 0,
+              resume: bool = False):
     """Train one CVAE: one training step (device-side batch sampling, forward, backward, deterministic
     reduction, Adam with its step counter on the device) is captured in a CUDA graph and replayed.
-    ``precision``: MS_FP32, or MS_BF16 (BF16 products with FP32 accumulation and FP32 master weights)."""
+    ``precision``: MS_FP32, or MS_BF16 (BF16 products with FP32 accumulation and FP32 master weights).
+    ``checkpoint``: a file the training state is written to every ``checkpoint_every`` steps and after the last
+    step; with ``resume`` and an existing file, training continues after the step it holds (its model, shape,
+    arithmetic, draw key, batch and learning rate must match)."""
     p_in, p_out, latent, width = synth.MODEL_SHAPES[name]
     shape = ms.cvae_shape(p_in, p_out, latent, width, precision=precision)
     dev = c.device
@@ -76,6 +85,26 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
     step = torch.ones(1, dtype=torch.int64, device=dev)
+    t_first, log = 1, []
+    if resume and checkpoint is not None and Path(checkpoint).exists():
+        st = ckpt.read(checkpoint)
+        want = dict(name=name, shape=[p_in, p_out, latent, width], precision=int(precision), seed=int(seed),
+                    batch=int(batch), lr=float(lr))
+        bad = {k: (st[k], v_) for k, v_ in want.items() if st[k] != v_}
+        if bad:
+            raise ckpt.CheckpointError(f"{checkpoint}: does not match this run: {bad}")
+        params.copy_(torch.from_numpy(st["params"]))
+        m.copy_(torch.from_numpy(st["m"]))
+        v.copy_(torch.from_numpy(st["v"]))
+        step.fill_(int(st["step"]) + 1)
+        t_first = int(st["step"]) + 1
+        log = [tuple(r) for r in st["extra"].get("log", [])]
+
+    def save_state(t):
+        torch.cuda.synchronize(dev)
+        ckpt.write(checkpoint, name=name, shape=(p_in, p_out, latent, width), precision=precision, step=t,
+                   seed=seed, lr=lr, batch=batch, params=params.cpu().numpy(), m=m.cpu().numpy(),
+                   v=v.cpu().numpy(), extra=dict(log=[list(r) for r in log]))
     loss3 = torch.zeros(3, device=dev)
     ws = ms.workspace(int(ms.lib().ms_cvae_train_step_dev_workspace_size(ms.C.byref(shape), batch)), dev)
     x = x.contiguous()
@@ -87,16 +116,21 @@ def train_one(name: str, c: torch.Tensor, x: torch.Tensor, *, steps: int, batch:
     with torch.cuda.stream(side):
         with torch.cuda.graph(graph):
             ms.ms_cvae_train_step_dev(shape, params, m, v, x, c, n, batch, step, seed=seed, lr=lr, loss3=loss3, ws=ws)
-    log = []
-    for t in range(1, steps + 1):
+    for t in range(t_first, steps + 1):
         graph.replay()
         if t % log_every == 0 or t == 1 or t == steps:
             log.append((t, *[float(v_) for v_ in loss3.tolist()]))
+        if checkpoint is not None and ((checkpoint_every and t % checkpoint_every == 0) or t == steps):
+            save_state(t)
     return params, log
 
 
 def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every=100,
-          precision: int = ms.MS_FP32, exact_n1: bool = False, exact_centre: bool = False) -> dict:
+          precision: int = ms.MS_FP32, exact_n1: bool = False, exact_centre: bool = False,
+          checkpoint_dir=None, checkpoint_every: int = 0) -> dict:
+    """Train the three CVAEs; with ``checkpoint_dir``, each model's state goes to ``<dir>/<model>.ckpt`` every
+    ``checkpoint_every`` steps and at its end, and a model whose file exists continues from it (a finished
+    model is not trained again)."""
     models = {}
     for i, name in enumerate(MODELS):
         ck, xk = RECORD_KEYS[name]
@@ -110,8 +144,10 @@ def train(records: dict, *, steps=20000, batch=65536, lr=1e-3, seed=1, log_every
             # the records whose representative event is a later one: the first event's X~ is exactly zero
             keep = (x[:, :3] != 0.0).any(dim=1)
             c, x = c[keep].contiguous(), x[keep].contiguous()
+        path = None if checkpoint_dir is None else Path(checkpoint_dir) / f"{name}.ckpt"
         params, log = train_one(name, c, x, steps=steps, batch=batch, lr=lr, seed=seed + 17 * i,
-                                log_every=log_every, precision=precision)
+                                log_every=log_every, precision=precision, checkpoint=path,
+                                checkpoint_every=checkpoint_every, resume=path is not None)
         models[name] = dict(params=params.cpu().numpy(), log=log)
     return models
 
@@ -197,6 +233,9 @@ def main(argv=None):
                     help="train the models on the N >= 2 records (the N = 1 step is then drawn exactly)")
     ap.add_argument("--exact-centre", action="store_true",
                     help="train EventGen without the centre-event records (that event is then drawn exactly)")
+    ap.add_argument("--checkpoint-dir", default=None,
+                    help="write each model's training state here, and continue from it when it exists")
+    ap.add_argument("--checkpoint-every", type=int, default=1000)
     a = ap.parse_args(argv)
     prec = ms.MS_BF16 if a.precision == "bf16" else ms.MS_FP32
     torch.cuda.synchronize()
@@ -205,7 +244,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     models = train(recs, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed, precision=prec, exact_n1=a.exact_n1,
-                   exact_centre=a.exact_centre)
+                   exact_centre=a.exact_centre, checkpoint_dir=a.checkpoint_dir,
+                   checkpoint_every=a.checkpoint_every)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     c = recs["counters"].cpu().tolist()
