@@ -432,9 +432,12 @@ def main(argv=None):
         refs = experiments.reference_images(SIGMAS, args.eq_res, args.eq_ref_spp, bf_variant, cset)
         rows = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
                                       variant=variant, refs=refs, tau_min=1.0, opts=opts, bf_variant=bf_variant)
-        rows_auto = experiments.equal_rmse(SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset,
-                                           variant=variant, refs=refs, tau_min=0.0, opts=opts,
-                                           bf_variant=bf_variant)
+        # the library's per-density threshold (min_optical_radius 0); when it is 1 at every density the rows
+        # above are already its rows
+        policy_tau = [float(ms.lib().ms_render_default_min_optical_radius(s)) for s in SIGMAS]
+        rows_auto = rows if all(t == 1.0 for t in policy_tau) else experiments.equal_rmse(
+            SIGMAS, res=args.eq_res, ref_spp=args.eq_ref_spp, st_spp=spp, cset=cset, variant=variant, refs=refs,
+            tau_min=0.0, opts=opts, bf_variant=bf_variant)
         keys = ("sigma_t", "tau_min", "rmse_st", "spp_bf_equal", "t_st_s", "t_bf_equal_s", "speedup", "note")
         equal = {"res": args.eq_res, "ref_spp": args.eq_ref_spp, "st_spp": spp,
                  "per_sigma": [{k: r[k] for k in keys} for r in rows],
