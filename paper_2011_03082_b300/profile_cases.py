@@ -3,6 +3,7 @@
 ``python -m paper_2011_03082_b300.profile_cases CASE [--repeat R]`` with CASE one of:
   walk      65,536 photons, optical radius 8, g 0.8, albedo 0.999, isotropic start (FP32)
   walk24    2^24 walks with the training media (FP32, reservoir); walk22: 2^22 of them (ncu captures)
+  records   the record transform (ms_training_records) of 2^24 such walks
   decoder   2^22 decoder queries, P_out 6 (FP32, Philox normals); decoder16: the same in FP16 (tensor cores)
   train     one training step of EventGen, batch 65,536
   render    one 128x128 px x 16 spp render at sigma_t 64, sphere tracing with the trained decoders
@@ -39,6 +40,18 @@ def case_walk24(n=1 << 24):
     tau, g, phi = synth.training_media(1, n)
     media = ms.media_tensor(tau.astype(np.float32), g.astype(np.float32), phi.astype(np.float32), (0, 0, 1), 0, 1)
     return case_walk(n, 2, media)
+
+
+def case_records(n=1 << 24):
+    """The record transform of 2^24 training walks (the walks run once, untimed, when the case is built)."""
+    tau, g, phi = synth.training_media(1, n)
+    media = ms.media_tensor(tau.astype(np.float32), g.astype(np.float32), phi.astype(np.float32), (0, 0, 1), 0, 1)
+    out = ms.walk_outputs(n)
+    ms.ms_simulate_walks(media, n, out, seed=1, reservoir=2, precision=ms.MS_FP32, max_events=1 << 24)
+    recs = {k: torch.empty(n, d, device="cuda") for k, d in
+            (("cL", 2), ("xL", 1), ("cP", 3), ("xP", 3), ("cE", 7), ("xE", 6))}
+    return lambda: ms.ms_training_records(n, out["n_events"], out["exit_pos"], out["exit_dir"], out["rep_pos"],
+                                          out["rep_dir"], media, 1001, recs)
 
 
 def case_decoder(n=1 << 22, p_out=6, precision=ms.MS_FP32):
@@ -105,7 +118,7 @@ def case_batch(res, spp=16, sigmas=(16.0, 32.0, 64.0, 128.0)):
     return run
 
 
-CASES = {"walk": case_walk, "walk24": case_walk24, "walk22": lambda: case_walk24(1 << 22), "decoder": case_decoder, "train": case_train,
+CASES = {"records": case_records, "walk": case_walk, "walk24": case_walk24, "walk22": lambda: case_walk24(1 << 22), "decoder": case_decoder, "train": case_train,
          "decoder16": lambda: case_decoder(precision=ms.MS_FP16),
          "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE),
          "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
