@@ -265,6 +265,21 @@ def fallback_policy(sigmas=(16.0, 32.0, 64.0, 128.0), res=128, spp=256, ref_spp=
     return out
 
 
+def autotuned_variants(sigmas, res, spp, cset=None, opts=None):
+    """(sphere-tracing variant, brute-force variant): each method's fastest renderer variant on one batch of the
+    given densities at res x res px x spp (each method gets its own pick, as in the benchmark)."""
+    cset, opts = _model_set(cset, opts)
+    picks = []
+    for mode in (ms.MS_SPHERE, ms.MS_BRUTE):
+        reqs = [ms.render_params(dict(synth.render_scene(s, width=res, height=res, spp=spp, mode=mode), **opts))
+                for s in sigmas]
+        img = torch.zeros(len(reqs) * res * res, dtype=torch.float64, device="cuda")
+        st = torch.zeros(len(reqs), ms.MS_RENDER_STATS, dtype=torch.int64, device="cuda")
+        best, _ = ms.ms_render_autotune(reqs, cset if mode == ms.MS_SPHERE else None, img, st)
+        picks.append(best)
+    return picks[0], picks[1]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--res", type=int, default=128)
@@ -297,8 +312,10 @@ def main(argv=None):
             print(json.dumps(r))
         return
     sigmas = tuple(float(v) for v in a.sigmas.split(","))
-    for r in equal_rmse(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp, cset=cset, opts=opts):
-        print(json.dumps(r))
+    sv, bv = autotuned_variants(sigmas, a.res, max(1, a.st_spp // 16), cset, opts)
+    for r in equal_rmse(sigmas=sigmas, res=a.res, ref_spp=a.ref_spp, st_spp=a.st_spp, cset=cset, opts=opts,
+                        variant=sv, bf_variant=bv):
+        print(json.dumps(dict(r, variant=sv, bf_variant=bv)))
 
 
 if __name__ == "__main__":
