@@ -2,8 +2,9 @@
 
 * Distributions (the evaluation grid of Sec. 5.3: sigma_t in {1, 4, 20, 100}, g in {-0.7, 0, 0.4, 0.9},
   albedo 1, 10,000 paths from the centre of the unit sphere with incoming direction (0,0,1)): the two-sample
-  KS statistic between decoder samples and oracle walks, for N (LengthGen) and for cos theta given the walk's
-  N (PathGen), compared between the trained and the untrained (Glorot) weights.
+  KS statistic between decoder samples and oracle walks, for N (LengthGen) and for cos theta, alpha and beta
+  given the walk's N (PathGen; the paper's Figs. 9-10 show the same four quantities), compared between the
+  trained and the untrained (Glorot) weights.
 * Rendering: a sphere-traced image with the trained decoders is much closer to a brute-force reference than
   the same render with untrained decoders; and with the set trained for the exact N = 1 step and centre event
   (both drawn exactly) the image mean matches brute force, where the paper-form set is several percent dark.
@@ -13,6 +14,7 @@ import pytest
 import torch
 from scipy import stats
 
+from oracle import cvae
 from paper_2011_03082_b300 import ms, pipeline, synth
 
 pytestmark = pytest.mark.gpu
@@ -48,19 +50,27 @@ def ground_truth(orc):
             r = orc.walk(int(1000 * s + 10 * g) + 1, N_SAMPLES,
                          dict(optical_radius=s, g=float(np.float32(g)), albedo=1.0, dir_in=(0.0, 0.0, 1.0),
                               isotropic_start=0, first_event_at_origin=1))
-            gt[(s, g)] = (r["n_events"].astype(np.float64), r["exit_pos"][:, 2])
+            n = r["n_events"].size
+            zero = np.zeros((n, 3))
+            tg = cvae.training_targets(r["n_events"], r["exit_pos"], r["exit_dir"], zero, zero, np.full(n, s),
+                                       np.full(n, g), np.ones(n), np.full(n, 0.5))
+            gt[(s, g)] = (r["n_events"].astype(np.float64), tg["xP"][:, 0], tg["xP"][:, 1], tg["xP"][:, 2])
     return gt
 
 
 def _ks_table(wdec, gt):
     out = {}
-    for (s, g), (N, ct) in gt.items():
+    for (s, g), (N, ct, al, be) in gt.items():
         cond = np.stack([np.full(N_SAMPLES, np.log(s)), np.full(N_SAMPLES, g)], 1)
         y = _sample(wdec, "length", cond, seed=11)[:, 0]
         Ns = np.maximum(1.0, np.floor(np.exp(np.minimum(y, 30.0)) + 0.5))
         condp = np.stack([cond[:, 0], cond[:, 1], np.log(N)], 1)
-        ctp = np.clip(_sample(wdec, "path", condp, seed=12)[:, 0], -1, 1)
-        out[(s, g)] = (stats.ks_2samp(np.log(Ns), np.log(N)).statistic, stats.ks_2samp(ctp, ct).statistic)
+        pth = _sample(wdec, "path", condp, seed=12)
+        ctp = np.clip(pth[:, 0], -1, 1)
+        # (alpha, beta) as the renderer uses them: rescaled to unit length when longer
+        ab = pth[:, 1:3] / np.maximum(1.0, np.sqrt((pth[:, 1:3] ** 2).sum(axis=1)))[:, None]
+        out[(s, g)] = (stats.ks_2samp(np.log(Ns), np.log(N)).statistic, stats.ks_2samp(ctp, ct).statistic,
+                       stats.ks_2samp(ab[:, 0], al).statistic, stats.ks_2samp(ab[:, 1], be).statistic)
     return out
 
 
@@ -73,10 +83,10 @@ def test_trained_decoders_beat_untrained_on_the_evaluation_grid(ground_truth, ca
     trained = _ks_table(_decoders(True), ground_truth)
     untrained = _ks_table(_decoders(False), ground_truth)
     with capsys.disabled():
-        print("\nsigma_t  g    KS(N) trained/untrained   KS(cos theta | N) trained/untrained")
+        print("\nsigma_t  g    KS trained/untrained: N | cos theta given N | alpha given N | beta given N")
         for k in sorted(trained):
-            print(f"{k[0]:6.0f} {k[1]:4.1f}   {trained[k][0]:.3f} / {untrained[k][0]:.3f}"
-                  f"            {trained[k][1]:.3f} / {untrained[k][1]:.3f}")
+            print(f"{k[0]:6.0f} {k[1]:4.1f}   " + "   ".join(f"{trained[k][j]:.3f} / {untrained[k][j]:.3f}"
+                                                          for j in range(4)))
     for k in trained:
         assert trained[k][1] < untrained[k][1], k
         if k[0] >= 4:
@@ -84,6 +94,8 @@ def test_trained_decoders_beat_untrained_on_the_evaluation_grid(ground_truth, ca
         else:
             assert trained[k][0] < 0.45, k
     assert np.mean([v[0] for v in trained.values()]) < np.mean([v[0] for v in untrained.values()])
+    for j in (2, 3):    # alpha and beta: better than untrained on the grid mean
+        assert np.mean([v[j] for v in trained.values()]) < np.mean([v[j] for v in untrained.values()]), j
 
 
 def test_trained_sphere_tracing_is_close_to_brute_force():
