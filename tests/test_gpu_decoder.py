@@ -144,3 +144,39 @@ def test_half_precision_decoder(p_in, p_out, latent, width, prec):
     mu32, _ = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :latent])
     assert np.abs(got[:, :p_out] - mu32).max() <= (2e-2 if prec == "bf16" else 3e-3)
     assert np.allclose(smp.cpu().numpy(), mu + np.exp(0.5 * lv) * ze[:, latent:], atol=1e-2)
+
+
+def test_decoder_error_report_on_the_benchmark_queries(capsys):
+    """The decoder workload's queries (condition (log tau, g, albedo, cos) + latent 4, width 16, P_out 1 and 6;
+    65,536 queries with given normals) in each precision: max |error| of (mu, log Sigma) against the FP64 oracle
+    with the weights the kernel multiplies (the kernel's arithmetic; <= 1e-5 FP32, <= 3e-3 FP16 / BF16) and
+    against the unrounded weights (the total error of the half-precision forms), printed as a table."""
+    n = 65536
+    cond = synth.decoder_queries(7, n)
+    rows = []
+    for p_out in (1, 6):
+        w = synth.xavier_decoder(7, 4, p_out)
+        ze = synth.standard_normals(5, (n, 4 + p_out))
+        shape = cvae.Shape(4, p_out, 4, 16)
+        mu64, lv64 = cvae.decoder_forward(w.astype(np.float64), shape, cond, ze[:, :4])
+        ref = np.concatenate([mu64, lv64], axis=1)
+        for prec, code in (("fp32", ms.MS_FP32), ("fp16", ms.MS_FP16), ("bf16", ms.MS_BF16)):
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+            mlv = torch.zeros(n, 2 * p_out, device="cuda")
+            d = ms.decoder_struct(dev(w), 4, p_out, 4, 16, precision=code)
+            ms.ms_cvae_infer(d, dev(cond), n, z_eps=dev(ze), out_mean_logvar=mlv)
+            torch.cuda.synchronize()
+            got = mlv.cpu().numpy()
+            if prec == "fp32":
+                err_k = np.abs(got - ref).max()
+            else:
+                wq = w.astype(np.float16).astype(np.float64) if prec == "fp16" else _round_bf16(w)
+                mq, lq = cvae.decoder_forward(wq, shape, cond, ze[:, :4])
+                err_k = np.abs(got - np.concatenate([mq, lq], axis=1)).max()
+            err_t = np.abs(got - ref).max()
+            rows.append((p_out, prec, err_k, err_t))
+            assert err_k <= (1e-5 if prec == "fp32" else 3e-3), (p_out, prec, err_k)
+    with capsys.disabled():
+        print("\nP_out  precision  max|err| kernel arithmetic   max|err| total (vs FP32 weights)")
+        for p_out, prec, ek, et in rows:
+            print(f"{p_out:5d}  {prec:9s}  {ek:.2e}                  {et:.2e}")
