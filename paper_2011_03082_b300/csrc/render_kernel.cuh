@@ -18,7 +18,8 @@
 //    tensor-core tile of up to 16 parked lanes (weights in shared memory in fragment order, decoder_mma.cuh),
 //    while the other lanes keep marching, with no block or grid barrier in the loop;
 //  * a path's NEE sum is kept in a register and added to its pixel (double) once; counters are per-lane
-//    registers flushed to shared, then global, memory;
+//    registers that run over the lane's paths of one request and are flushed to shared, then global, memory
+//    when the lane changes request or finishes;
 //  * everything is bounded: segments per path, steps per march, and the loop ends when the ticket is drained
 //    and no lane holds a path.
 //
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     if (tid == 0) atomicMin(B.t_start, global_ns());
     __syncthreads();
 
-    // counters of the lane's current path (flushed into its request's shared counters when the path ends)
+    // counters of the lane's paths of request `req` (see flush_counters)
     constexpr int kCnt = kTimers ? kUsedStats + 1 : kUsedStats;   // + shadow-march steps (stats[11])
     unsigned cnt[kCnt];
 #pragma unroll
@@ -306,6 +307,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
     Geo geo{0.0f, 0.0f, 1.0f, 1.0f, 0.0f};
     bool drained = false;                       // warp-uniform: camera tickets exhausted
 
+    // The lane's counters belong to request `req` and run over the lane's successive paths of that request; they
+    // go into the block's counters when the lane takes a path of another request, when the largest nears 2^32,
+    // and when the lane finishes.
+    auto flush_counters = [&]() {
+#pragma unroll
+        for (int j = 0; j < kCnt; ++j) {
+            if (cnt[j]) atomicAdd(&s_stats[req * kStats + (j < kUsedStats ? j : 11)], (unsigned long long)cnt[j]);
+            cnt[j] = 0u;
+        }
+    };
     auto end_path = [&]() {
         const Req& qe = B.r[req];
         if (acc != 0.0f) atomicAdd(&B.image[qe.image_offset + id_hi], (double)acc);
@@ -313,11 +324,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         const unsigned long long total_r = (unsigned long long)qe.W * qe.H * qe.spp;
         if (atomicAdd(&B.done[req], 1ull) + 1ull == total_r)
             atomicExch(&B.stats[req * kStats + 10], global_ns() - *((volatile unsigned long long*)B.t_start));
-#pragma unroll
-        for (int j = 0; j < kCnt; ++j) {
-            if (cnt[j]) atomicAdd(&s_stats[req * kStats + (j < kUsedStats ? j : 11)], (unsigned long long)cnt[j]);
-            cnt[j] = 0u;
-        }
         st = kIdle;
     };
     auto start_shadow = [&]() {
@@ -352,7 +358,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
             if (t0 + __popc(idle) >= B.total) drained = true;
             const uint64_t t = t0 + __popc(idle & ((1u << lane) - 1u));
             if (st == kIdle && t < B.total) {
-                req = find_req(B, t);
+                const int nreq = find_req(B, t);
+                if (nreq != req || cnt[8] > (1u << 30)) flush_counters();
+                req = nreq;
                 const Req& q = B.r[req];
                 const uint64_t local = t - q.samples_begin;
                 if ((local >> 32) == 0) {                         // the usual case: 32-bit division
@@ -686,6 +694,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) render_kernel(const __gr
         }
     }
 
+    flush_counters();
     // ---------------- block counters -> global ----------------
     if constexpr (kTimers) {
         if (lane == 0)
