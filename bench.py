@@ -6,7 +6,8 @@ doubling, g = 0.8, albedo 0.999), with the three decoders trained by ``paper_201
 the four images in one persistent ``ms_render_batch`` launch.  The decoders are the model set
 ``pipeline.RENDER_SET`` (trained for the exact N = 1 step and centre event; ``--models paper`` for the set in the
 paper's form).  ``value`` counts camera paths (light paths)
-per second over all ranks.  The brute-force tracer is timed on the same workload for context.
+per second over all ranks.  The brute-force tracer is timed on the same workload for context, with its own
+autotuned kernel variant.
 
 ``python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]``; under torchrun every rank renders
 its own samples (sample offset = rank * spp): weak scaling, no collective on the data path.
