@@ -1,7 +1,7 @@
 """Small, fixed invocations of each kernel for profiling (ncu) and quick timing.
 
 ``python -m paper_2011_03082_b300.profile_cases CASE [--repeat R]`` with CASE one of:
-  walk      65,536 photons, optical radius 8, g 0.8, albedo 0.999, isotropic start (FP32)
+  walk      65,536 photons, optical radius 8, g 0.8, albedo 0.999, isotropic start (FP32); walk_sat: 2^24 of them
   walk24    2^24 walks with the training media (FP32, reservoir); walk22: 2^22 of them (ncu captures)
   records   the record transform (ms_training_records) of 2^24 such walks
   decoder   2^22 decoder queries, P_out 6 (FP32, Philox normals); decoder16: the same in FP16 (tensor cores)
@@ -118,7 +118,7 @@ def case_batch(res, spp=16, sigmas=(16.0, 32.0, 64.0, 128.0)):
     return run
 
 
-CASES = {"records": case_records, "walk": case_walk, "walk24": case_walk24, "walk22": lambda: case_walk24(1 << 22), "decoder": case_decoder, "train": case_train,
+CASES = {"records": case_records, "walk": case_walk, "walk_sat": lambda: case_walk(1 << 24), "walk24": case_walk24, "walk22": lambda: case_walk24(1 << 22), "decoder": case_decoder, "train": case_train,
          "decoder16": lambda: case_decoder(precision=ms.MS_FP16),
          "render": case_render, "brute": lambda: case_render(ms.MS_BRUTE),
          "render512": lambda: case_render(ms.MS_SPHERE, 512, 64, 128.0),
